@@ -1,0 +1,166 @@
+/*
+ * bn.h -- C ABI of the GB300 (sm_103a) Fourier-Galerkin Boltzmann-Nordheim
+ * collision-operator library (libbn.so).
+ *
+ * The library evaluates the Fourier-Galerkin (Filbet-Hu-Jin) approximation of
+ * the space-homogeneous Boltzmann-Nordheim collision operator Q_eps(f) on the
+ * periodised velocity box [-T,T]^d, d = 2 or 3 (Mouton & Rey,
+ * arXiv:2110.13735), and advances d f/dt = Q_eps(f) in time:
+ *
+ *   grid        v_j = 2 T j / N, j in I_N = {-N/2, ..., N/2-1}^d        (Sec. 3.3)
+ *   transform   G^_k = N^-d sum_j f_j exp(-2 i pi k.j/N)                   (Sec. 3.3, step 2(a))
+ *   operator    Q^_n = sum_{k+l=n} [beta(k,l) - beta(l,l)] G^_k G^_l
+ *                      - alpha sum_{k+l+m=n} [beta(k+m,l+m) + beta(l,m)
+ *                                             - beta(l+m,l) - beta(l,l+m)] G^_k G^_l G^_m
+ *               with alpha = -eps, k,l,m,n in I_N, no wrap-around       (Lemma, Sec. 2.3; step 2(c))
+ *   kernel      beta(a,b) = C sum_p alpha_p(a) alpha'_p(b)                (Sec. 2.5, eq. betadD)
+ *   scaling     Q_eps(f)(v_j) = (T/pi)^{d+gamma} Re sum_n Q^_n exp(2 i pi n.j/N)   (Sec. 3.2)
+ *
+ * eps = +1 bosons, -1 fermions, 0 classical particles (any real eps is
+ * accepted, e.g. eps = -hbar^d).  Kernels: 2-D Maxwell molecules (gamma = 0)
+ * and 3-D hard spheres (gamma = 1), b == 1, truncation radius R in velocity
+ * units with R_xi = pi R / T satisfying R_xi (3 + sqrt 2) <= 2 pi (Sec. 4.1).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a bn_status; no call aborts, throws or exits.  After a
+ *    failure bn_last_error() returns a message for the calling thread.
+ *  - Host arrays are owned by the caller; the library copies in and out and
+ *    keeps no host pointer.  Device arrays passed in ("_device" calls) must be
+ *    on the solver's device; the library reads/writes them on the solver's
+ *    stream and keeps no pointer after the call returns.
+ *  - Arrays of grid values are row-major over I_N^d (index j_i + N/2, last
+ *    dimension fastest), FP64, count = N^d.
+ *  - A solver owns all of its device memory and one CUDA stream (the one given
+ *    to bn_create_solver, or the legacy default stream if NULL).  A solver is
+ *    not thread-safe; distinct solvers may be used from distinct threads.
+ *  - Calls that return host data synchronise the solver's stream; the others
+ *    are asynchronous with respect to the host unless stated.
+ */
+#ifndef BN_H
+#define BN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bn_solver bn_solver;
+
+typedef enum {
+    BN_OK = 0,
+    BN_ERR_ARG = -1,         /* invalid argument (sizes, d, N, kernel, null pointer) */
+    BN_ERR_ALIAS = -2,       /* R_xi (3 + sqrt 2) > 2 pi: anti-aliasing condition violated (Sec. 4.1) */
+    BN_ERR_NOMEM = -3,       /* device or host allocation failed */
+    BN_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    BN_ERR_NONFINITE = -5,   /* the state became NaN/Inf during step_rk (state rolled back) */
+    BN_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    BN_ERR_STATE = -7,       /* call out of order (e.g. no state set) */
+    BN_ERR_UNSUPPORTED = -8  /* combination not implemented (e.g. 2-D hard spheres) */
+} bn_status;
+
+typedef enum { BN_MAXWELL = 0, BN_HARD_SPHERE = 1 } bn_kernel;
+
+typedef enum { BN_FP64 = 0, BN_MIXED = 1 } bn_precision;
+
+typedef struct {
+    int M;            /* 2-D angular points of eq. beta2D; 0 = default 2N */
+    int M1, M2;       /* 3-D (theta, phi) points of eq. beta3D; 0 = default N/2 each */
+    int precision;    /* BN_FP64, or BN_MIXED: FP32 bulk pair/triple sums with
+                         compensated accumulation, FP64 kernel modes, transforms,
+                         combination, moments, conservation correction and state */
+    int conserve;     /* 1: project Q onto zero mass, momentum and energy (FP64) */
+    double c_phi;     /* C_Phi; 0 = default 1/(2 pi) (2-D), 1/(4 pi) (3-D) */
+    int integrator;   /* 0 = classical RK4, 1 = SSP-RK2 (Heun) */
+    int quad3d;       /* 3-D theta rule: 0 = Gauss-Legendre in cos(theta),
+                         1 = the printed sin(theta_p)-weighted rectangle rule */
+} bn_options;
+
+/* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
+bn_status bn_default_options(bn_options* opt);
+
+/*
+ * Create a solver for the operator (d, N, T, R, kernel, eps).  d in {2,3};
+ * N even, 4 <= N <= 64 (2-D) or <= 48 (3-D); T > 0 the box half-width; R > 0
+ * the truncation radius (velocity units); kernel BN_MAXWELL (d = 2) or
+ * BN_HARD_SPHERE (d = 3); opt may be NULL; cuda_stream is a cudaStream_t or
+ * NULL.  Builds the kernel-mode tables in FP64 on the device (once per
+ * solver; solvers with equal (d, N, R_xi, kernel, M, precision) share them).
+ * On success *out owns the solver; release it with bn_destroy_solver.
+ */
+bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double eps,
+                           const bn_options* opt, void* cuda_stream, bn_solver** out);
+
+/* Release the solver and its device memory (shared tables are refcounted). */
+void bn_destroy_solver(bn_solver* s);
+
+/* State f_j = f(v_j) from host memory (count = N^d); resets t to 0. */
+bn_status bn_set_state(bn_solver* s, const double* f, size_t count);
+/* Same from device memory on the solver's device. */
+bn_status bn_set_state_device(bn_solver* s, const double* f_dev, size_t count);
+/* Copy the current state to host memory (synchronises). */
+bn_status bn_get_state(bn_solver* s, double* f, size_t count);
+/* Copy the current state to device memory (asynchronous on the solver's stream). */
+bn_status bn_get_state_device(bn_solver* s, double* f_dev, size_t count);
+
+/* Q_eps(f)(v_j) of the current state, in velocity units, to host memory (synchronises). */
+bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count);
+/* Q_eps(f) of the device array f_dev into the device array Q_dev (both N^d FP64);
+ * the solver's state is not touched.  Asynchronous on the solver's stream. */
+bn_status bn_eval_collision_device(bn_solver* s, const double* f_dev, double* Q_dev, size_t count);
+
+/* Advance the state by nsteps steps of size dt with the chosen integrator
+ * (c = 1 in eq. Boltzmann_homo).  The steps run as one captured CUDA graph per
+ * step.  If the state turns non-finite the call returns BN_ERR_NONFINITE and
+ * the state is that of the last finite step (bn_moments reports its time).
+ * Synchronises the solver's stream. */
+bn_status bn_step_rk(bn_solver* s, double dt, int nsteps);
+
+/*
+ * Moments of the current state (Sec. 4, head), FP64, count >= d + 6:
+ * out = [rho, rho u_1 .. rho u_d, e, E_c, H, max f, t] with
+ * rho = dv sum f, rho u = dv sum v f, e = dv sum |v-u|^2 f / (2 rho),
+ * E_c = dv sum |v|^2 f, H = dv sum [f ln f + (1 + eps f)/(-eps) ln(1 + eps f)]
+ * (eps != 0; dv sum f ln f for eps = 0; non-positive arguments skipped),
+ * dv = (2T/N)^d.  Synchronises.
+ */
+bn_status bn_moments(bn_solver* s, double* out, size_t count);
+
+/* Work counts of one evaluation: out[0] = quadratic terms (C2), out[1] =
+ * terms of the reducible cubic sums, out[2] = terms of the Q_{1,q} triple sum
+ * (C3, 0 when eps = 0), out[3] = N^d.  count >= 4. */
+bn_status bn_work_counts(const bn_solver* s, double* out, size_t count);
+
+/* Device kernel launches issued by this solver since creation (all kernels). */
+long long bn_kernel_launches(const bn_solver* s);
+
+/*
+ * Live timing of the dominant kernel (the Q_{1,q} triple sum): when enabled,
+ * CUDA events are recorded on the solver's stream around every launch of that
+ * kernel (also inside the captured step graph).  bn_profile_read returns
+ * out[0] = summed duration in ms and out[1] = number of launches timed since
+ * the last read, then resets both.  Within one bn_step_rk call only the last
+ * step's launches can be timed (earlier replays reuse the same events); call
+ * it with nsteps = 1 to time every launch.  Enabling or disabling recaptures
+ * the step graph.  count >= 2.
+ */
+bn_status bn_profile_enable(bn_solver* s, int enable);
+bn_status bn_profile_read(bn_solver* s, double* out, size_t count);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* bn_last_error(void);
+
+/*
+ * Batched stepping: advance n solvers by nsteps RK steps of their own dt
+ * (dts[i]) in shared launches.  The solvers may differ in d, N, eps, kernel
+ * and precision; each must have a state.  All run on the stream of solvers[0].
+ * Stops at the first non-finite solver (status BN_ERR_NONFINITE, *failed set
+ * to its index, its state rolled back); others keep their progress.
+ */
+bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int nsteps, int* failed);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BN_H */

@@ -1,0 +1,207 @@
+"""Python binding of libbn (include/bn.h): argument marshalling only.
+
+Every step of the collision operator and of the time stepping runs in the CUDA
+library; this module converts numpy arrays / torch tensors to pointers and
+statuses to exceptions.  Importing it does not need a GPU; creating a solver
+does, and fails loudly when the library or the device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbn.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bn.h")
+
+BN_OK = 0
+STATUS = {0: "BN_OK", -1: "BN_ERR_ARG", -2: "BN_ERR_ALIAS", -3: "BN_ERR_NOMEM", -4: "BN_ERR_CUDA",
+          -5: "BN_ERR_NONFINITE", -6: "BN_ERR_TIMEOUT", -7: "BN_ERR_STATE", -8: "BN_ERR_UNSUPPORTED"}
+MAXWELL, HARD_SPHERE = 0, 1
+FP64, MIXED = 0, 1
+
+
+class BNError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("precision", ctypes.c_int),
+                ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
+                ("quad3d", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbn.so (built by ``paper_2110_13735_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbn.so not found at {path}: run paper_2110_13735_gb300/build.py (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    lib.bn_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.bn_create_solver.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+    lib.bn_destroy_solver.argtypes = [vp]
+    lib.bn_destroy_solver.restype = None
+    lib.bn_set_state.argtypes = [vp, dp, sz]
+    lib.bn_set_state_device.argtypes = [vp, vp, sz]
+    lib.bn_get_state.argtypes = [vp, dp, sz]
+    lib.bn_get_state_device.argtypes = [vp, vp, sz]
+    lib.bn_eval_collision.argtypes = [vp, dp, sz]
+    lib.bn_eval_collision_device.argtypes = [vp, vp, vp, sz]
+    lib.bn_step_rk.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.bn_moments.argtypes = [vp, dp, sz]
+    lib.bn_work_counts.argtypes = [vp, dp, sz]
+    lib.bn_kernel_launches.argtypes = [vp]
+    lib.bn_kernel_launches.restype = ctypes.c_longlong
+    lib.bn_last_error.restype = ctypes.c_char_p
+    lib.bn_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.bn_profile_read.argtypes = [vp, dp, sz]
+    lib.bn_step_rk_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    _lib = lib
+    return lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions declared in include/bn.h."""
+    import re
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bn_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != BN_OK:
+        msg = _lib.bn_last_error().decode() if _lib is not None else ""
+        raise BNError(status, msg)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0) -> Options:
+    o = Options()
+    o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
+    o.c_phi, o.integrator, o.quad3d = c_phi, integrator, quad3d
+    return o
+
+
+class Solver:
+    """One collision operator (d, N, T, R, kernel, eps) with its device state.
+
+    ``stream`` may be a ``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer.
+    """
+
+    def __init__(self, d, N, T, R, kernel=MAXWELL, eps=0.0, stream=None, **opts):
+        lib = load()
+        self.d, self.N, self.T, self.R, self.kernel, self.eps = int(d), int(N), float(T), float(R), int(kernel), float(eps)
+        self.opts = options(**opts)
+        raw = 0
+        if stream is not None:
+            raw = int(getattr(stream, "cuda_stream", stream))
+        h = ctypes.c_void_p()
+        _check(lib.bn_create_solver(self.d, self.N, self.T, self.R, self.kernel, self.eps, ctypes.byref(self.opts),
+                                    ctypes.c_void_p(raw) if raw else None, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_modes(self):
+        return self.N ** self.d
+
+    @property
+    def shape(self):
+        return (self.N,) * self.d
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.bn_destroy_solver(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        _check(_lib.bn_set_state(self._h, _dptr(f), f.size))
+
+    def set_state_device(self, f_dev):
+        """f_dev: a contiguous float64 CUDA tensor with N^d entries."""
+        _check(_lib.bn_set_state_device(self._h, ctypes.c_void_p(f_dev.data_ptr()), f_dev.numel()))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(self.n_modes)
+        _check(_lib.bn_get_state(self._h, _dptr(out), out.size))
+        return out.reshape(self.shape)
+
+    def get_state_device(self, out_dev):
+        _check(_lib.bn_get_state_device(self._h, ctypes.c_void_p(out_dev.data_ptr()), out_dev.numel()))
+
+    def eval_collision(self) -> np.ndarray:
+        out = np.empty(self.n_modes)
+        _check(_lib.bn_eval_collision(self._h, _dptr(out), out.size))
+        return out.reshape(self.shape)
+
+    def eval_collision_device(self, f_dev, Q_dev):
+        _check(_lib.bn_eval_collision_device(self._h, ctypes.c_void_p(f_dev.data_ptr()),
+                                             ctypes.c_void_p(Q_dev.data_ptr()), f_dev.numel()))
+
+    def step_rk(self, dt: float, nsteps: int):
+        _check(_lib.bn_step_rk(self._h, float(dt), int(nsteps)))
+
+    def moments(self) -> np.ndarray:
+        out = np.empty(self.d + 6)
+        _check(_lib.bn_moments(self._h, _dptr(out), out.size))
+        return out
+
+    def work_counts(self) -> np.ndarray:
+        out = np.empty(4)
+        _check(_lib.bn_work_counts(self._h, _dptr(out), out.size))
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(_lib.bn_kernel_launches(self._h))
+
+    def profile_enable(self, on: bool = True):
+        _check(_lib.bn_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        """(summed ms, launches) of the triple-sum kernel since the last read."""
+        out = np.zeros(2)
+        _check(_lib.bn_profile_read(self._h, _dptr(out), 2))
+        return float(out[0]), int(out[1])
+
+
+def step_rk_batch(solvers, dts, nsteps: int):
+    """Advance several solvers together (include/bn.h: bn_step_rk_batch); returns the failed index or -1."""
+    lib = load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    failed = ctypes.c_int(-1)
+    st = lib.bn_step_rk_batch(hs, n, _dptr(d), int(nsteps), ctypes.byref(failed))
+    _check(st)
+    return failed.value

@@ -1,0 +1,439 @@
+// bn_api.cu -- the C ABI of libbn (include/bn.h): solver lifecycle, evaluation of
+// Q_eps(f) (Mouton & Rey, Sec. 3.3 step 2, classical method of Sec. 3.2) and
+// Runge-Kutta time stepping with one captured CUDA graph per step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "bn_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+bn_status fail(bn_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+bn_status cuda_fail(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? BN_ERR_NOMEM : BN_ERR_CUDA, m);
+}
+
+void free_buffers(bn_solver* s) {
+    void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->S2, s->quad,
+                    s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (s->flags_host) cudaFreeHost(s->flags_host);
+}
+
+// One evaluation Q = Q_eps(f_in) in velocity units, entirely on the solver's stream.
+void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
+    bn::launch_dft_forward(s, f_in, s->Ghat);
+    if (s->opt.precision == BN_MIXED) bn::launch_to_fp32(s, s->Ghat, s->Ghat32, s->g.nModes);
+    bn::launch_pair_sums(s);
+    if (s->eps != 0.0) {
+        const int slot = s->prof_slot;
+        if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
+        bn::launch_triple_sum(s);
+        if (s->prof && slot < 8) {
+            cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
+            s->prof_slot = slot + 1;
+        }
+    }
+    bn::launch_combine(s);
+    bn::launch_dft_inverse_real(s, s->Qhat, Q_out, s->scale);
+    if (s->opt.conserve) bn::launch_conserve(s, Q_out);
+}
+
+// One time step of the chosen integrator on s->f (state committed only if finite).
+void record_step(bn_solver* s, double dt) {
+    if (s->opt.integrator == 0) {
+        // classical RK4: K1..K4, f += dt/6 (K1 + 2 K2 + 2 K3 + K4)
+        eval_device(s, s->f, s->Qv);
+        bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 1.0, 0.5, dt, 1);
+        eval_device(s, s->y, s->Qv);
+        bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 2.0, 0.5, dt, 0);
+        eval_device(s, s->y, s->Qv);
+        bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 2.0, 1.0, dt, 0);
+        eval_device(s, s->y, s->Qv);
+        bn::launch_rk_final(s, s->f, s->kacc, s->Qv, 1.0, dt, s->f_prev, s->flags);
+    } else {
+        // SSP-RK2 (Heun): y = f + dt K(f); f = (f + y + dt K(y)) / 2
+        eval_device(s, s->f, s->Qv);
+        bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 0.0, 1.0, dt, 1);
+        eval_device(s, s->y, s->Qv);
+        bn::launch_heun_final(s, s->f, s->y, s->Qv, dt, s->f_prev, s->flags);
+    }
+}
+
+bn_status ensure_graph(bn_solver* s, double dt) {
+    if (s->step_graph && s->graph_dt == dt) return BN_OK;
+    if (s->step_graph) {
+        cudaGraphExecDestroy(s->step_graph);
+        s->step_graph = nullptr;
+    }
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "stream capture");
+    long long before = s->launches;
+    s->prof_slot = 0;
+    record_step(s, dt);
+    s->prof_slots_used = s->prof_slot;
+    s->graph_launches = s->launches - before;
+    s->launches = before;   // captured launches are counted when the graph runs
+    e = cudaStreamEndCapture(s->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "stream capture end");
+    e = cudaGraphInstantiate(&s->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    s->graph_dt = dt;
+    return BN_OK;
+}
+
+bool valid_solver(const bn_solver* s) { return s != nullptr; }
+
+// Accumulate the durations of the triple-sum launches recorded by the last graph replay
+// or direct evaluation (the stream has been synchronised).
+void harvest_profile(bn_solver* s, int slots) {
+    if (!s->prof) return;
+    for (int i = 0; i < slots && i < 8; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]) == cudaSuccess) {
+            s->prof_ms += ms;
+            s->prof_count += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+bn_status bn_default_options(bn_options* opt) {
+    if (!opt) return fail(BN_ERR_ARG, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    return BN_OK;
+}
+
+const char* bn_last_error(void) { return g_err.c_str(); }
+
+bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double eps, const bn_options* opt,
+                           void* cuda_stream, bn_solver** out) {
+    if (!out) return fail(BN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (d != 2 && d != 3) return fail(BN_ERR_ARG, "d must be 2 or 3");
+    if (N < 4 || N % 2 != 0) return fail(BN_ERR_ARG, "N must be even and >= 4");
+    if ((d == 2 && N > 64) || (d == 3 && N > 16))
+        return fail(BN_ERR_UNSUPPORTED, d == 2 ? "2-D N > 64 is not supported" : "3-D N > 16 is not supported yet");
+    if (!(T > 0) || !(R > 0) || !std::isfinite(T) || !std::isfinite(R)) return fail(BN_ERR_ARG, "T and R must be > 0");
+    if (!std::isfinite(eps)) return fail(BN_ERR_ARG, "eps must be finite");
+    if (kernel != BN_MAXWELL && kernel != BN_HARD_SPHERE) return fail(BN_ERR_ARG, "unknown kernel");
+    if (d == 2 && kernel != BN_MAXWELL)
+        return fail(BN_ERR_UNSUPPORTED, "2-D hard spheres: the kernel is not separable (no formula in the paper)");
+    if (d == 3 && kernel != BN_HARD_SPHERE) return fail(BN_ERR_UNSUPPORTED, "3-D supports hard spheres only");
+    const double Rxi = M_PI * R / T;
+    if (Rxi * (3.0 + std::sqrt(2.0)) > 2.0 * M_PI * (1.0 + 1e-12))
+        return fail(BN_ERR_ALIAS, "anti-aliasing: pi R / T (3 + sqrt 2) must not exceed 2 pi");
+
+    bn_solver* s = new bn_solver();
+    s->g.d = d;
+    s->g.N = N;
+    s->g.nModes = d == 2 ? N * N : N * N * N;
+    s->g.E = 2 * N;
+    s->g.nExt = d == 2 ? 4 * N * N : 8 * N * N * N;
+    s->T = T;
+    s->R = R;
+    s->Rxi = Rxi;
+    s->eps = eps;
+    s->kernel = kernel;
+    if (opt) s->opt = *opt;
+    else bn_default_options(&s->opt);
+    if (s->opt.precision != BN_FP64 && s->opt.precision != BN_MIXED) {
+        delete s;
+        return fail(BN_ERR_ARG, "precision must be BN_FP64 or BN_MIXED");
+    }
+    if (s->opt.integrator != 0 && s->opt.integrator != 1) {
+        delete s;
+        return fail(BN_ERR_ARG, "integrator must be 0 (RK4) or 1 (SSP-RK2)");
+    }
+    if (s->opt.M <= 0) s->opt.M = 2 * N;
+    if (s->opt.M1 <= 0) s->opt.M1 = N / 2;
+    if (s->opt.M2 <= 0) s->opt.M2 = N / 2;
+    if (s->opt.c_phi <= 0) s->opt.c_phi = d == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI);
+    if (d == 2) { s->opt.M1 = s->opt.M2 = 0; s->opt.quad3d = 0; }
+    else s->opt.M = 0;
+    s->scale = std::pow(T / M_PI, d + (kernel == BN_HARD_SPHERE ? 1 : 0));
+
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { delete s; return cuda_fail(e, "no CUDA device"); }
+    if (cuda_stream) {
+        s->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete s; return cuda_fail(e, "stream create"); }
+        s->own_stream = true;
+    }
+    std::string err;
+    bn_status st = bn::acquire_tables(s, &err);
+    if (st != BN_OK) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return fail(st, err);
+    }
+    st = bn::build_work_list(s, &err);
+    if (st != BN_OK) {
+        bn::release_tables(s->tabs);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return fail(st, err);
+    }
+    s->n_partials = bn::triple_partials(s);
+    const size_t n = s->g.nModes;
+    e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&s->f, n * sizeof(double));
+    alloc((void**)&s->f_prev, n * sizeof(double));
+    alloc((void**)&s->y, n * sizeof(double));
+    alloc((void**)&s->kacc, n * sizeof(double));
+    alloc((void**)&s->Qv, n * sizeof(double));
+    alloc((void**)&s->Ghat, n * sizeof(double2));
+    alloc((void**)&s->Ghat32, n * sizeof(float2));
+    alloc((void**)&s->work_c, n * sizeof(double2));
+    alloc((void**)&s->S2, (size_t)s->g.nExt * sizeof(double2));
+    alloc((void**)&s->quad, n * sizeof(double2));
+    alloc((void**)&s->red, n * sizeof(double2));
+    alloc((void**)&s->q1q, n * sizeof(double2));
+    alloc((void**)&s->partials, (size_t)s->n_partials * n * sizeof(double2));
+    alloc((void**)&s->Qhat, n * sizeof(double2));
+    alloc((void**)&s->moments, 16 * sizeof(double));
+    alloc((void**)&s->flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->flags_host, 4 * sizeof(int));
+    if (e != cudaSuccess) {
+        bn_status r = cuda_fail(e, "device buffers");
+        free_buffers(s);
+        bn::release_tables(s->tabs);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return r;
+    }
+    cudaMemsetAsync(s->flags, 0, 4 * sizeof(int), s->stream);
+    cudaMemsetAsync(s->S2, 0, (size_t)s->g.nExt * sizeof(double2), s->stream);
+    cudaMemsetAsync(s->q1q, 0, n * sizeof(double2), s->stream);
+    cudaMemsetAsync(s->red, 0, n * sizeof(double2), s->stream);
+    *out = s;
+    return BN_OK;
+}
+
+void bn_destroy_solver(bn_solver* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
+    for (cudaEvent_t ev : s->prof_ev)
+        if (ev) cudaEventDestroy(ev);
+    free_buffers(s);
+    bn::release_tables(s->tabs);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+bn_status bn_set_state(bn_solver* s, const double* f, size_t count) {
+    if (!valid_solver(s) || !f) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    cudaError_t e = cudaMemcpyAsync(s->f, f, count * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state");
+    s->has_state = true;
+    s->t = 0;
+    return BN_OK;
+}
+
+bn_status bn_set_state_device(bn_solver* s, const double* f_dev, size_t count) {
+    if (!valid_solver(s) || !f_dev) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    cudaError_t e = cudaMemcpyAsync(s->f, f_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state_device");
+    s->has_state = true;
+    s->t = 0;
+    return BN_OK;
+}
+
+bn_status bn_get_state(bn_solver* s, double* f, size_t count) {
+    if (!valid_solver(s) || !f) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    cudaError_t e = cudaMemcpyAsync(f, s->f, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state");
+    return BN_OK;
+}
+
+bn_status bn_get_state_device(bn_solver* s, double* f_dev, size_t count) {
+    if (!valid_solver(s) || !f_dev) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    cudaError_t e = cudaMemcpyAsync(f_dev, s->f, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state_device");
+    return BN_OK;
+}
+
+bn_status bn_eval_collision_device(bn_solver* s, const double* f_dev, double* Q_dev, size_t count) {
+    if (!valid_solver(s) || !f_dev || !Q_dev) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    s->prof_slot = 0;
+    eval_device(s, f_dev, Q_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "eval_collision launch");
+    return BN_OK;
+}
+
+bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count) {
+    if (!valid_solver(s) || !Q) return fail(BN_ERR_ARG, "null argument");
+    if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    s->prof_slot = 0;
+    eval_device(s, s->f, s->Qv);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Q, s->Qv, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "eval_collision");
+    harvest_profile(s, s->prof_slot);
+    return BN_OK;
+}
+
+bn_status bn_step_rk(bn_solver* s, double dt, int nsteps) {
+    if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(BN_ERR_ARG, "dt must be > 0 and nsteps >= 0");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    if (nsteps == 0) return BN_OK;
+    bn_status st = ensure_graph(s, dt);
+    if (st != BN_OK) return st;
+    cudaError_t e = cudaMemsetAsync(s->flags, 0, 2 * sizeof(int), s->stream);
+    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
+        e = cudaGraphLaunch(s->step_graph, s->stream);
+        s->launches += s->graph_launches;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_rk");
+    harvest_profile(s, s->prof_slots_used);
+    const int committed = s->flags_host[1];
+    s->t += committed * dt;
+    if (s->flags_host[0] != 0) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "state became non-finite at step %d of %d; state kept at t = %.17g", committed + 1,
+                      nsteps, s->t);
+        return fail(BN_ERR_NONFINITE, buf);
+    }
+    return BN_OK;
+}
+
+bn_status bn_moments(bn_solver* s, double* out, size_t count) {
+    if (!valid_solver(s) || !out) return fail(BN_ERR_ARG, "null argument");
+    if (count < (size_t)(s->g.d + 6)) return fail(BN_ERR_ARG, "count must be >= d + 6");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    bn::launch_moments(s, s->f, s->moments);
+    double h[16];
+    cudaError_t e = cudaMemcpyAsync(h, s->moments, (s->g.d + 5) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments");
+    for (int i = 0; i < s->g.d + 5; ++i) out[i] = h[i];
+    out[s->g.d + 5] = s->t;
+    return BN_OK;
+}
+
+bn_status bn_work_counts(const bn_solver* s, double* out, size_t count) {
+    if (!valid_solver(s) || !out) return fail(BN_ERR_ARG, "null argument");
+    if (count < 4) return fail(BN_ERR_ARG, "count must be >= 4");
+    out[0] = bn::count_pair_terms(s->g.d, s->g.N);
+    out[1] = s->eps != 0.0 ? bn::count_reducible_terms(s->g.d, s->g.N) : 0.0;
+    out[2] = s->eps != 0.0 ? bn::count_triple_terms(s->g.d, s->g.N) : 0.0;
+    out[3] = s->g.nModes;
+    return BN_OK;
+}
+
+long long bn_kernel_launches(const bn_solver* s) { return s ? s->launches : 0; }
+
+bn_status bn_profile_enable(bn_solver* s, int enable) {
+    if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
+    const bool on = enable != 0;
+    if (on && !s->prof_ev[0]) {
+        for (cudaEvent_t& ev : s->prof_ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        }
+    }
+    if (on != s->prof && s->step_graph) {
+        cudaStreamSynchronize(s->stream);
+        cudaGraphExecDestroy(s->step_graph);
+        s->step_graph = nullptr;
+    }
+    s->prof = on;
+    s->prof_ms = 0;
+    s->prof_count = 0;
+    return BN_OK;
+}
+
+bn_status bn_profile_read(bn_solver* s, double* out, size_t count) {
+    if (!valid_solver(s) || !out) return fail(BN_ERR_ARG, "null argument");
+    if (count < 2) return fail(BN_ERR_ARG, "count must be >= 2");
+    out[0] = s->prof_ms;
+    out[1] = (double)s->prof_count;
+    s->prof_ms = 0;
+    s->prof_count = 0;
+    return BN_OK;
+}
+
+bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int nsteps, int* failed) {
+    if (failed) *failed = -1;
+    if (!solvers || n <= 0 || !dts || nsteps < 0) return fail(BN_ERR_ARG, "invalid batch arguments");
+    for (int i = 0; i < n; ++i) {
+        if (!solvers[i]) return fail(BN_ERR_ARG, "null solver in batch");
+        if (!solvers[i]->has_state) return fail(BN_ERR_STATE, "solver in batch has no state");
+        bn_status st = ensure_graph(solvers[i], dts[i]);
+        if (st != BN_OK) return st;
+    }
+    cudaStream_t st0 = solvers[0]->stream;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        if (solvers[i]->stream != st0) {
+            // order this solver's stream before the shared stream
+            cudaEvent_t ev;
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            cudaEventRecord(ev, solvers[i]->stream);
+            cudaStreamWaitEvent(st0, ev, 0);
+            cudaEventDestroy(ev);
+        }
+        e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
+    }
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            e = cudaGraphLaunch(solvers[i]->step_graph, st0);
+            solvers[i]->launches += solvers[i]->graph_launches;
+        }
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
+    if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
+    bn_status result = BN_OK;
+    for (int i = 0; i < n; ++i) {
+        bn_solver* s = solvers[i];
+        harvest_profile(s, s->prof_slots_used);
+        s->t += s->flags_host[1] * dts[i];
+        if (s->flags_host[0] != 0 && result == BN_OK) {
+            if (failed) *failed = i;
+            result = fail(BN_ERR_NONFINITE, "a solver in the batch became non-finite");
+        }
+    }
+    return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// bn_internal.cuh -- declarations shared by the translation units of libbn.
+// Fourier-Galerkin Boltzmann-Nordheim operator (Mouton & Rey, arXiv:2110.13735).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bn.h"
+
+namespace bn {
+
+// ---------------------------------------------------------------- complex helpers
+template <typename R> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <typename R> using cplx = typename cplx_t<R>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im) {
+    C c; c.x = re; c.y = im; return c;
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ---------------------------------------------------------------- index geometry
+// Modes k in I_N = [-N/2, N/2-1]^d are stored row-major at k_i + N/2 (last fastest).
+// Kernel-mode arguments a in the extended box [-N, N-1]^d are stored at a_i + N.
+struct Geometry {
+    int d = 2;
+    int N = 16;
+    int nModes = 0;   // N^d
+    int E = 0;        // 2N
+    int nExt = 0;     // (2N)^d
+};
+
+// ---------------------------------------------------------------- shared tables
+// Kernel modes beta(a,b) for one (d, N, R_xi, kernel, quadrature).
+struct KernelTables {
+    std::string key;
+    int refcount = 0;
+    Geometry g;
+    int P = 0;                    // quadrature terms
+    double* alpha64 = nullptr;    // [P][nExt]  (weights folded in)
+    double* alphap64 = nullptr;   // [P][nExt]
+    double* beta64 = nullptr;     // [nExt(b)][nExt(a)] = beta(a, b)  (b-major)
+    float* beta32 = nullptr;      // same, rounded to FP32
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------- triple-sum work list
+struct WorkList {
+    int* items = nullptr;   // flat extended index of b, sorted by descending work
+    int count = 0;
+    double terms = 0;       // sum over items of |box_n| |box_s|
+};
+
+}  // namespace bn
+
+// ---------------------------------------------------------------- solver object
+struct bn_solver {
+    bn::Geometry g;
+    double T = 0, R = 0, Rxi = 0, eps = 0;
+    int kernel = 0;
+    bn_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    double scale = 1.0;          // (T/pi)^{d+gamma}
+    bn::KernelTables* tabs = nullptr;
+    bn::WorkList work;
+    int n_partials = 0;          // CTAs of the triple-sum kernel (rows of the partial buffer)
+
+    // device buffers
+    double* f = nullptr;         // state, N^d
+    double* f_prev = nullptr;    // last finite state
+    double* y = nullptr;         // RK stage argument
+    double* kacc = nullptr;      // RK accumulator
+    double* Qv = nullptr;        // Q in velocity units (stage derivative)
+    double2* Ghat = nullptr;     // modes of the stage argument (FP64)
+    float2* Ghat32 = nullptr;    // same in FP32 (mixed precision)
+    double2* work_c = nullptr;   // transform scratch, N^d
+    double2* S2 = nullptr;       // reducible pair sums S(t), t in ext box
+    double2* quad = nullptr;     // quadratic modes, N^d
+    double2* red = nullptr;      // reducible cubic modes, N^d
+    double2* q1q = nullptr;      // Q_{1,q} modes, N^d
+    double2* partials = nullptr; // [n_partials][N^d]
+    double2* Qhat = nullptr;     // combined modes
+    double* moments = nullptr;   // d+6
+    int* flags = nullptr;        // [0]: non-finite, [1]: committed steps
+    int* flags_host = nullptr;   // pinned
+
+    bool has_state = false;
+    double t = 0;
+    long long launches = 0;
+
+    // captured step graphs
+    cudaGraphExec_t step_graph = nullptr;
+    double graph_dt = 0;
+    long long graph_launches = 0;  // kernels in one captured step
+
+    // live timing of the triple-sum kernel
+    bool prof = false;
+    cudaEvent_t prof_ev[16] = {};   // pairs (start, stop) per evaluation slot
+    int prof_slot = 0;              // next slot while recording
+    int prof_slots_used = 0;        // slots recorded by the current graph / last eval
+    double prof_ms = 0;
+    long long prof_count = 0;
+};
+
+namespace bn {
+
+// tables (bn_tables.cu)
+bn_status acquire_tables(bn_solver* s, std::string* err);
+void release_tables(KernelTables* t);
+bn_status build_work_list(bn_solver* s, std::string* err);
+double count_triple_terms(int d, int N);
+double count_pair_terms(int d, int N);
+double count_reducible_terms(int d, int N);
+
+// transforms and stage kernels (bn_transform.cu)
+void launch_dft_forward(bn_solver* s, const double* f, double2* out);
+void launch_dft_inverse_real(bn_solver* s, const double2* in, double* out, double scale);
+void launch_to_fp32(bn_solver* s, const double2* in, float2* out, int n);
+void launch_rk_stage(bn_solver* s, const double* f, const double* K, double* acc, double* y, double w_acc,
+                     double c_next, double dt, int first);
+void launch_rk_final(bn_solver* s, double* f, const double* acc, const double* K, double w_last, double dt,
+                     double* f_prev, int* flags);
+void launch_heun_final(bn_solver* s, double* f, const double* y, const double* K, double dt, double* f_prev,
+                       int* flags);
+void launch_moments(bn_solver* s, const double* f, double* out);
+void launch_conserve(bn_solver* s, double* Q);
+
+// sums (bn_sums.cu)
+void launch_pair_sums(bn_solver* s);        // S2, quad, red from Ghat
+void launch_triple_sum(bn_solver* s);       // q1q from Ghat
+void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
+int triple_partials(const bn_solver* s);
+
+}  // namespace bn
+
+#define BN_CUDA_LAUNCH_CHECK() ((void)0)

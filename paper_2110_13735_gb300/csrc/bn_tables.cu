@@ -1,0 +1,258 @@
+// bn_tables.cu -- kernel-mode tables beta(a,b) (Mouton & Rey, Sec. 2.5, eq. betadD)
+// built once per (d, N, R_xi, kernel, quadrature) in FP64 on the device and shared
+// (refcounted) by every solver that uses the same operator; and the work list of the
+// Q_{1,q} triple sum.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+namespace {
+
+std::mutex g_tables_mutex;
+std::map<std::string, KernelTables*> g_tables;
+
+// Sinc(x) = sin(x)/x: phi_R(s) = int_{-R}^{R} e^{i rho s} d rho = 2R Sinc(Rs) (Sec. 2.5).
+__device__ __forceinline__ double sinc_d(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
+
+// 3-D radial transform for b == 1: int_{-R}^{R} |rho| e^{i rho s} d rho = 2R sin(Rs)/s - 2(1-cos Rs)/s^2.
+__device__ __forceinline__ double phi3_d(double R, double s) {
+    double x = R * s;
+    if (fabs(x) < 1e-4) {   // series: R^2 (1 - x^2/4 + x^4/72)
+        double x2 = x * x;
+        return R * R * (1.0 - x2 * 0.25 + x2 * x2 / 72.0);
+    }
+    double h = sin(0.5 * x) / (0.5 * x);
+    return R * R * (2.0 * sin(x) / x - h * h);
+}
+
+// psi(q) = int_0^pi phi3(q cos t) dt over the half great circle = 2 pi R J1(Rq)/q, psi(0) = pi R^2.
+__device__ __forceinline__ double psi3_d(double R, double q) {
+    double x = R * q;
+    if (fabs(x) < 1e-6) return M_PI * R * R * (1.0 - x * x * 0.125);
+    return 2.0 * M_PI * R * j1(x) / q;
+}
+
+// Quadrature node: direction e (2-D: e_theta, e2 unused) and weight (2-D: pi/M).
+struct Node { double e0, e1, e2, w; };
+
+__global__ void k_alpha_tables(int d, int N, int P, double Rxi, double c_phi, const Node* __restrict__ nodes,
+                               double* __restrict__ alpha, double* __restrict__ alphap) {
+    const int E = 2 * N;
+    const int nExt = d == 2 ? E * E : E * E * E;
+    const long long total = (long long)P * nExt;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(idx / nExt), ia = (int)(idx % nExt);
+        const Node nd = nodes[p];
+        if (d == 2) {
+            const double a0 = ia / E - N, a1 = ia % E - N;
+            // alpha_p(k) = 2 C_Phi phi(k.e_p), alpha'_p(l) = phi(l.e_{p+pi/2}); C = pi/M folded into alpha.
+            const double ke = a0 * nd.e0 + a1 * nd.e1;
+            const double le = -a0 * nd.e1 + a1 * nd.e0;   // e_{theta+pi/2} = (-sin, cos)
+            alpha[idx] = nd.w * 2.0 * c_phi * 2.0 * Rxi * sinc_d(Rxi * ke);
+            alphap[idx] = 2.0 * Rxi * sinc_d(Rxi * le);
+        } else {
+            const double a0 = ia / (E * E) - N, a1 = (ia / E) % E - N, a2 = ia % E - N;
+            // alpha(k) = w 4 C_Phi phi3(k.e), alpha'(l) = psi(|Pi_{e^perp} l|).
+            const double ke = a0 * nd.e0 + a1 * nd.e1 + a2 * nd.e2;
+            const double n2 = a0 * a0 + a1 * a1 + a2 * a2 - ke * ke;
+            alpha[idx] = nd.w * 4.0 * c_phi * phi3_d(Rxi, ke);
+            alphap[idx] = psi3_d(Rxi, sqrt(fmax(n2, 0.0)));
+        }
+    }
+}
+
+// beta[ib][ia] = sum_p alpha_p(a) alpha'_p(b) (eq. betadD), FP64, plus an FP32 copy.
+__global__ void k_beta_table(int nExt, int P, const double* __restrict__ alpha, const double* __restrict__ alphap,
+                             double* __restrict__ beta64, float* __restrict__ beta32) {
+    const long long total = (long long)nExt * nExt;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int ib = (int)(idx / nExt), ia = (int)(idx % nExt);
+        double s = 0.0;
+        for (int p = 0; p < P; ++p) s = fma(alpha[(size_t)p * nExt + ia], alphap[(size_t)p * nExt + ib], s);
+        beta64[idx] = s;
+        beta32[idx] = (float)s;
+    }
+}
+
+// Gauss-Legendre rule on [-1, 1]: Newton iteration on P_n from Tricomi's initial guesses.
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm1 = 1.0, pk = z;   // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                double pn = ((2.0 * k - 1.0) * z * pk - (k - 1.0) * pm1) / k;
+                pm1 = pk;
+                pk = pn;
+            }
+            if (n == 1) { pk = z; pm1 = 1.0; }
+            dp = n * (pm1 - z * pk) / (1.0 - z * z);
+            double step = pk / dp;
+            z -= step;
+            if (std::fabs(step) < 4e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+std::string table_key(const bn_solver* s) {
+    std::ostringstream os;
+    os.precision(17);
+    os << s->device << ":" << s->g.d << ":" << s->g.N << ":" << s->Rxi << ":" << s->kernel << ":";
+    if (s->g.d == 2) os << s->opt.M;
+    else os << s->opt.M1 << "x" << s->opt.M2 << ":" << s->opt.quad3d;
+    os << ":" << s->opt.c_phi;
+    return os.str();
+}
+
+}  // namespace
+
+bn_status acquire_tables(bn_solver* s, std::string* err) {
+    std::lock_guard<std::mutex> lock(g_tables_mutex);
+    const std::string key = table_key(s);
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) {
+        it->second->refcount++;
+        s->tabs = it->second;
+        return BN_OK;
+    }
+    KernelTables* t = new KernelTables();
+    t->key = key;
+    t->g = s->g;
+    const int d = s->g.d, nExt = s->g.nExt;
+    std::vector<Node> nodes;
+    if (d == 2) {
+        const int M = s->opt.M;
+        for (int p = 0; p < M; ++p) {
+            double th = p * M_PI / M;
+            nodes.push_back(Node{std::cos(th), std::sin(th), 0.0, M_PI / M});
+        }
+    } else {
+        const int M1 = s->opt.M1, M2 = s->opt.M2;
+        std::vector<double> mu, wt;
+        if (s->opt.quad3d == 0) {
+            gauss_legendre_rule(M1, mu, wt);
+        } else {
+            mu.resize(M1);
+            wt.resize(M1);
+            for (int i = 0; i < M1; ++i) {
+                mu[i] = std::cos(i * M_PI / M1);
+                wt[i] = (M_PI / M1) * std::sin(i * M_PI / M1);
+            }
+        }
+        for (int i = 0; i < M1; ++i)
+            for (int q = 0; q < M2; ++q) {
+                double st = std::sqrt(std::max(0.0, 1.0 - mu[i] * mu[i])), ph = q * M_PI / M2;
+                nodes.push_back(Node{st * std::cos(ph), st * std::sin(ph), mu[i], wt[i] * (M_PI / M2)});
+            }
+    }
+    t->P = (int)nodes.size();
+    const size_t nAl = (size_t)t->P * nExt, nBeta = (size_t)nExt * nExt;
+    Node* d_nodes = nullptr;
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&d_nodes, sizeof(Node) * nodes.size());
+    if (e == cudaSuccess) e = cudaMalloc(&t->alpha64, sizeof(double) * nAl);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphap64, sizeof(double) * nAl);
+    if (e == cudaSuccess) e = cudaMalloc(&t->beta64, sizeof(double) * nBeta);
+    if (e == cudaSuccess) e = cudaMalloc(&t->beta32, sizeof(float) * nBeta);
+    if (e != cudaSuccess) {
+        *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
+        cudaFree(d_nodes);
+        cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
+        delete t;
+        cudaGetLastError();
+        return BN_ERR_NOMEM;
+    }
+    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * nBeta;
+    cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
+    k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, d_nodes, t->alpha64,
+                                               t->alphap64);
+    k_beta_table<<<4096, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
+    s->launches += 2;
+    e = cudaStreamSynchronize(s->stream);
+    cudaFree(d_nodes);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
+        cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
+        delete t;
+        return BN_ERR_CUDA;
+    }
+    t->refcount = 1;
+    g_tables[key] = t;
+    s->tabs = t;
+    return BN_OK;
+}
+
+void release_tables(KernelTables* t) {
+    if (!t) return;
+    std::lock_guard<std::mutex> lock(g_tables_mutex);
+    if (--t->refcount > 0) return;
+    g_tables.erase(t->key);
+    cudaFree(t->alpha64);
+    cudaFree(t->alphap64);
+    cudaFree(t->beta64);
+    cudaFree(t->beta32);
+    delete t;
+}
+
+// Per dimension, for b in [-N+1, N-2]: the outputs n with n, n-b in I_N number N-|b|
+// and the inner indices s with s, b-s in I_N number N-|b+1|.
+static inline long long box_n(int N, int b) { return N - std::abs(b); }
+static inline long long box_s(int N, int b) { return N - std::abs(b + 1); }
+
+double count_triple_terms(int d, int N) {
+    double c = 2.0 * ((double)N * N * N - N) / 3.0;   // sum_b (N-|b|)(N-|b+1|)
+    return std::pow(c, d);
+}
+double count_pair_terms(int d, int N) { return std::pow(0.75 * N * N, d); }
+double count_reducible_terms(int d, int N) {
+    return std::pow((double)N * N, d) + std::pow((double)N * N - 1.0, d);
+}
+
+bn_status build_work_list(bn_solver* s, std::string* err) {
+    const int d = s->g.d, N = s->g.N, E = s->g.E;
+    std::vector<std::pair<long long, int>> items;
+    const int nb = d == 2 ? E * E : E * E * E;
+    double total = 0;
+    for (int ib = 0; ib < nb; ++ib) {
+        int b[3];
+        int r = ib;
+        for (int i = d - 1; i >= 0; --i) { b[i] = r % E - N; r /= E; }
+        long long w = 1;
+        for (int i = 0; i < d; ++i) {
+            long long ln = box_n(N, b[i]), ls = box_s(N, b[i]);
+            if (ln <= 0 || ls <= 0) { w = 0; break; }
+            w *= ln * ls;
+        }
+        if (w > 0) { items.push_back({w, ib}); total += (double)w; }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
+    std::vector<int> flat(items.size());
+    for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].second;
+    if (cudaMalloc(&s->work.items, sizeof(int) * flat.size()) != cudaSuccess) {
+        cudaGetLastError();
+        *err = "work list allocation failed";
+        return BN_ERR_NOMEM;
+    }
+    cudaMemcpy(s->work.items, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice);
+    s->work.count = (int)flat.size();
+    s->work.terms = total;
+    return BN_OK;
+}
+
+}  // namespace bn

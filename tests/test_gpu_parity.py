@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Tolerance (FP64 mode): e_Q = ||Q_gpu - Q_oracle||_2 / ||Q^{1c}_oracle||_2 <= 1e-12 (normalised by the
+classical gain term, which does not vanish near equilibrium); states: ||f_gpu - f_oracle||_2 /
+||f_oracle||_2 <= 1e-12.  Mixed precision (FP32 sums, FP64 elsewhere): e_Q <= 2e-6 (measured and
+reported per case)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_13735_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+R6 = 6.0
+T6 = I.box_half_width(R6)
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_13735_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2110_13735_gb300 import bn
+    bn.load()
+    return bn
+
+
+def rel(a, b, ref):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def _f0(d, N, kind, seed=0):
+    T = T6
+    if kind == "two":
+        return I.two_gaussians(d, N, T, 1.0, (2.0, 1.0) if d == 2 else (1.5, 0.0, 0.0), 0.8)
+    if kind == "gauss":
+        return I.gaussian(d, N, T, 5.0 if d == 2 else 8.0, 0.5 if d == 2 else 0.6)
+    rng = np.random.Generator(np.random.PCG64(I.SEED + seed))
+    return I.two_gaussians(d, N, T, 1.2, (1.0, -0.5, 0.3)[:d], 0.6) * (1.0 + 0.2 * rng.uniform(size=(N,) * d))
+
+
+CASES_2D = [(4, -1.0, "rand"), (8, 1.0, "rand"), (16, -1.0, "two"), (16, 0.0, "two"), (16, 1.0, "gauss"),
+            (16, 2.5, "rand"), (24, -1.0, "rand"), (32, 1.0, "gauss")]
+
+
+@pytest.mark.parametrize("N,eps,kind", CASES_2D)
+def test_eval_parity_2d_fp64(B, N, eps, kind):
+    f = _f0(2, N, kind)
+    ora = O.Operator(2, N, T6, R6, 0, eps, M=2 * N)
+    Q_o, gain, _, _ = ora.eval_collision(f, parts=True)
+    with B.Solver(2, N, T6, R6, B.MAXWELL, eps) as s:
+        s.set_state(f)
+        Q_g = s.eval_collision()
+    assert rel(Q_g, Q_o, gain) <= 1e-12
+
+
+@pytest.mark.parametrize("N,eps", [(4, 1.0), (6, -1.0), (8, 1.0), (8, -2.0)])
+def test_eval_parity_3d_fp64(B, N, eps):
+    f = _f0(3, N, "rand", seed=N)
+    ora = O.Operator(3, N, T6, R6, 1, eps, M1=6, M2=6)
+    Q_o, gain, _, _ = ora.eval_collision(f, parts=True)
+    with B.Solver(3, N, T6, R6, B.HARD_SPHERE, eps, M1=6, M2=6) as s:
+        s.set_state(f)
+        Q_g = s.eval_collision()
+    assert rel(Q_g, Q_o, gain) <= 1e-12
+
+
+@pytest.mark.parametrize("N,eps,kind", [(16, -1.0, "two"), (32, 1.0, "gauss")])
+def test_eval_mixed_precision_error(B, N, eps, kind):
+    f = _f0(2, N, kind)
+    ora = O.Operator(2, N, T6, R6, 0, eps, M=2 * N)
+    Q_o, gain, _, _ = ora.eval_collision(f, parts=True)
+    with B.Solver(2, N, T6, R6, B.MAXWELL, eps, precision=B.MIXED) as s:
+        s.set_state(f)
+        Q_g = s.eval_collision()
+    err = rel(Q_g, Q_o, gain)
+    print(f"mixed precision e_Q (2-D N={N}, eps={eps}) = {err:.3e}")
+    assert err <= 2e-6
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_step_parity_fp64(B, integrator):
+    N, eps, dt, n = 16, -1.0, 0.01, 5
+    f = _f0(2, N, "two")
+    ora = O.Operator(2, N, T6, R6, 0, eps, M=2 * N)
+    f_o = ora.step(f, dt, n, integrator)
+    with B.Solver(2, N, T6, R6, B.MAXWELL, eps, integrator=integrator) as s:
+        s.set_state(f)
+        s.step_rk(dt, n)
+        f_g = s.get_state()
+        m = s.moments()
+    assert rel(f_g, f_o, f_o) <= 1e-12
+    m_o = ora.moments(f_o)
+    assert np.allclose(m[:-1], m_o, rtol=1e-12, atol=1e-14)
+    assert m[-1] == pytest.approx(n * dt, rel=1e-14)
+
+
+def test_bkw_on_gpu(B):
+    """Classical BKW datum: GPU Q equals d/dt f_BKW within the spectral error at N=32 (as the oracle)."""
+    N = 32
+    v = I.grid(2, N, T6)
+    with B.Solver(2, N, T6, R6, B.MAXWELL, 0.0, M=N) as s:
+        s.set_state(I.bkw_2d(1.0, v))
+        Q = s.eval_collision()
+    ref = I.bkw_2d_dt(1.0, v)
+    assert np.abs(Q - ref).max() / np.abs(ref).max() < 5e-2
+
+
+def test_determinism(B):
+    f = _f0(2, 16, "rand")
+    outs = []
+    for _ in range(2):
+        with B.Solver(2, 16, T6, R6, B.MAXWELL, 1.0) as s:
+            s.set_state(f)
+            outs.append(s.eval_collision())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_mass_conserved_on_gpu(B):
+    f = _f0(2, 16, "rand")
+    with B.Solver(2, 16, T6, R6, B.MAXWELL, -1.0) as s:
+        s.set_state(f)
+        Q = s.eval_collision()
+    assert abs(Q.sum()) <= 1e-13 * np.abs(Q).sum() * 10
+
+
+def test_state_errors(B):
+    with B.Solver(2, 8, T6, R6, B.MAXWELL, 1.0) as s:
+        with pytest.raises(B.BNError) as ei:
+            s.eval_collision()
+        assert ei.value.status == -7
+        with pytest.raises(B.BNError):
+            s.set_state(np.zeros(10))
+
+
+def test_nonfinite_rollback(B):
+    """A state that overflows stops step_rk with BN_ERR_NONFINITE and keeps the last finite state."""
+    N = 8
+    f = _f0(2, N, "rand")
+    with B.Solver(2, N, T6, R6, B.MAXWELL, 1.0) as s:
+        s.set_state(f * 1e100)
+        with pytest.raises(B.BNError) as ei:
+            s.step_rk(0.5, 20)
+        assert ei.value.status == -5
+        g = s.get_state()
+        assert np.all(np.isfinite(g))
+        t = s.moments()[-1]
+        assert t < 20 * 0.5
+
+
+def test_conservation_projection(B):
+    N = 16
+    f = _f0(2, N, "two")
+    with B.Solver(2, N, T6, R6, B.MAXWELL, -1.0, conserve=1) as s:
+        s.set_state(f)
+        Q = s.eval_collision()
+    v = I.grid(2, N, T6)
+    scale = np.abs(Q).sum() * (1 + np.abs(v).max() ** 2)
+    assert abs(Q.sum()) < 1e-13 * scale
+    assert np.abs(np.tensordot(Q, v, axes=([0, 1], [0, 1]))).max() < 1e-13 * scale
+    assert abs(np.sum(Q * np.sum(v * v, -1))) < 1e-13 * scale
