@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Fourier-Galerkin Boltzmann-Nordheim operator.
+
+Workload (one "step" = one classical RK4 step of the whole hot path for every request
+on the GPU): the 2-D classical + bosonic pair on Maxwell molecules, N = 32 modes per
+dimension, R = 6, T = (3 + sqrt 2) R / 2, dt = 0.005 --
+  * eps = 0 on the BKW datum at t0 = 1,
+  * eps = +1 on a Gaussian of mass 5 and temperature 0.5,
+in mixed precision (FP32 bulk sums with FP64 tables, transforms, accumulation of Q^,
+moments and state); the same pair in FP64 is timed beside it.
+
+Metric: Lemma terms per second ("mode-pairs/s"): each evaluation of Q_eps counts the
+quadratic terms of the Lemma (pairs k+l = n in I_N) plus, when eps != 0, its cubic terms
+(triples k+l+m = n), i.e. C2 = (3N^2/4)^d and C3 = (2(N^3-N)/3)^d; four evaluations per
+RK4 step.  Multi-GPU runs are replicas (every rank steps its own pair; no collective on the
+data path; weak scaling).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this project) on a bounded
+sample of the same workload and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Q_ε mode-pairs/s & solves/s, mixed vs FP64 same GB300; p50/p99 solve latency"
+UNIT = "mode-pairs/s"
+N_MODES, R_TRUNC, DT = 32, 6.0, 0.005
+T_END = {"bkw": 5.0 - 1.0, "boson": 5.0}   # integration spans of the two solves
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def lemma_terms(d: int, N: int, cubic: bool) -> float:
+    c2 = (0.75 * N * N) ** d
+    c3 = (2.0 * (N ** 3 - N) / 3.0) ** d
+    return c2 + (c3 if cubic else 0.0)
+
+
+def lemma_terms_box(N: int, lo: int, cnt: int, cubic: bool) -> float:
+    """Lemma terms of the outputs n in the box [lo, lo+cnt)^2 (per-dimension counts multiply)."""
+    I = np.arange(-N // 2, N // 2)
+    q1 = np.array([np.sum((n - I >= -N // 2) & (n - I < N // 2)) for n in range(lo, lo + cnt)], float)
+    kl = (I[:, None] + I[None, :]).ravel()
+    c1 = np.array([np.sum((n - kl >= -N // 2) & (n - kl < N // 2)) for n in range(lo, lo + cnt)], float)
+    return float(q1.sum() ** 2 + (c1.sum() ** 2 if cubic else 0.0))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def clocks_sampler_start(path: str):
+    q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        fh = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"],
+                             stdout=fh, stderr=subprocess.DEVNULL)
+        time.sleep(0.5)   # let the sampler come up before the timed region
+        return p, fh
+    except Exception:
+        return None, None
+
+
+def clocks_sampler_stop(p, fh, path: str, gpu: int, window):
+    """Median SM clock and throttle reasons from the samples taken inside `window`
+    (wall-clock seconds since the epoch); falls back to every sample of the run."""
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    fh.close()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10 or not parts[1].isdigit() or int(parts[1]) != gpu:
+            continue
+        try:
+            ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+            frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+            rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[6:10]))
+        except (ValueError, IndexError):
+            continue
+    if not rows:
+        return None
+    inside = [r for r in rows if window[0] - 0.05 <= r[0] <= window[1] + 0.05]
+    used = inside if inside else rows
+    reasons = sorted({n for r in used for n, flag in zip(names, r[3]) if flag.lower() == "active"})
+    return {"sm_mhz": float(np.median([r[1] for r in used])), "sm_max_mhz": float(max(r[2] for r in used)),
+            "reasons": reasons, "samples": len(used), "window": "timed region" if inside else "whole run"}
+
+
+def source_sha(path: str) -> str:
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the
+    kernel source is unchanged since it was captured; else None."""
+    src = os.path.join(ROOT, "paper_2110_13735_gb300", "csrc", "bn_fused2d.cu")
+    rec = os.path.join(ROOT, "profiles", "fused2d_traffic.json")
+    if not os.path.exists(rec):
+        return None
+    try:
+        data = json.load(open(rec))
+        if data.get("kernel_sha") == source_sha(src):
+            return float(data["dram_bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
+def make_pair(bn, I, precision, stream):
+    T = I.box_half_width(R_TRUNC)
+    bkw = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 0.0, stream=stream, precision=precision)
+    bos = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 1.0, stream=stream, precision=precision)
+    f_bkw = I.config1_bkw_f0(N_MODES, R_TRUNC)
+    f_bos = I.config1_boson_f0(N_MODES, R_TRUNC)
+    bkw.set_state(f_bkw)
+    bos.set_state(f_bos)
+    return [bkw, bos], [f_bkw, f_bos]
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2110_13735_gb300 import build as BUILD
+    if rank == 0 or ws == 1:
+        BUILD.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_2110_13735_gb300 import bn
+    from paper_2110_13735_gb300 import inputs as I
+    bn.load()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    terms_step = 4.0 * (lemma_terms(2, N_MODES, False) + lemma_terms(2, N_MODES, True))
+
+    def timed(solvers, steps, warmup, profile=False):
+        dts = [DT] * len(solvers)
+        for _ in range(warmup):
+            bn.step_rk_batch(solvers, dts, 1)
+        if profile:
+            for s in solvers:
+                s.profile_enable(True)
+            bn.step_rk_batch(solvers, dts, 1)   # recapture the graphs with timing events
+            for s in solvers:
+                s.profile_read()
+        launches0 = sum(s.kernel_launches() for s in solvers)
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        evs = []
+        t_wall0 = time.time()
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bn.step_rk_batch(solvers, dts, 1)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        t_wall1 = time.time()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        launches = sum(s.kernel_launches() for s in solvers) - launches0
+        prof = None
+        if profile:
+            prof = []
+            for s in solvers:
+                prof.append(s.profile_read())
+                s.profile_enable(False)
+        return ms, launches, prof, (t_wall0, t_wall1)
+
+    # ---- mixed precision (the headline)
+    solvers, f0 = make_pair(bn, I, bn.MIXED, stream)
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f".clocks_rank{rank}.csv")
+    p, fh = clocks_sampler_start(clk_path)
+    ms, launches, prof, window = timed(solvers, args.steps, args.warmup, profile=True)
+    clocks = clocks_sampler_stop(p, fh, clk_path, local, window)
+    prof_boson = prof[1] if prof else None
+    total_ms = float(np.sum(ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * terms_step * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    h_in = [np.ascontiguousarray(f.reshape(-1)) for f in f0]
+    h_out = [np.empty_like(h) for h in h_in]
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s, h in zip(solvers, h_in):
+            s.set_state(h)
+        bn.step_rk_batch(solvers, [DT] * 2, 1)
+        for s, o in zip(solvers, h_out):
+            o[:] = s.get_state().reshape(-1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * terms_step * e2e_steps / e2e_s
+    bytes_io = sum(h.nbytes for h in h_in)
+
+    # ---- dominant kernel: live timing of the fused operator kernel inside the timed steps.
+    # Only the eps=+1 request runs the Q_{1,q} triple sum; the eps=0 request's launches are the
+    # quadratic part, so the timing below uses the bosonic solver's launches only (index 1).
+    flops_launch = 4.0 * (2.0 * (N_MODES ** 3 - N_MODES) / 3.0) ** 2   # 2 FFMA per Q_{1,q} term
+    peak = SM_COUNT * FP32_LANES * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
+    kern_ms, basis = None, None
+    if prof_boson and prof_boson[1] > 0 and prof_boson[0] > 0:
+        kern_ms, basis = prof_boson[0] / prof_boson[1], "CUDA events recorded around each launch inside the step graph"
+    elif prof_boson and prof_boson[3] > 0 and prof_boson[2] > 0:
+        kern_ms, basis = prof_boson[2] / prof_boson[3], "kernel %globaltimer span (first CTA start to last CTA end)"
+    achieved = flops_launch / (kern_ms * 1e-3) / 1e12 if kern_ms else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": recorded_traffic(), "kernel": "k_fused2d<float,8,128> (whole 2-D operator, eps=+1 request)",
+                "launches_timed": (prof_boson[1] or prof_boson[3]) if prof_boson else 0, "ms_per_launch": kern_ms,
+                "timing": basis,
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts, max clock)"}
+    if clocks and achieved:
+        roofline["frac_at_median_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    for s in solvers:
+        s.close()
+
+    # ---- FP64 beside it (fewer steps)
+    solvers64, _ = make_pair(bn, I, bn.FP64, stream)
+    k64 = max(3, args.steps // 4)
+    ms64, _, _, _ = timed(solvers64, k64, min(args.warmup, 3))
+    for s in solvers64:
+        s.close()
+    ms64_step = float(np.mean(ms64))
+    fp64 = {"value": terms_step / (ms64_step * 1e-3) * ws, "unit": UNIT, "ms_per_step": ms64_step, "steps": k64}
+
+    steps_to_end = {k: int(round(v / DT)) for k, v in T_END.items()}
+    solves = {"pair_solve_s_mixed": ms_per_step * max(steps_to_end.values()) / 1e3,
+              "pair_solve_s_fp64": ms64_step * max(steps_to_end.values()) / 1e3}
+    solves["solves_per_s_mixed"] = ws * 2.0 / solves["pair_solve_s_mixed"]
+    solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2-D Maxwell molecules N=32 R=6 T=(3+sqrt2)R/2: BKW eps=0 (t0=1) + Gaussian "
+                                   "(mass 5, T 0.5) eps=+1, RK4 dt=0.005, mixed precision",
+                       "d": 2, "N": N_MODES, "requests_per_gpu": 2, "parallelism": f"replicas x{ws}",
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+                    "steps": e2e_steps},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+            "fp64": fp64,
+            "solves": solves,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(seconds: float):
+    """The oracle as it stands on this host: full Lemma evaluations of the two requests at
+    N=32, repeated until `seconds` of CPU time have passed."""
+    import oracle as O
+    from paper_2110_13735_gb300 import inputs as I
+    T = I.box_half_width(R_TRUNC)
+    ops = [(O.Operator(2, N_MODES, T, R_TRUNC, 0, 0.0), I.config1_bkw_f0(N_MODES, R_TRUNC), False),
+           (O.Operator(2, N_MODES, T, R_TRUNC, 0, 1.0), I.config1_boson_f0(N_MODES, R_TRUNC), True)]
+    for op, _, _ in ops:
+        op.beta()
+    terms, evals, t0 = 0.0, 0, time.perf_counter()
+    while True:
+        for op, f, cubic in ops:
+            op.eval_collision(f)
+            terms += lemma_terms(2, N_MODES, cubic)
+            evals += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": terms / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{evals} full FP64 evaluations of Q_eps (N=32 BKW eps=0 and Gaussian eps=+1), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2110_13735_gb300 import inputs as I
+    T = I.box_half_width(R_TRUNC)
+    op_b = O.Operator(2, N_MODES, T, R_TRUNC, 0, 1.0)
+    op_c = O.Operator(2, N_MODES, T, R_TRUNC, 0, 0.0)
+    g_b = op_b.dft(I.config1_boson_f0(N_MODES, R_TRUNC))
+    g_c = op_c.dft(I.config1_bkw_f0(N_MODES, R_TRUNC))
+    op_b.beta()
+    op_c.beta()
+    lo, cnt = -8, 16   # sample: the central 16x16 output modes of each request
+    terms_step = lemma_terms_box(N_MODES, lo, cnt, True) + lemma_terms_box(N_MODES, lo, cnt, False)
+
+    def step():
+        op_b.collision_modes(g_b, lo, cnt)
+        op_c.collision_modes(g_c, lo, cnt)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = terms_step * args.steps / el
+    sample = (f"per step: Lemma sums of the central 16x16 of 32x32 output modes for the Gaussian eps=+1 and "
+              f"BKW eps=0 requests (FP64 oracle, {O.num_threads()} threads)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2-D Maxwell molecules N=32 R=6: BKW eps=0 + Gaussian (mass 5, T 0.5) eps=+1, "
+                               "oracle sample", "d": 2, "N": N_MODES},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

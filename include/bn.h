@@ -138,8 +138,10 @@ long long bn_kernel_launches(const bn_solver* s);
  * Live timing of the dominant kernel (the Q_{1,q} triple sum): when enabled,
  * CUDA events are recorded on the solver's stream around every launch of that
  * kernel (also inside the captured step graph).  bn_profile_read returns
- * out[0] = summed duration in ms and out[1] = number of launches timed since
- * the last read, then resets both.  Within one bn_step_rk call only the last
+ * out[0] = summed event duration in ms and out[1] = number of launches timed
+ * since the last read; with count >= 4 also out[2] = summed kernel span in ms
+ * from the kernel's own %globaltimer stamps (first CTA start to last CTA end)
+ * and out[3] = launches stamped; then resets all.  Within one bn_step_rk call only the last
  * step's launches can be timed (earlier replays reuse the same events); call
  * it with nsteps = 1 to time every launch.  Enabling or disabling recaptures
  * the step graph.  count >= 2.

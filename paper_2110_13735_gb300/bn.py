@@ -189,10 +189,11 @@ class Solver:
         _check(_lib.bn_profile_enable(self._h, int(bool(on))))
 
     def profile_read(self):
-        """(summed ms, launches) of the triple-sum kernel since the last read."""
-        out = np.zeros(2)
-        _check(_lib.bn_profile_read(self._h, _dptr(out), 2))
-        return float(out[0]), int(out[1])
+        """Dominant-kernel timing since the last read:
+        (event ms total, event launches, device-stamp ms total, stamped launches)."""
+        out = np.zeros(4)
+        _check(_lib.bn_profile_read(self._h, _dptr(out), 4))
+        return float(out[0]), int(out[1]), float(out[2]), int(out[3])
 
 
 def step_rk_batch(solvers, dts, nsteps: int):

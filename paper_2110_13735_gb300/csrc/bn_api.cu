@@ -25,7 +25,7 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 
 void free_buffers(bn_solver* s) {
     void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->S2, s->quad,
-                    s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items};
+                    s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items, s->work_quad.items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
@@ -35,6 +35,19 @@ void free_buffers(bn_solver* s) {
 void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
     bn::launch_dft_forward(s, f_in, s->Ghat);
     if (s->opt.precision == BN_MIXED) bn::launch_to_fp32(s, s->Ghat, s->Ghat32, s->g.nModes);
+    if (s->g.d == 2) {
+        // the whole 2-D operator in one pass over b (quadratic + reducible + Q_{1,q})
+        const int slot = s->prof_slot;
+        if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
+        bn::launch_fused2d(s);
+        if (s->prof && slot < 8) {
+            cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
+            s->prof_slot = slot + 1;
+        }
+        bn::launch_dft_inverse_real(s, s->Qhat, Q_out, s->scale);
+        if (s->opt.conserve) bn::launch_conserve(s, Q_out);
+        return;
+    }
     bn::launch_pair_sums(s);
     if (s->eps != 0.0) {
         const int slot = s->prof_slot;
@@ -101,6 +114,18 @@ bool valid_solver(const bn_solver* s) { return s != nullptr; }
 // or direct evaluation (the stream has been synchronised).
 void harvest_profile(bn_solver* s, int slots) {
     if (!s->prof) return;
+    if (s->prof_stamps && slots > 0) {
+        unsigned long long st[16];
+        if (cudaMemcpy(st, s->prof_stamps, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            for (int i = 0; i < slots && i < 8; ++i)
+                if (st[2 * i + 1] > st[2 * i] && st[2 * i] != ~0ull) {
+                    s->prof_ns_total += (double)(st[2 * i + 1] - st[2 * i]);
+                    s->prof_ns_count += 1;
+                }
+        } else {
+            cudaGetLastError();
+        }
+    }
     for (int i = 0; i < slots && i < 8; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]) == cudaSuccess) {
@@ -226,6 +251,7 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         return r;
     }
     cudaMemsetAsync(s->flags, 0, 4 * sizeof(int), s->stream);
+    cudaMemsetAsync(s->Qhat, 0, n * sizeof(double2), s->stream);
     cudaMemsetAsync(s->S2, 0, (size_t)s->g.nExt * sizeof(double2), s->stream);
     cudaMemsetAsync(s->q1q, 0, n * sizeof(double2), s->stream);
     cudaMemsetAsync(s->red, 0, n * sizeof(double2), s->stream);
@@ -239,6 +265,7 @@ void bn_destroy_solver(bn_solver* s) {
     if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
     for (cudaEvent_t ev : s->prof_ev)
         if (ev) cudaEventDestroy(ev);
+    if (s->prof_stamps) cudaFree(s->prof_stamps);
     free_buffers(s);
     bn::release_tables(s->tabs);
     if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -303,9 +330,11 @@ bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count) {
     eval_device(s, s->f, s->Qv);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(Q, s->Qv, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "eval_collision");
     harvest_profile(s, s->prof_slot);
+    if (s->flags_host[2] != 0) return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during eval_collision");
     return BN_OK;
 }
 
@@ -321,10 +350,11 @@ bn_status bn_step_rk(bn_solver* s, double dt, int nsteps) {
         e = cudaGraphLaunch(s->step_graph, s->stream);
         s->launches += s->graph_launches;
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_rk");
     harvest_profile(s, s->prof_slots_used);
+    if (s->flags_host[2] != 0) return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during step_rk");
     const int committed = s->flags_host[1];
     s->t += committed * dt;
     if (s->flags_host[0] != 0) {
@@ -370,6 +400,8 @@ bn_status bn_profile_enable(bn_solver* s, int enable) {
             cudaError_t e = cudaEventCreate(&ev);
             if (e != cudaSuccess) return cuda_fail(e, "profile events");
         }
+        cudaError_t e = cudaMalloc(&s->prof_stamps, 16 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "profile stamps");
     }
     if (on != s->prof && s->step_graph) {
         cudaStreamSynchronize(s->stream);
@@ -379,6 +411,8 @@ bn_status bn_profile_enable(bn_solver* s, int enable) {
     s->prof = on;
     s->prof_ms = 0;
     s->prof_count = 0;
+    s->prof_ns_total = 0;
+    s->prof_ns_count = 0;
     return BN_OK;
 }
 
@@ -387,8 +421,14 @@ bn_status bn_profile_read(bn_solver* s, double* out, size_t count) {
     if (count < 2) return fail(BN_ERR_ARG, "count must be >= 2");
     out[0] = s->prof_ms;
     out[1] = (double)s->prof_count;
+    if (count >= 4) {
+        out[2] = s->prof_ns_total * 1e-6;
+        out[3] = (double)s->prof_ns_count;
+    }
     s->prof_ms = 0;
     s->prof_count = 0;
+    s->prof_ns_total = 0;
+    s->prof_ns_count = 0;
     return BN_OK;
 }
 
@@ -420,7 +460,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
             solvers[i]->launches += solvers[i]->graph_launches;
         }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st0);
+        e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
     if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
     bn_status result = BN_OK;
@@ -428,6 +468,10 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
         bn_solver* s = solvers[i];
         harvest_profile(s, s->prof_slots_used);
         s->t += s->flags_host[1] * dts[i];
+        if (s->flags_host[2] != 0 && result == BN_OK) {
+            if (failed) *failed = i;
+            result = fail(BN_ERR_TIMEOUT, "a bounded device wait gave up in the batch");
+        }
         if (s->flags_host[0] != 0 && result == BN_OK) {
             if (failed) *failed = i;
             result = fail(BN_ERR_NONFINITE, "a solver in the batch became non-finite");

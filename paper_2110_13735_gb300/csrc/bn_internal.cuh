@@ -72,7 +72,8 @@ struct bn_solver {
     int device = 0;
     double scale = 1.0;          // (T/pi)^{d+gamma}
     bn::KernelTables* tabs = nullptr;
-    bn::WorkList work;
+    bn::WorkList work;           // b with non-empty triple-sum boxes (eps != 0)
+    bn::WorkList work_quad;      // b in I_N (quadratic part only, eps == 0)
     int n_partials = 0;          // CTAs of the triple-sum kernel (rows of the partial buffer)
 
     // device buffers
@@ -110,6 +111,9 @@ struct bn_solver {
     int prof_slots_used = 0;        // slots recorded by the current graph / last eval
     double prof_ms = 0;
     long long prof_count = 0;
+    unsigned long long* prof_stamps = nullptr;  // device [16]: per slot (start, end) %globaltimer
+    double prof_ns_total = 0;                   // kernel-span time from the device stamps
+    long long prof_ns_count = 0;
 };
 
 namespace bn {
@@ -140,6 +144,11 @@ void launch_pair_sums(bn_solver* s);        // S2, quad, red from Ghat
 void launch_triple_sum(bn_solver* s);       // q1q from Ghat
 void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
 int triple_partials(const bn_solver* s);
+
+// fused 2-D operator (bn_fused2d.cu)
+void configure_fused2d();
+size_t fused2d_smem(int N, int precision);
+void launch_fused2d(bn_solver* s);   // s->Qhat from s->Ghat / s->Ghat32
 
 }  // namespace bn
 

@@ -331,9 +331,16 @@ int triple_partials(const bn_solver* s) {
     configure_triple<double, 2, 4>();
     configure_triple<float, 3, 8>();
     configure_triple<double, 3, 4>();
+    configure_fused2d();
     int dev = s->device, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
+    if (s->g.d == 2) {
+        // resident CTAs per SM of the fused kernel, limited by its shared memory (227 KB per SM usable)
+        const size_t smem = fused2d_smem(s->g.N, s->opt.precision);
+        const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 1024))));
+        return std::max(1, std::min(s->work.count, per_sm * sms));
+    }
     return std::max(1, std::min(s->work.count, 2 * sms));
 }
 

@@ -244,14 +244,34 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
                      [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
     std::vector<int> flat(items.size());
     for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].second;
-    if (cudaMalloc(&s->work.items, sizeof(int) * flat.size()) != cudaSuccess) {
+    // b in I_N only (the quadratic part), ordered by output-box size
+    std::vector<std::pair<long long, int>> qitems;
+    for (int ib = 0; ib < nb; ++ib) {
+        int b[3];
+        int r = ib;
+        for (int i = d - 1; i >= 0; --i) { b[i] = r % E - N; r /= E; }
+        long long w = 1;
+        for (int i = 0; i < d; ++i) {
+            if (b[i] < -N / 2 || b[i] >= N / 2) { w = 0; break; }
+            w *= box_n(N, b[i]);
+        }
+        if (w > 0) qitems.push_back({w, ib});
+    }
+    std::stable_sort(qitems.begin(), qitems.end(),
+                     [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
+    std::vector<int> qflat(qitems.size());
+    for (size_t i = 0; i < qitems.size(); ++i) qflat[i] = qitems[i].second;
+    if (cudaMalloc(&s->work.items, sizeof(int) * flat.size()) != cudaSuccess ||
+        cudaMalloc(&s->work_quad.items, sizeof(int) * qflat.size()) != cudaSuccess) {
         cudaGetLastError();
         *err = "work list allocation failed";
         return BN_ERR_NOMEM;
     }
     cudaMemcpy(s->work.items, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->work_quad.items, qflat.data(), sizeof(int) * qflat.size(), cudaMemcpyHostToDevice);
     s->work.count = (int)flat.size();
     s->work.terms = total;
+    s->work_quad.count = (int)qflat.size();
     return BN_OK;
 }
 
