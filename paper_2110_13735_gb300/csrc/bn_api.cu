@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "bn_internal.cuh"
 
@@ -24,7 +25,7 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 void free_buffers(bn_solver* s) {
-    void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->S2, s->quad,
+    void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->twiddle, s->S2, s->quad,
                     s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items, s->work_quad.items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -33,8 +34,7 @@ void free_buffers(bn_solver* s) {
 
 // One evaluation Q = Q_eps(f_in) in velocity units, entirely on the solver's stream.
 void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
-    bn::launch_dft_forward(s, f_in, s->Ghat);
-    if (s->opt.precision == BN_MIXED) bn::launch_to_fp32(s, s->Ghat, s->Ghat32, s->g.nModes);
+    bn::launch_dft_forward(s, f_in, s->Ghat);   // also writes the FP32 copy in mixed precision
     if (s->g.d == 2) {
         // the whole 2-D operator in one pass over b (quadratic + reducible + Q_{1,q})
         const int slot = s->prof_slot;
@@ -233,6 +233,7 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     alloc((void**)&s->Ghat, n * sizeof(double2));
     alloc((void**)&s->Ghat32, n * sizeof(float2));
     alloc((void**)&s->work_c, n * sizeof(double2));
+    alloc((void**)&s->twiddle, (size_t)N * sizeof(double2));
     alloc((void**)&s->S2, (size_t)s->g.nExt * sizeof(double2));
     alloc((void**)&s->quad, n * sizeof(double2));
     alloc((void**)&s->red, n * sizeof(double2));
@@ -252,6 +253,13 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     }
     cudaMemsetAsync(s->flags, 0, 4 * sizeof(int), s->stream);
     cudaMemsetAsync(s->Qhat, 0, n * sizeof(double2), s->stream);
+    {
+        // twiddles e^{-2 i pi m / N} in FP64 on the host (one table per solver)
+        std::vector<double2> tw(N);
+        for (int m = 0; m < N; ++m) tw[m] = make_double2(std::cos(2.0 * M_PI * m / N), -std::sin(2.0 * M_PI * m / N));
+        cudaMemcpyAsync(s->twiddle, tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+    }
     cudaMemsetAsync(s->S2, 0, (size_t)s->g.nExt * sizeof(double2), s->stream);
     cudaMemsetAsync(s->q1q, 0, n * sizeof(double2), s->stream);
     cudaMemsetAsync(s->red, 0, n * sizeof(double2), s->stream);

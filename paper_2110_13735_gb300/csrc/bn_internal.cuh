@@ -49,6 +49,8 @@ struct KernelTables {
     double* alphap64 = nullptr;   // [P][nExt]
     double* beta64 = nullptr;     // [nExt(b)][nExt(a)] = beta(a, b)  (b-major)
     float* beta32 = nullptr;      // same, rounded to FP32
+    double* sw64 = nullptr;       // 2-D: [b (ext)][s in I_N] = beta(s,b-s) - beta(b,s) - beta(s,b) (0 off box_s(b))
+    float* sw32 = nullptr;
     size_t bytes = 0;
 };
 
@@ -85,6 +87,7 @@ struct bn_solver {
     double2* Ghat = nullptr;     // modes of the stage argument (FP64)
     float2* Ghat32 = nullptr;    // same in FP32 (mixed precision)
     double2* work_c = nullptr;   // transform scratch, N^d
+    double2* twiddle = nullptr;  // e^{-2 i pi m / N}, m = 0..N-1
     double2* S2 = nullptr;       // reducible pair sums S(t), t in ext box
     double2* quad = nullptr;     // quadratic modes, N^d
     double2* red = nullptr;      // reducible cubic modes, N^d

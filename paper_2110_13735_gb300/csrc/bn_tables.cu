@@ -83,6 +83,28 @@ __global__ void k_beta_table(int nExt, int P, const double* __restrict__ alpha, 
     }
 }
 
+// Reducible weights W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b) for s, b-s in I_N (2-D),
+// stored [b][s] so that the weights of one b are contiguous.
+__global__ void k_sw_table(int N, const double* __restrict__ beta, double* __restrict__ sw64, float* __restrict__ sw32) {
+    const int E = 2 * N, nExt = E * E, nm = N * N;
+    const long long total = (long long)nExt * nm;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int ib = (int)(idx / nm), is = (int)(idx % nm);
+        const int b1 = ib / E - N, b2 = ib % E - N;
+        const int s1 = is / N - N / 2, s2 = is % N - N / 2;
+        const int m1 = b1 - s1, m2 = b2 - s2;
+        double w = 0.0;
+        if (m1 >= -N / 2 && m1 < N / 2 && m2 >= -N / 2 && m2 < N / 2) {
+            const int es = (s1 + N) * E + (s2 + N), em = (m1 + N) * E + (m2 + N);
+            // beta(a, b) is stored at [b][a]
+            w = beta[(size_t)em * nExt + es] - beta[(size_t)es * nExt + ib] - beta[(size_t)ib * nExt + es];
+        }
+        sw64[idx] = w;
+        sw32[idx] = (float)w;
+    }
+}
+
 // Gauss-Legendre rule on [-1, 1]: Newton iteration on P_n from Tricomi's initial guesses.
 void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
     x.assign(n, 0.0);
@@ -168,26 +190,35 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e == cudaSuccess) e = cudaMalloc(&t->alphap64, sizeof(double) * nAl);
     if (e == cudaSuccess) e = cudaMalloc(&t->beta64, sizeof(double) * nBeta);
     if (e == cudaSuccess) e = cudaMalloc(&t->beta32, sizeof(float) * nBeta);
+    const size_t nSw = d == 2 ? (size_t)nExt * s->g.nModes : 0;
+    if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw64, sizeof(double) * nSw);
+    if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw32, sizeof(float) * nSw);
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
         cudaFree(d_nodes);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
+        cudaFree(t->sw64); cudaFree(t->sw32);
         delete t;
         cudaGetLastError();
         return BN_ERR_NOMEM;
     }
-    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * nBeta;
+    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw);
     cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
     k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, d_nodes, t->alpha64,
                                                t->alphap64);
     k_beta_table<<<4096, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
     s->launches += 2;
+    if (nSw) {
+        k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
+        s->launches++;
+    }
     e = cudaStreamSynchronize(s->stream);
     cudaFree(d_nodes);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
+        cudaFree(t->sw64); cudaFree(t->sw32);
         delete t;
         return BN_ERR_CUDA;
     }
@@ -206,6 +237,8 @@ void release_tables(KernelTables* t) {
     cudaFree(t->alphap64);
     cudaFree(t->beta64);
     cudaFree(t->beta32);
+    cudaFree(t->sw64);
+    cudaFree(t->sw32);
     delete t;
 }
 

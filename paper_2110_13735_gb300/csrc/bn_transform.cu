@@ -14,29 +14,27 @@ constexpr int kThreads = 256;
 
 inline int blocks_for(long long n) { return (int)std::min<long long>((n + kThreads - 1) / kThreads, 65535); }
 
-// e^{sign 2 i pi m / N} for integer m, evaluated exactly-rounded through sincospi.
-__device__ __forceinline__ double2 twiddle(long long m, int N, int sign) {
-    long long r = m % N;
-    if (r < 0) r += N;
-    double s, c;
-    sincospi(2.0 * (double)r / (double)N, &s, &c);
-    return make_double2(c, sign * s);
-}
-
-// One separable pass of the DFT along the axis of stride `stride`:
-// out[.., k, ..] = scale * sum_j in[.., j, ..] e^{sign 2 i pi k j / N}, j,k in I_N.
-// `real_in` (if non-null) replaces `in` with a real input.
+// One separable pass of the DFT along the axis of stride `stride`, one warp per output:
+// out[.., k, ..] = scale * sum_j in[.., j, ..] e^{sign 2 i pi k j / N}, j,k in I_N, with the
+// twiddles from the table tw[m] = e^{-2 i pi m / N}; the lanes split the sum over j and a fixed
+// shuffle tree combines them.  `real_in` replaces `in` with a real input; `real_out` receives
+// the real part instead of `out`; `out32` (optional) receives an FP32 copy.
 __global__ void k_dft_axis(const double2* __restrict__ in, const double* __restrict__ real_in,
-                           double2* __restrict__ out, double* __restrict__ real_out, int N, int nTotal, int stride,
-                           int sign, double scale) {
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nTotal; idx += gridDim.x * blockDim.x) {
+                           double2* __restrict__ out, float2* __restrict__ out32, double* __restrict__ real_out,
+                           const double2* __restrict__ tw, int N, int nTotal, int stride, int sign, double scale) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < nTotal; idx += warps) {
         const int c = (idx / stride) % N;
         const int base = idx - c * stride;
         const int k = c - N / 2;
         double sr = 0.0, si = 0.0;
-        for (int jj = 0; jj < N; ++jj) {
+        for (int jj = lane; jj < N; jj += 32) {
             const int j = jj - N / 2;
-            const double2 w = twiddle((long long)k * j, N, sign);
+            int m = (k * j) % N;
+            if (m < 0) m += N;
+            double2 w = __ldg(tw + m);
+            if (sign > 0) w.y = -w.y;
             if (real_in) {
                 const double x = real_in[base + jj * stride];
                 sr = fma(x, w.x, sr);
@@ -47,8 +45,21 @@ __global__ void k_dft_axis(const double2* __restrict__ in, const double* __restr
                 si = fma(x.x, w.y, fma(x.y, w.x, si));
             }
         }
-        if (real_out) real_out[idx] = sr * scale;
-        else out[idx] = make_double2(sr * scale, si * scale);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+            sr *= scale;
+            si *= scale;
+            if (real_out) {
+                real_out[idx] = sr;
+            } else {
+                out[idx] = make_double2(sr, si);
+                if (out32) out32[idx] = make_float2((float)sr, (float)si);
+            }
+        }
     }
 }
 
@@ -225,22 +236,27 @@ __global__ void k_conserve(int d, int N, double T, ConsInv ginv, double* __restr
 
 }  // namespace
 
+// warps of 32 per block; one warp per output element
+inline int dft_blocks(int n) { return std::min((n + 7) / 8, 65535); }
+
 void launch_dft_forward(bn_solver* s, const double* f, double2* out) {
     const int d = s->g.d, N = s->g.N, n = s->g.nModes;
     const double scale = 1.0 / n;
-    // d passes: last axis first (reads the real input), then the others; ping-pong through work_c.
+    float2* out32 = s->opt.precision == BN_MIXED ? s->Ghat32 : nullptr;
+    // d passes: last axis first (reads the real input), then the others; ping-pong through work_c
+    // so that the final pass lands in `out` (and its FP32 copy).
     int stride = 1;
     double2* bufs[2] = {out, s->work_c};
-    // choose the starting buffer so the final pass lands in `out`
     int cur = (d % 2 == 1) ? 0 : 1;
-    k_dft_axis<<<blocks_for(n), kThreads, 0, s->stream>>>(nullptr, f, bufs[cur], nullptr, N, n, stride, -1,
-                                                          d == 1 ? scale : 1.0);
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, s->stream>>>(nullptr, f, bufs[cur], nullptr, nullptr, s->twiddle, N, n,
+                                                          stride, -1, 1.0);
     s->launches++;
     for (int ax = 1; ax < d; ++ax) {
         stride *= N;
         const int nxt = cur ^ 1;
-        k_dft_axis<<<blocks_for(n), kThreads, 0, s->stream>>>(bufs[cur], nullptr, bufs[nxt], nullptr, N, n, stride, -1,
-                                                              ax == d - 1 ? scale : 1.0);
+        const bool last = ax == d - 1;
+        k_dft_axis<<<dft_blocks(n), kThreads, 0, s->stream>>>(bufs[cur], nullptr, bufs[nxt], last ? out32 : nullptr,
+                                                              nullptr, s->twiddle, N, n, stride, -1, last ? scale : 1.0);
         s->launches++;
         cur = nxt;
     }
@@ -254,13 +270,15 @@ void launch_dft_inverse_real(bn_solver* s, const double2* in, double* out, doubl
     double2* bufs[2] = {s->work_c, s->red};  // `red` is consumed before the inverse transform
     int cur = 0;
     for (int ax = 0; ax < d - 1; ++ax) {
-        k_dft_axis<<<blocks_for(n), kThreads, 0, s->stream>>>(src, nullptr, bufs[cur], nullptr, N, n, stride, +1, 1.0);
+        k_dft_axis<<<dft_blocks(n), kThreads, 0, s->stream>>>(src, nullptr, bufs[cur], nullptr, nullptr, s->twiddle, N, n,
+                                                              stride, +1, 1.0);
         s->launches++;
         src = bufs[cur];
         cur ^= 1;
         stride /= N;
     }
-    k_dft_axis<<<blocks_for(n), kThreads, 0, s->stream>>>(src, nullptr, nullptr, out, N, n, stride, +1, scale);
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, s->stream>>>(src, nullptr, nullptr, nullptr, out, s->twiddle, N, n, stride,
+                                                          +1, scale);
     s->launches++;
 }
 
