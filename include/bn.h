@@ -109,6 +109,11 @@ bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count);
  * the solver's state is not touched.  Asynchronous on the solver's stream. */
 bn_status bn_eval_collision_device(bn_solver* s, const double* f_dev, double* Q_dev, size_t count);
 
+/* Fourier modes Q^_n, n in I_N^d (row-major at n_i + N/2), of the current
+ * state (Lemma, Sec. 2.3; before the inverse transform and the (T/pi)^{d+gamma}
+ * prefactor), as interleaved (re, im) FP64 pairs: count = 2 N^d.  Synchronises. */
+bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count);
+
 /* Advance the state by nsteps steps of size dt with the chosen integrator
  * (c = 1 in eq. Boltzmann_homo).  The steps run as one captured CUDA graph per
  * step.  If the state turns non-finite the call returns BN_ERR_NONFINITE and
@@ -160,6 +165,63 @@ const char* bn_last_error(void);
  * to its index, its state rolled back); others keep their progress.
  */
 bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int nsteps, int* failed);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Continuous-batching solve server.
+ *
+ * A request is one homogeneous solve: the operator (as in bn_create_solver),
+ * the initial state f0 (N^d FP64 values on the grid, row-major), the step dt
+ * and the final time t_end (steps = round(t_end / dt) of the chosen
+ * integrator, from t = 0).  bn_server_submit copies f0 and returns at once; a
+ * worker thread owned by the server admits queued requests in arrival order as
+ * long as the device-memory budget allows (the kernel-mode tables of one
+ * operator are shared and counted once), advances all running requests
+ * together in shared launches (a few RK steps per tick; 2-D requests in one
+ * captured graph per set of running requests), and retires finished requests
+ * with their final state copied to host memory.  A request's result does not
+ * depend on the other requests in the batch.  Server calls are thread-safe.
+ * Errors of server calls are reported by bn_server_last_error().
+ * ---------------------------------------------------------------------------
+ */
+typedef struct bn_server bn_server;
+
+typedef struct {
+    int d, N;           /* as in bn_create_solver */
+    double T, R;
+    int kernel;
+    double eps;
+    bn_options opt;     /* zero-filled = defaults */
+    double dt, t_end;   /* step and final time (> 0) */
+} bn_request;
+
+/* Create a server on the current device.  device_bytes: budget for admission
+ * (0 = 80% of the free device memory); max_active: most requests running at
+ * once; cuda_stream: stream for all work (NULL = a new stream). */
+bn_status bn_server_create(size_t device_bytes, int max_active, void* cuda_stream, bn_server** out);
+
+/* Queue a request; *id receives its identifier (> 0).  f0 is copied. */
+bn_status bn_server_submit(bn_server* srv, const bn_request* req, const double* f0, size_t count, long long* id);
+
+/* State of a request: *state = 0 queued, 1 running, 2 done, 3 failed.  When
+ * done and f_out != NULL, the final state (count = N^d) is copied to f_out.
+ * times (ntimes >= 3, may be NULL) receives [submit, admit, done] in seconds
+ * since the server was created.  Returns BN_ERR_STATE for a failed request. */
+bn_status bn_server_poll(bn_server* srv, long long id, int* state, double* f_out, size_t count, double* times,
+                         size_t ntimes);
+
+/* Block until nothing is queued or running, or timeout_s elapses (BN_ERR_TIMEOUT). */
+bn_status bn_server_wait_idle(bn_server* srv, double timeout_s);
+
+/* out (count >= 8): [submitted, admitted, done, failed, ticks, most running at once,
+ * budgeted bytes in use, budget]. */
+bn_status bn_server_stats(bn_server* srv, double* out, size_t count);
+
+/* Message of the last failed server call on this thread. */
+const char* bn_server_last_error(void);
+
+/* Stop the worker (queued and running requests are abandoned) and free everything. */
+void bn_server_destroy(bn_server* srv);
 
 #ifdef __cplusplus
 }

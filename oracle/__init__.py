@@ -119,7 +119,7 @@ class Operator:
 
     # full kernel-mode tables above this many entries are not formed; beta is then
     # evaluated on demand from the alpha tables (the sum of eq. betadD)
-    TABLE_LIMIT = 1 << 27
+    TABLE_LIMIT = 1 << 29
 
     @property
     def use_table(self) -> bool:

@@ -35,6 +35,12 @@ class Options(ctypes.Structure):
                 ("quad3d", ctypes.c_int)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int), ("T", ctypes.c_double), ("R", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("eps", ctypes.c_double), ("opt", Options), ("dt", ctypes.c_double),
+                ("t_end", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -59,6 +65,7 @@ def load(path: str | None = None):
     lib.bn_get_state_device.argtypes = [vp, vp, sz]
     lib.bn_eval_collision.argtypes = [vp, dp, sz]
     lib.bn_eval_collision_device.argtypes = [vp, vp, vp, sz]
+    lib.bn_eval_collision_modes.argtypes = [vp, dp, sz]
     lib.bn_step_rk.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.bn_moments.argtypes = [vp, dp, sz]
     lib.bn_work_counts.argtypes = [vp, dp, sz]
@@ -68,6 +75,14 @@ def load(path: str | None = None):
     lib.bn_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.bn_profile_read.argtypes = [vp, dp, sz]
     lib.bn_step_rk_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.bn_server_create.argtypes = [sz, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.bn_server_submit.argtypes = [vp, ctypes.POINTER(Request), dp, sz, ctypes.POINTER(ctypes.c_longlong)]
+    lib.bn_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), dp, sz, dp, sz]
+    lib.bn_server_wait_idle.argtypes = [vp, ctypes.c_double]
+    lib.bn_server_stats.argtypes = [vp, dp, sz]
+    lib.bn_server_last_error.restype = ctypes.c_char_p
+    lib.bn_server_destroy.argtypes = [vp]
+    lib.bn_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -165,6 +180,12 @@ class Solver:
         _check(_lib.bn_eval_collision(self._h, _dptr(out), out.size))
         return out.reshape(self.shape)
 
+    def eval_collision_modes(self) -> np.ndarray:
+        """Q^_n, n in I_N^d (complex, shape (N,)*d), before the inverse transform and prefactor."""
+        out = np.empty(2 * self.n_modes)
+        _check(_lib.bn_eval_collision_modes(self._h, _dptr(out), out.size))
+        return out.view(np.complex128).reshape(self.shape)
+
     def eval_collision_device(self, f_dev, Q_dev):
         _check(_lib.bn_eval_collision_device(self._h, ctypes.c_void_p(f_dev.data_ptr()),
                                              ctypes.c_void_p(Q_dev.data_ptr()), f_dev.numel()))
@@ -206,3 +227,68 @@ def step_rk_batch(solvers, dts, nsteps: int):
     st = lib.bn_step_rk_batch(hs, n, _dptr(d), int(nsteps), ctypes.byref(failed))
     _check(st)
     return failed.value
+
+
+class Server:
+    """Continuous-batching solve server (include/bn.h: bn_server_*)."""
+
+    def __init__(self, device_bytes: int = 0, max_active: int = 64, stream=None):
+        lib = load()
+        raw = int(getattr(stream, "cuda_stream", stream)) if stream is not None else 0
+        h = ctypes.c_void_p()
+        st = lib.bn_server_create(int(device_bytes), int(max_active), ctypes.c_void_p(raw) if raw else None,
+                                  ctypes.byref(h))
+        if st != BN_OK:
+            raise BNError(st, lib.bn_server_last_error().decode())
+        self._h = h
+
+    def _chk(self, st):
+        if st != BN_OK:
+            raise BNError(st, _lib.bn_server_last_error().decode())
+
+    def submit(self, d, N, T, R, kernel, eps, f0, dt, t_end, **opts) -> int:
+        r = Request()
+        r.d, r.N, r.T, r.R, r.kernel, r.eps = int(d), int(N), float(T), float(R), int(kernel), float(eps)
+        r.opt = options(**opts)
+        r.dt, r.t_end = float(dt), float(t_end)
+        f = np.ascontiguousarray(np.asarray(f0, dtype=np.float64).reshape(-1))
+        rid = ctypes.c_longlong()
+        self._chk(_lib.bn_server_submit(self._h, ctypes.byref(r), _dptr(f), f.size, ctypes.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, rid: int, n_modes: int | None = None):
+        """(state, result or None, (t_submit, t_admit, t_done)); state 0 queued, 1 running, 2 done, 3 failed."""
+        state = ctypes.c_int()
+        times = np.zeros(3)
+        out = np.empty(n_modes) if n_modes else None
+        st = _lib.bn_server_poll(self._h, int(rid), ctypes.byref(state), _dptr(out) if out is not None else None,
+                                 out.size if out is not None else 0, _dptr(times), 3)
+        if st != BN_OK and state.value != 3:
+            self._chk(st)
+        return state.value, (out if state.value == 2 else None), tuple(times)
+
+    def wait_idle(self, timeout: float = 600.0):
+        self._chk(_lib.bn_server_wait_idle(self._h, float(timeout)))
+
+    def stats(self):
+        out = np.zeros(8)
+        self._chk(_lib.bn_server_stats(self._h, _dptr(out), 8))
+        keys = ["submitted", "admitted", "done", "failed", "ticks", "max_active", "bytes_in_use", "budget"]
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.bn_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -6,12 +6,29 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <mutex>
 
 #include "bn_internal.cuh"
 
 namespace {
 
 thread_local std::string g_err;
+
+// cache of captured batched steps (a few recent solver sets)
+std::mutex g_plan_mu;
+std::vector<bn::BatchPlan*> g_plans;
+
+void drop_plans_with(const bn_solver* s) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        if (bn::plan_contains(*it, s)) {
+            bn::destroy_plan(*it);
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
 
 bn_status fail(bn_status st, const std::string& msg) {
     g_err = msg;
@@ -270,6 +287,7 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
 void bn_destroy_solver(bn_solver* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    drop_plans_with(s);
     if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
     for (cudaEvent_t ev : s->prof_ev)
         if (ev) cudaEventDestroy(ev);
@@ -343,6 +361,22 @@ bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count) {
     if (e != cudaSuccess) return cuda_fail(e, "eval_collision");
     harvest_profile(s, s->prof_slot);
     if (s->flags_host[2] != 0) return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during eval_collision");
+    return BN_OK;
+}
+
+bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count) {
+    if (!valid_solver(s) || !Qhat) return fail(BN_ERR_ARG, "null argument");
+    if (count != 2 * (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be 2 N^d");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    s->prof_slot = 0;
+    eval_device(s, s->f, s->Qv);   // leaves the combined modes in s->Qhat
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Qhat, s->Qhat, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "eval_collision_modes");
+    harvest_profile(s, s->prof_slot);
+    if (s->flags_host[2] != 0) return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during eval_collision_modes");
     return BN_OK;
 }
 
@@ -443,30 +477,60 @@ bn_status bn_profile_read(bn_solver* s, double* out, size_t count) {
 bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int nsteps, int* failed) {
     if (failed) *failed = -1;
     if (!solvers || n <= 0 || !dts || nsteps < 0) return fail(BN_ERR_ARG, "invalid batch arguments");
+    bool shared = true;   // every request 2-D with one integrator and no live profiling: one graph for all
     for (int i = 0; i < n; ++i) {
         if (!solvers[i]) return fail(BN_ERR_ARG, "null solver in batch");
         if (!solvers[i]->has_state) return fail(BN_ERR_STATE, "solver in batch has no state");
-        bn_status st = ensure_graph(solvers[i], dts[i]);
-        if (st != BN_OK) return st;
+        if (!(dts[i] > 0) || !std::isfinite(dts[i])) return fail(BN_ERR_ARG, "dt must be > 0");
+        for (int j = 0; j < i; ++j)
+            if (solvers[j] == solvers[i]) return fail(BN_ERR_ARG, "a solver appears twice in the batch");
+        if (solvers[i]->g.d != 2 || solvers[i]->opt.integrator != solvers[0]->opt.integrator || solvers[i]->prof)
+            shared = false;
     }
+    if (nsteps == 0) return BN_OK;
     cudaStream_t st0 = solvers[0]->stream;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    for (int i = 0; i < n; ++i)
         if (solvers[i]->stream != st0) {
-            // order this solver's stream before the shared stream
+            // order each solver's own stream before the shared stream
             cudaEvent_t ev;
             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
             cudaEventRecord(ev, solvers[i]->stream);
             cudaStreamWaitEvent(st0, ev, 0);
             cudaEventDestroy(ev);
         }
-        e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
-    }
-    for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
-            e = cudaGraphLaunch(solvers[i]->step_graph, st0);
-            solvers[i]->launches += solvers[i]->graph_launches;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
+    if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
+    if (shared) {
+        bn::BatchPlan* plan = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(g_plan_mu);
+            for (bn::BatchPlan* p : g_plans)
+                if (bn::plan_matches(p, solvers, n, dts)) { plan = p; break; }
         }
+        if (!plan) {
+            std::string err;
+            bn_status st = bn::build_plan(solvers, n, dts, st0, &plan, &err);
+            if (st != BN_OK) return fail(st, err);
+            std::lock_guard<std::mutex> lock(g_plan_mu);
+            g_plans.push_back(plan);
+            while (g_plans.size() > 4) {
+                bn::destroy_plan(g_plans.front());
+                g_plans.erase(g_plans.begin());
+            }
+        }
+        if (bn::replay_plan(plan, st0, nsteps) != BN_OK) return cuda_fail(cudaGetLastError(), "batch replay");
+    } else {
+        for (int i = 0; i < n; ++i) {
+            bn_status st = ensure_graph(solvers[i], dts[i]);
+            if (st != BN_OK) return st;
+        }
+        for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                e = cudaGraphLaunch(solvers[i]->step_graph, st0);
+                solvers[i]->launches += solvers[i]->graph_launches;
+            }
+    }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
@@ -474,7 +538,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
     bn_status result = BN_OK;
     for (int i = 0; i < n; ++i) {
         bn_solver* s = solvers[i];
-        harvest_profile(s, s->prof_slots_used);
+        if (!shared) harvest_profile(s, s->prof_slots_used);
         s->t += s->flags_host[1] * dts[i];
         if (s->flags_host[2] != 0 && result == BN_OK) {
             if (failed) *failed = i;

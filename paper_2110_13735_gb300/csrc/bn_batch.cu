@@ -1,0 +1,340 @@
+// bn_batch.cu -- many 2-D requests advanced together: every stage of one RK step of all
+// requests runs as a fixed set of shared launches (transforms, the fused operator per
+// precision/size variant, partial sums, stage updates), captured once per set of requests
+// as one CUDA graph.  Each request keeps its own CTA partition, so its result is identical
+// to the one it gets alone.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// one request in the batched element-wise / transform launches
+struct ElemJob {
+    int N, nm;
+    double* f;          // state
+    double* y;          // stage argument
+    double* kacc;       // RK accumulator
+    double* Qv;         // stage derivative in velocity units
+    double* cand;       // candidate state
+    int* flags;         // [0] non-finite, [1] committed steps
+    double2* Ghat;
+    float2* Ghat32;     // null in FP64 mode
+    double2* work_c;
+    const double2* tw;
+    double2* Qhat;
+    double2* partials;
+    int nPart;
+    double dt, scale;
+};
+
+__device__ __forceinline__ double2 warp_sum2(double sr, double si) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    return make_double2(sr, si);
+}
+
+__device__ __forceinline__ double2 tw_at(const double2* tw, int k, int j, int N, int sign) {
+    int m = (k * j) % N;
+    if (m < 0) m += N;
+    double2 w = __ldg(tw + m);
+    if (sign > 0) w.y = -w.y;
+    return w;
+}
+
+// Pass `pass` of the 2-D transforms for job blockIdx.y, one warp per output:
+//   0: real stage input (f or y) along n_2 -> work_c         (forward)
+//   1: work_c along n_1 -> Ghat (and Ghat32), scale N^-2      (forward)
+//   2: Qhat along n_1 -> work_c                               (inverse)
+//   3: work_c along n_2 -> Qv = scale * Re                    (inverse)
+__global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stage_in) {
+    const ElemJob J = jobs[blockIdx.y];
+    const int N = J.N, nm = J.nm, lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int stride = (pass == 0 || pass == 3) ? 1 : N;
+    const int sign = pass < 2 ? -1 : +1;
+    const double* rin = stage_in == 0 ? J.f : J.y;
+    for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < nm; idx += warps) {
+        const int c = (idx / stride) % N, base = idx - c * stride, k = c - N / 2;
+        double sr = 0.0, si = 0.0;
+        for (int jj = lane; jj < N; jj += 32) {
+            const double2 w = tw_at(J.tw, k, jj - N / 2, N, sign);
+            if (pass == 0) {
+                const double x = rin[base + jj * stride];
+                sr = fma(x, w.x, sr);
+                si = fma(x, w.y, si);
+            } else {
+                const double2 x = (pass == 2 ? J.Qhat : J.work_c)[base + jj * stride];
+                sr = fma(x.x, w.x, fma(-x.y, w.y, sr));
+                si = fma(x.x, w.y, fma(x.y, w.x, si));
+            }
+        }
+        const double2 sum = warp_sum2(sr, si);
+        if (lane == 0) {
+            if (pass == 0 || pass == 2) {
+                J.work_c[idx] = sum;
+            } else if (pass == 1) {
+                const double sc = 1.0 / nm;
+                J.Ghat[idx] = make_double2(sum.x * sc, sum.y * sc);
+                if (J.Ghat32) J.Ghat32[idx] = make_float2((float)(sum.x * sc), (float)(sum.y * sc));
+            } else {
+                J.Qv[idx] = sum.x * J.scale;
+            }
+        }
+    }
+}
+
+// Fixed-order sum of each job's partials into its Q^ (same order as the single-request kernel).
+__global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __restrict__ jobs) {
+    const ElemJob J = jobs[blockIdx.y];
+    __shared__ double2 sh[32][8];
+    const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
+    const int i = blockIdx.x * 8 + m;
+    if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
+    double x = 0, y = 0;
+    if (i < J.nm) {
+        for (int c = w; c < J.nPart; c += 32) {
+            const double2 v = J.partials[(size_t)c * J.nm + i];
+            x += v.x;
+            y += v.y;
+        }
+    }
+    sh[w][m] = make_double2(x, y);
+    __syncthreads();
+    if (threadIdx.x < 8 && i < J.nm) {
+        double sx = 0, sy = 0;
+        for (int k = 0; k < 32; ++k) { sx += sh[k][m].x; sy += sh[k][m].y; }
+        J.Qhat[i] = make_double2(sx, sy);
+    }
+}
+
+// RK4 stage update for every job: acc = (first ? 0 : acc) + w_acc K;  y = f + c dt K
+__global__ void k_rk_stage_batch(const ElemJob* __restrict__ jobs, double w_acc, double c, int first) {
+    const ElemJob J = jobs[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) {
+        const double k = J.Qv[i];
+        J.kacc[i] = first ? w_acc * k : fma(w_acc, k, J.kacc[i]);
+        J.y[i] = fma(c * J.dt, k, J.f[i]);
+    }
+}
+
+// candidate = f + dt/6 (acc + K); non-finite -> flags[0]
+__global__ void k_rk_final_batch(const ElemJob* __restrict__ jobs) {
+    const ElemJob J = jobs[blockIdx.y];
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) {
+        const double v = fma(J.dt / 6.0, J.kacc[i] + J.Qv[i], J.f[i]);
+        J.cand[i] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(&J.flags[0], 1);
+}
+
+// SSP-RK2: candidate = (f + y + dt K) / 2
+__global__ void k_heun_final_batch(const ElemJob* __restrict__ jobs) {
+    const ElemJob J = jobs[blockIdx.y];
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) {
+        const double v = 0.5 * (J.f[i] + fma(J.dt, J.Qv[i], J.y[i]));
+        J.cand[i] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(&J.flags[0], 1);
+}
+
+__global__ void k_commit_batch(const ElemJob* __restrict__ jobs) {
+    const ElemJob J = jobs[blockIdx.y];
+    if (J.flags[0] != 0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) J.f[i] = J.cand[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) J.flags[1] += 1;
+}
+
+}  // namespace
+
+// A captured batched step for a fixed list of 2-D solvers.
+struct BatchPlan {
+    std::vector<bn_solver*> solvers;
+    std::vector<double> dts;
+    int integrator = 0;
+    ElemJob* d_elem = nullptr;
+    struct Group {
+        int variant = 0, njobs = 0, total = 0, maxN = 0;
+        void* d_jobs = nullptr;
+        int* d_cta = nullptr;
+    };
+    std::vector<Group> groups;
+    int maxN = 0, maxNm = 0;
+    cudaGraphExec_t graph = nullptr;
+    long long launches = 0;   // kernels per replay
+};
+
+void destroy_plan(BatchPlan* p) {
+    if (!p) return;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    cudaFree(p->d_elem);
+    for (auto& g : p->groups) {
+        cudaFree(g.d_jobs);
+        cudaFree(g.d_cta);
+    }
+    delete p;
+}
+
+static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in) {
+    const int nj = (int)p->solvers.size();
+    const dim3 gw((p->maxNm * 32 + kThreads - 1) / kThreads, nj);
+    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
+    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
+    for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
+    k_sum_partials_batch<<<dim3((p->maxNm + 7) / 8, nj), 256, 0, st>>>(p->d_elem);
+    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
+    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in);
+    p->launches += 5 + (long long)p->groups.size();
+    for (bn_solver* s : p->solvers)
+        if (s->opt.conserve) {
+            cudaStream_t own = s->stream;   // the projection kernel joins the capture on the shared stream
+            s->stream = st;
+            launch_conserve(s, s->Qv);
+            s->stream = own;
+        }
+}
+
+bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t st, BatchPlan** out,
+                     std::string* err) {
+    BatchPlan* p = new BatchPlan();
+    p->integrator = solvers[0]->opt.integrator;
+    std::vector<ElemJob> elem;
+    std::map<int, std::vector<int>> by_variant;
+    for (int i = 0; i < n; ++i) {
+        bn_solver* s = solvers[i];
+        p->solvers.push_back(s);
+        p->dts.push_back(dts[i]);
+        ElemJob J{};
+        J.N = s->g.N;
+        J.nm = s->g.nModes;
+        J.f = s->f;
+        J.y = s->y;
+        J.kacc = s->kacc;
+        J.Qv = s->Qv;
+        J.cand = s->f_prev;
+        J.flags = s->flags;
+        J.Ghat = s->Ghat;
+        J.Ghat32 = s->opt.precision == BN_MIXED ? s->Ghat32 : nullptr;
+        J.work_c = s->work_c;
+        J.tw = s->twiddle;
+        J.Qhat = s->Qhat;
+        J.partials = s->partials;
+        J.nPart = std::max(1, std::min(s->eps != 0.0 ? s->work.count : s->work_quad.count, s->n_partials));
+        J.dt = dts[i];
+        J.scale = s->scale;
+        elem.push_back(J);
+        p->maxN = std::max(p->maxN, s->g.N);
+        p->maxNm = std::max(p->maxNm, s->g.nModes);
+        by_variant[fused2d_variant(s)].push_back(i);
+    }
+    cudaError_t e = cudaMalloc(&p->d_elem, sizeof(ElemJob) * elem.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_elem, elem.data(), sizeof(ElemJob) * elem.size(), cudaMemcpyHostToDevice);
+    for (auto& kv : by_variant) {
+        if (e != cudaSuccess) break;
+        BatchPlan::Group g;
+        g.variant = kv.first;
+        const bool mixed = kv.first <= 1;
+        const size_t asz = mixed ? sizeof(FusedArgs<float>) : sizeof(FusedArgs<double>);
+        std::vector<unsigned char> args(asz * kv.second.size());
+        std::vector<int> cta(1, 0);
+        for (size_t k = 0; k < kv.second.size(); ++k) {
+            bn_solver* s = solvers[kv.second[k]];
+            fill_fused_args(s, args.data() + asz * k);
+            cta.push_back(cta.back() + elem[kv.second[k]].nPart);
+            g.maxN = std::max(g.maxN, s->g.N);
+        }
+        g.njobs = (int)kv.second.size();
+        g.total = cta.back();
+        e = cudaMalloc(&g.d_jobs, args.size());
+        if (e == cudaSuccess) e = cudaMalloc((void**)&g.d_cta, sizeof(int) * cta.size());
+        if (e == cudaSuccess) e = cudaMemcpy(g.d_jobs, args.data(), args.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g.d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice);
+        p->groups.push_back(g);
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("batch plan: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        destroy_plan(p);
+        return e == cudaErrorMemoryAllocation ? BN_ERR_NOMEM : BN_ERR_CUDA;
+    }
+    // capture one step of every request
+    cudaGraph_t graph;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        *err = std::string("batch capture: ") + cudaGetErrorString(e);
+        destroy_plan(p);
+        return BN_ERR_CUDA;
+    }
+    const int nj = n;
+    const dim3 ge((p->maxNm + kThreads - 1) / kThreads, nj);
+    if (p->integrator == 0) {
+        const double wacc[4] = {1.0, 2.0, 2.0, 1.0}, cnext[3] = {0.5, 0.5, 1.0};
+        for (int stage = 0; stage < 4; ++stage) {
+            record_batched_eval(p, st, stage == 0 ? 0 : 1);
+            if (stage < 3) {
+                k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, wacc[stage], cnext[stage], stage == 0);
+                p->launches++;
+            }
+        }
+        k_rk_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
+    } else {
+        record_batched_eval(p, st, 0);
+        k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, 0.0, 1.0, 1);
+        record_batched_eval(p, st, 1);
+        k_heun_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
+        p->launches++;
+    }
+    k_commit_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
+    p->launches += 2;
+    e = cudaStreamEndCapture(st, &graph);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&p->graph, graph, 0);
+        cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("batch graph: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        destroy_plan(p);
+        return BN_ERR_CUDA;
+    }
+    *out = p;
+    return BN_OK;
+}
+
+bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts) {
+    if (!p || (int)p->solvers.size() != n) return false;
+    for (int i = 0; i < n; ++i)
+        if (p->solvers[i] != solvers[i] || p->dts[i] != dts[i]) return false;
+    return true;
+}
+
+bn_status replay_plan(BatchPlan* p, cudaStream_t st, int nsteps) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(p->graph, st);
+    if (e != cudaSuccess) return BN_ERR_CUDA;
+    for (bn_solver* s : p->solvers) s->launches += p->launches * nsteps / (long long)p->solvers.size();
+    return BN_OK;
+}
+
+long long plan_launches(const BatchPlan* p) { return p ? p->launches : 0; }
+
+bool plan_contains(const BatchPlan* p, const bn_solver* s) {
+    return p && std::find(p->solvers.begin(), p->solvers.end(), s) != p->solvers.end();
+}
+
+}  // namespace bn

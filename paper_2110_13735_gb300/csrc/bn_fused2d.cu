@@ -22,6 +22,7 @@
 // partials in a fixed order (deterministic results).
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 
 #include "bn_internal.cuh"
 
@@ -68,19 +69,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-template <typename Real>
-struct FusedArgs {
-    int N;
-    double eps;              // 0: quadratic part only
-    const cplx<Real>* G;     // modes (N^2)
-    const Real* beta;        // [b][a] kernel-mode table
-    const int* items;        // b (flat extended index), descending work
-    int count;
-    double2* partials;       // [gridDim.x][N^2]
-    int* err;                // [0] set to 1 if a bounded wait gave up
-    unsigned long long* stamps;  // optional [2]: min start / max end %globaltimer (ns) over CTAs
-    const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
-};
+
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -119,8 +108,8 @@ template <> struct Acc<float> {
     }
 };
 
-// Shared-memory layout (bytes) for a given N, thread count and staging choice.
-template <typename Real, int RW, bool STAGE>
+// Shared-memory layout (bytes) for a given N, thread count, staging and double buffering.
+template <typename Real, int RW, bool STAGE, bool DB>
 struct Layout2D {
     // padded row stride of the staged beta rectangle: >= RW ceil(N/RW) + N columns and
     // congruent to 1 mod 32, so lanes on 8 consecutive rows x 4 groups of RW columns hit
@@ -129,7 +118,8 @@ struct Layout2D {
         const int w = RW * ((N + RW - 1) / RW) + N;
         return 32 * ((w - 1 + 31) / 32) + 1;
     }
-    static __host__ __device__ size_t region(int N, int nt) {   // beta rectangle, reused for split sums
+    // one buffer: the staged beta rectangle, reused for the split sums after the sweep
+    static __host__ __device__ size_t slot(int N, int nt) {
         const size_t bs = STAGE ? (size_t)(2 * N) * stride(N) * sizeof(Real) : 0;
         const size_t cp = (size_t)nt * RW * sizeof(cplx<Real>);
         return ((bs > cp ? bs : cp) + 15) / 16 * 16;
@@ -137,9 +127,9 @@ struct Layout2D {
     static __host__ __device__ size_t bytes(int N, int nt) {
         const size_t nm = (size_t)N * N;
         size_t b = nm * sizeof(cplx<Real>) * (Acc<Real>::kComp ? 2 : 1);   // Q accumulator (+ compensation)
-        b += 2 * nm * sizeof(cplx<Real>);                                    // Gs, Pb
-        b += region(N, nt);                                                  // beta rectangle / split sums
-        b += 64 * sizeof(double2);                                           // S(b) warp partials
+        b += nm * sizeof(cplx<Real>);                                        // Gs
+        b += (size_t)N * (N + 2) * sizeof(cplx<Real>);                      // Pb (rows padded to even length)
+        b += slot(N, nt) * (DB ? 2 : 1);                                     // beta rectangle(s) / split sums
         b += 16;                                                             // mbarrier
         return b;
     }
@@ -152,32 +142,105 @@ __device__ __forceinline__ void task_rc(int rem, int Gg, int& i, int& g) {
     i = rem / Gg;
     g = rem % Gg;
 }
-__device__ __forceinline__ int rc_task(int i, int g, int Gg) { return i * Gg + g; }
+
+// 4- or 8-byte asynchronous copy global -> shared (zero-filled when !valid).
+template <typename Real>
+__device__ __forceinline__ void cp_async_elem(Real* dst, const Real* src, bool valid) {
+    if (sizeof(Real) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 8 : 0)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+// Box geometry of one b (per dimension: outputs n with n, n-b in I_N; inner s with s, b-s in I_N)
+// and the beta rectangle a = n - s that the sweep reads.
+template <int RW>
+struct ItemGeo {
+    int b1, b2, nlo1, L1, nlo2, L2, slo1, S1, slo2, S2, Gg, A1, a1lo, A2, a2lo;
+    bool quad;
+    __device__ __forceinline__ ItemGeo(int ib, int N) {
+        const int E = 2 * N;
+        b1 = ib / E - N;
+        b2 = ib % E - N;
+        nlo1 = max(-N / 2, b1 - N / 2);
+        L1 = min(N / 2 - 1, b1 + N / 2 - 1) - nlo1 + 1;
+        nlo2 = max(-N / 2, b2 - N / 2);
+        L2 = min(N / 2 - 1, b2 + N / 2 - 1) - nlo2 + 1;
+        slo1 = max(-N / 2, b1 - N / 2 + 1);
+        S1 = min(N / 2 - 1, b1 + N / 2) - slo1 + 1;
+        slo2 = max(-N / 2, b2 - N / 2 + 1);
+        S2 = min(N / 2 - 1, b2 + N / 2) - slo2 + 1;
+        quad = b1 >= -N / 2 && b1 < N / 2 && b2 >= -N / 2 && b2 < N / 2;
+        Gg = (L2 + RW - 1) / RW;
+        A1 = L1 + S1 - 1;
+        a1lo = nlo1 - slo1 - S1 + 1;
+        A2 = RW * Gg + S2;            // one spare column on the left
+        a2lo = nlo2 - slo2 - S2;
+    }
+};
+
+// Issue the asynchronous copies of the beta rectangle of item `ib` into `Bs` (padded stride WS).
+template <typename Real, int RW, int NT>
+__device__ __forceinline__ void stage_rect(Real* Bs, const Real* __restrict__ beta, int ib, int N, int WS) {
+    const ItemGeo<RW> g(ib, N);
+    const int E = 2 * N, nExt = E * E;
+    const Real* __restrict__ bsl = beta + (size_t)ib * nExt;
+    for (int q = threadIdx.x; q < g.A1 * g.A2; q += NT) {
+        const int r = q / g.A2, c = q % g.A2;
+        const int a1 = g.a1lo + r, a2 = g.a2lo + c;
+        const bool ok = a2 >= -N && a2 < N;
+        cp_async_elem(Bs + r * WS + c, bsl + (a1 + N) * E + (ok ? a2 + N : 0), ok);
+    }
+}
+
+// Two consecutive P_b entries (16 bytes; FP32 only).
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+    a = p[0];
+    b = p[1];
+}
 
 // One s_1 row of the Toeplitz product: ar/ai[r] += sum_{s2} beta(c0 + r - s2) P(s2), with the
 // weights held in a register window whose slots rotate (slot of offset x is x mod RW), so that
-// every step costs one load of beta, one load of P and 2 RW FMA, with no register moves.
+// every step costs one load of beta, half a load of P (pairs, the row starts 16-byte aligned)
+// and 2 RW FMA, with no register moves.
 template <typename Real, int RW, typename LoadB>
 __device__ __forceinline__ void row_sweep(LoadB ldb, int c0, const cplx<Real>* __restrict__ prow, int S2,
                                           Real (&ar)[RW], Real (&ai)[RW]) {
+    static_assert(RW % 2 == 0, "RW must be even");
     Real w[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) w[r] = ldb(c0 + r);
     int sl = 0;
     for (; sl + RW <= S2; sl += RW) {
 #pragma unroll
-        for (int k = 0; k < RW; ++k) {
-            if (k == 0) {
-                if (sl > 0) w[0] = ldb(c0 - sl);
-            } else {
-                w[RW - k] = ldb(c0 - sl - k);
-            }
-            const cplx<Real> p = prow[sl + k];
+        for (int k = 0; k < RW; k += 2) {
+            cplx<Real> p0, p1;
+            ld_pair(prow + sl + k, p0, p1);
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const Real wr = w[(r - k + RW) % RW];
-                ar[r] = fma(wr, p.x, ar[r]);
-                ai[r] = fma(wr, p.y, ai[r]);
+            for (int h = 0; h < 2; ++h) {
+                const int kk = k + h;
+                if (kk == 0) {
+                    if (sl > 0) w[0] = ldb(c0 - sl);
+                } else {
+                    w[RW - kk] = ldb(c0 - sl - kk);
+                }
+                const cplx<Real> p = h == 0 ? p0 : p1;
+#pragma unroll
+                for (int r = 0; r < RW; ++r) {
+                    const Real wr = w[(r - kk + RW) % RW];
+                    ar[r] = fma(wr, p.x, ar[r]);
+                    ai[r] = fma(wr, p.y, ai[r]);
+                }
             }
         }
     }
@@ -199,33 +262,37 @@ __device__ __forceinline__ void row_sweep(LoadB ldb, int c0, const cplx<Real>* _
     }
 }
 
-template <typename Real, int RW, int NT, bool STAGE>
-__global__ void __launch_bounds__(NT) k_fused2d(FusedArgs<Real> A) {
+// The operator for one request, run by CTA `blk` of the `nblk` CTAs that serve it.
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+__device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, int nblk) {
     using C = cplx<Real>;
     using AC = Acc<Real>;
+    using LY = Layout2D<Real, RW, STAGE, DB>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = A.N, E = 2 * N, nExt = E * E, nm = N * N;
-    const int WS = Layout2D<Real, RW, STAGE>::stride(N);
+    const int WS = LY::stride(N);
     C* Qs = reinterpret_cast<C*>(smem_raw);
     C* Qc = Qs + (AC::kComp ? nm : 0);
     C* Gs = Qc + nm;
     C* Pb = Gs + nm;
-    unsigned char* region = reinterpret_cast<unsigned char*>(Pb + nm);
-    Real* Bs = reinterpret_cast<Real*>(region);
-    C* Cpart = reinterpret_cast<C*>(region);   // reused after the sweep (split sums)
-    double2* Sred = reinterpret_cast<double2*>(region + Layout2D<Real, RW, STAGE>::region(N, NT));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Sred + 64);
-    const int tid = threadIdx.x;
+    unsigned char* slots = reinterpret_cast<unsigned char*>(Pb + N * (N + 2));
+    const size_t slot_bytes = LY::slot(N, NT);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(slots + slot_bytes * (DB ? 2 : 1));
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool cubic = A.eps != 0.0;
     const Real eps_r = (Real)A.eps;
     if (A.stamps && tid == 0) atomicMin(&A.stamps[0], global_ns());
 
-    // G^ -> shared memory with one bulk copy (TMA engine), overlapped with zeroing the accumulator.
+    // G^ -> shared memory with one bulk copy (TMA engine); the first beta rectangle is requested
+    // at the same time and the accumulator zeroed while both are in flight.
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, (uint32_t)(nm * sizeof(C)));
         bulk_g2s(Gs, A.G, (uint32_t)(nm * sizeof(C)), bar);
     }
+    if (STAGE && cubic && blk < A.count)
+        stage_rect<Real, RW, NT>(reinterpret_cast<Real*>(slots), A.beta, A.items[blk], N, WS);
+    cp_async_commit();
     for (int i = tid; i < nm; i += NT) {
         Qs[i] = cmake<C>(0.0, 0.0);
         if (AC::kComp) Qc[i] = cmake<C>(0.0, 0.0);
@@ -236,63 +303,68 @@ __global__ void __launch_bounds__(NT) k_fused2d(FusedArgs<Real> A) {
         // copy in flight, and give up
         atomicOr(A.err, 1);
         mbar_wait_bounded(bar, 0, kWaitLimit);
+        cp_async_wait<0>();
         return;
     }
 
-    for (int item = blockIdx.x; item < A.count; item += gridDim.x) {
+    int buf = 0;
+    for (int item = blk; item < A.count; item += nblk, buf ^= (DB ? 1 : 0)) {
         const int ib = A.items[item];
-        const int b1 = ib / E - N, b2 = ib % E - N;
-        const int nlo1 = max(-N / 2, b1 - N / 2), L1 = min(N / 2 - 1, b1 + N / 2 - 1) - nlo1 + 1;
-        const int nlo2 = max(-N / 2, b2 - N / 2), L2 = min(N / 2 - 1, b2 + N / 2 - 1) - nlo2 + 1;
-        const int slo1 = max(-N / 2, b1 - N / 2 + 1), S1 = min(N / 2 - 1, b1 + N / 2) - slo1 + 1;
-        const int slo2 = max(-N / 2, b2 - N / 2 + 1), S2 = min(N / 2 - 1, b2 + N / 2) - slo2 + 1;
-        const bool quad = b1 >= -N / 2 && b1 < N / 2 && b2 >= -N / 2 && b2 < N / 2;
-        const int Gg = (L2 + RW - 1) / RW;
+        const ItemGeo<RW> g(ib, N);
         const Real* __restrict__ bsl = A.beta + (size_t)ib * nExt;   // beta(., b), [a1][a2]
-        const C gb = quad ? Gs[(b1 + N / 2) * N + (b2 + N / 2)] : cmake<C>(0.0, 0.0);
-        const Real wbb = quad ? __ldg(bsl + (b1 + N) * E + (b2 + N)) : Real(0);
+        const C gb = g.quad ? Gs[(g.b1 + N / 2) * N + (g.b2 + N / 2)] : cmake<C>(0.0, 0.0);
+        const Real wbb = g.quad ? __ldg(bsl + (g.b1 + N) * E + (g.b2 + N)) : Real(0);
+        Real* Bs = reinterpret_cast<Real*>(slots + slot_bytes * buf);
+        C* Cpart = reinterpret_cast<C*>(Bs);   // reused after the sweep (split sums)
 
         // D_b(n) = eps (C + S) + quadratic term; Qacc[n] += G^_{n-b} D
         auto epilogue = [&](int n1, int n2, Real cx, Real cy, Real Sx, Real Sy) {
             C D = cmake<C>(eps_r * (cx + Sx), eps_r * (cy + Sy));
-            if (quad) {
-                const Real wq = __ldg(bsl + (n1 - b1 + N) * E + (n2 - b2 + N)) - wbb;
+            if (g.quad) {
+                const Real wq = __ldg(bsl + (n1 - g.b1 + N) * E + (n2 - g.b2 + N)) - wbb;
                 D.x = fma(wq, gb.x, D.x);
                 D.y = fma(wq, gb.y, D.y);
             }
             const int on = (n1 + N / 2) * N + (n2 + N / 2);
-            const C gk = Gs[(n1 - b1 + N / 2) * N + (n2 - b2 + N / 2)];
+            const C gk = Gs[(n1 - g.b1 + N / 2) * N + (n2 - g.b2 + N / 2)];
             AC::add(Qs + on, Qc + on, cmul(gk, D));
         };
 
-        // staged beta rectangle: a1 in [a1lo, a1lo + A1), a2 in [a2lo, a2lo + A2)
-        const int A1 = L1 + S1 - 1, a1lo = nlo1 - slo1 - S1 + 1;
-        const int A2 = RW * Gg + S2, a2lo = nlo2 - slo2 - S2;   // one spare column on the left
-        __syncthreads();   // readers of the previous item are done
+        __syncthreads();   // [A] the previous item is done with Pb, its slot and the accumulator entries
+        if (cubic && STAGE) {
+            if (DB) {
+                const int next = item + nblk;
+                if (next < A.count)
+                    stage_rect<Real, RW, NT>(reinterpret_cast<Real*>(slots + slot_bytes * (buf ^ 1)), A.beta,
+                                             A.items[next], N, WS);
+            } else if (item != blk) {
+                stage_rect<Real, RW, NT>(Bs, A.beta, ib, N, WS);
+            }
+            cp_async_commit();
+        }
+        const int S2e = (g.S2 + 1) & ~1;   // P_b row stride (even: 16-byte aligned rows)
         if (cubic) {
-            if (STAGE) {
-                for (int q = tid; q < A1 * A2; q += NT) {
-                    const int r = q / A2, c = q % A2;
-                    const int a1 = a1lo + r, a2 = a2lo + c;
-                    Real v = 0;
-                    if (a2 >= -N && a2 < N) v = __ldg(bsl + (a1 + N) * E + (a2 + N));
-                    Bs[r * WS + c] = v;
-                }
-            }
-            for (int q = tid; q < S1 * S2; q += NT) {
-                const int s1 = slo1 + q / S2, s2 = slo2 + q % S2;
+            for (int q = tid; q < g.S1 * g.S2; q += NT) {
+                const int s1 = g.slo1 + q / g.S2, s2 = g.slo2 + q % g.S2;
                 const C x = Gs[(s1 + N / 2) * N + (s2 + N / 2)];
-                const C y = Gs[(b1 - s1 + N / 2) * N + (b2 - s2 + N / 2)];
-                Pb[q] = cmul(x, y);
+                const C y = Gs[(g.b1 - s1 + N / 2) * N + (g.b2 - s2 + N / 2)];
+                Pb[(q / g.S2) * S2e + q % g.S2] = cmul(x, y);
             }
-            __syncthreads();
-            // S(b) = sum over box_s of W(b, s) P_b(s), W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b)
+            if (STAGE) {
+                if (DB) cp_async_wait<1>();   // this thread's copies of the current rectangle have landed
+                else cp_async_wait<0>();
+            }
+        }
+        __syncthreads();   // [B] Pb and the staged rectangle are visible
+
+        if (cubic) {
+            // S(b) = sum over box_s of W(b, s) P_b(s), reduced by every warp on its own (no barrier)
             Real sr = 0, si = 0;
             const Real* __restrict__ wrow = A.sw + (size_t)ib * nm;
-            for (int q = tid; q < S1 * S2; q += NT) {
-                const int s1 = slo1 + q / S2, s2 = slo2 + q % S2;
+            for (int q = lane; q < g.S1 * g.S2; q += 32) {
+                const int s1 = g.slo1 + q / g.S2, s2 = g.slo2 + q % g.S2;
                 const Real w = __ldg(wrow + (s1 + N / 2) * N + (s2 + N / 2));
-                const C p = Pb[q];
+                const C p = Pb[(q / g.S2) * S2e + q % g.S2];
                 sr = fma(w, p.x, sr);
                 si = fma(w, p.y, si);
             }
@@ -301,77 +373,73 @@ __global__ void __launch_bounds__(NT) k_fused2d(FusedArgs<Real> A) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if ((tid & 31) == 0) Sred[tid >> 5] = make_double2((double)sr, (double)si);
-            __syncthreads();
-            Real Sx = 0, Sy = 0;
-            for (int w = 0; w < NT / 32; ++w) { Sx += (Real)Sred[w].x; Sy += (Real)Sred[w].y; }
+            const Real Sx = sr, Sy = si;
 
-            // C_b over (s_1 chunk, row, group) tasks
-            const int base = L1 * Gg;
-            int J = base >= NT ? 1 : min(S1, NT / base);
-            const int chunk = (S1 + J - 1) / J;
-            J = (S1 + chunk - 1) / chunk;
+            // C_b over (s_1 chunk, row, group) tasks; lanes of a warp share the s_1 chunk (P_b loads
+            // are broadcasts) and differ in (row, group) (beta loads on distinct banks)
+            const int base = g.L1 * g.Gg;
+            int J = base >= NT ? 1 : min(g.S1, NT / base);
+            const int chunk = (g.S1 + J - 1) / J;
+            J = (g.S1 + chunk - 1) / chunk;
             const int ntask = base * J;   // <= NT whenever J > 1
             for (int task0 = 0; task0 < ntask; task0 += NT) {
                 const int task = task0 + tid;
                 Real ar[RW], ai[RW];
 #pragma unroll
                 for (int r = 0; r < RW; ++r) { ar[r] = 0; ai[r] = 0; }
-                int i = 0, g = 0;
+                int i = 0, gg = 0;
                 if (task < ntask) {
                     const int j = task / base;
-                    task_rc(task % base, Gg, i, g);
-                    const int n1 = nlo1 + i, n20 = nlo2 + RW * g;
-                    const int s1b = slo1 + j * chunk, s1e = min(slo1 + S1, s1b + chunk);
-                    if (i < L1) {
-                        for (int s1 = s1b; s1 < s1e; ++s1) {
-                            const C* __restrict__ prow = Pb + (s1 - slo1) * S2;
-                            if (STAGE) {
-                                const Real* __restrict__ brow = Bs + (n1 - s1 - a1lo) * WS;
-                                row_sweep<Real, RW>([&](int c) { return brow[c]; }, RW * g + S2, prow, S2, ar, ai);
-                            } else {
-                                const Real* __restrict__ brow = bsl + (n1 - s1 + N) * E;
-                                row_sweep<Real, RW>([&](int c) { return __ldg(brow + min(max(c, 0), E - 1)); },
-                                                    n20 - slo2 + N, prow, S2, ar, ai);
-                            }
+                    task_rc(task % base, g.Gg, i, gg);
+                    const int n1 = g.nlo1 + i, n20 = g.nlo2 + RW * gg;
+                    const int s1b = g.slo1 + j * chunk, s1e = min(g.slo1 + g.S1, s1b + chunk);
+                    for (int s1 = s1b; s1 < s1e; ++s1) {
+                        const C* __restrict__ prow = Pb + (s1 - g.slo1) * S2e;
+                        if (STAGE) {
+                            const Real* __restrict__ brow = Bs + (n1 - s1 - g.a1lo) * WS;
+                            row_sweep<Real, RW>([&](int c) { return brow[c]; }, RW * gg + g.S2, prow, g.S2, ar, ai);
+                        } else {
+                            const Real* __restrict__ brow = bsl + (n1 - s1 + N) * E;
+                            row_sweep<Real, RW>([&](int c) { return __ldg(brow + min(max(c, 0), E - 1)); },
+                                                n20 - g.slo2 + N, prow, g.S2, ar, ai);
                         }
                     }
                 }
                 if (J == 1) {
-                    if (task < ntask && i < L1) {
-                        const int n1 = nlo1 + i, n20 = nlo2 + RW * g;
+                    if (task < ntask) {
+                        const int n1 = g.nlo1 + i, n20 = g.nlo2 + RW * gg;
 #pragma unroll
                         for (int r = 0; r < RW; ++r) {
-                            if (n20 + r >= nlo2 + L2) break;
+                            if (n20 + r >= g.nlo2 + g.L2) break;
                             epilogue(n1, n20 + r, ar[r], ai[r], Sx, Sy);
                         }
                     }
                 } else {
-                    __syncthreads();   // every sweep is done with the staged rectangle: reuse it
+                    __syncthreads();   // every sweep is done with the staged rectangle: reuse its slot
                     if (task < ntask) {
 #pragma unroll
                         for (int r = 0; r < RW; ++r) Cpart[(size_t)task * RW + r] = cmake<C>(ar[r], ai[r]);
                     }
                     __syncthreads();
-                    for (int o = tid; o < L1 * L2; o += NT) {
-                        const int ii = o / L2, c = o % L2, gg = c / RW, r = c % RW;
+                    for (int o = tid; o < g.L1 * g.L2; o += NT) {
+                        const int ii = o / g.L2, c = o % g.L2, gq = c / RW, r = c % RW;
                         Real cx = 0, cy = 0;
                         for (int j = 0; j < J; ++j) {
-                            const int t = j * base + rc_task(ii, gg, Gg);
-                            const C v = Cpart[(size_t)t * RW + r];
+                            const C v = Cpart[((size_t)(j * base + ii * g.Gg + gq)) * RW + r];
                             cx += v.x;
                             cy += v.y;
                         }
-                        epilogue(nlo1 + ii, nlo2 + c, cx, cy, Sx, Sy);
+                        epilogue(g.nlo1 + ii, g.nlo2 + c, cx, cy, Sx, Sy);
                     }
                 }
             }
-        } else if (quad) {
-            for (int o = tid; o < L1 * L2; o += NT) epilogue(nlo1 + o / L2, nlo2 + o % L2, 0, 0, 0, 0);
+        } else if (g.quad) {
+            for (int o = tid; o < g.L1 * g.L2; o += NT) epilogue(g.nlo1 + o / g.L2, g.nlo2 + o % g.L2, 0, 0, 0, 0);
         }
     }
+    if (STAGE) cp_async_wait<0>();
     __syncthreads();
-    double2* out = A.partials + (size_t)blockIdx.x * nm;
+    double2* out = A.partials + (size_t)blk * nm;
     for (int i = tid; i < nm; i += NT) {
         const C v = Qs[i];
         if (AC::kComp) {
@@ -387,72 +455,158 @@ __global__ void __launch_bounds__(NT) k_fused2d(FusedArgs<Real> A) {
     }
 }
 
-// Fixed-order sum of the per-CTA partials into Q^ (deterministic): a block owns 32 modes; warp w
-// sums the partials c = w, w+8, ... of its lane's mode, then the 8 warp sums combine in order.
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+__global__ void __launch_bounds__(NT) k_fused2d(FusedArgs<Real> A) {
+    fused2d_body<Real, RW, NT, STAGE, DB>(A, blockIdx.x, gridDim.x);
+}
+
+// Many requests in one launch: CTAs [cta_begin[j], cta_begin[j+1]) serve request j with the same
+// CTA count (and hence the same partial sums) as its own launch, so a request's result does not
+// depend on what else is in the batch.  The dynamic shared memory is sized for the largest N.
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+__global__ void __launch_bounds__(NT) k_fused2d_batch(const FusedArgs<Real>* __restrict__ jobs,
+                                                      const int* __restrict__ cta_begin, int njobs) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cta_begin[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const FusedArgs<Real> A = jobs[lo];
+    fused2d_body<Real, RW, NT, STAGE, DB>(A, blockIdx.x - cta_begin[lo], cta_begin[lo + 1] - cta_begin[lo]);
+}
+
+// Fixed-order sum of the per-CTA partials into Q^ (deterministic): a block owns 8 modes; the 32
+// thread groups sum the partials c = w, w + 32, ... of their mode, then combine in order.
 __global__ void __launch_bounds__(256) k_sum_partials(int nm, int nPart, const double2* __restrict__ partials,
                                                       double2* __restrict__ out) {
-    __shared__ double2 sh[8][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
+    __shared__ double2 sh[32][8];
+    const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
+    const int i = blockIdx.x * 8 + m;
     double x = 0, y = 0;
     if (i < nm) {
-        for (int c = w; c < nPart; c += 8) {
+        for (int c = w; c < nPart; c += 32) {
             const double2 v = partials[(size_t)c * nm + i];
             x += v.x;
             y += v.y;
         }
     }
-    sh[w][lane] = make_double2(x, y);
+    sh[w][m] = make_double2(x, y);
     __syncthreads();
-    if (w == 0 && i < nm) {
+    if (threadIdx.x < 8 && i < nm) {
         double sx = 0, sy = 0;
-        for (int k = 0; k < 8; ++k) { sx += sh[k][lane].x; sy += sh[k][lane].y; }
+        for (int k = 0; k < 32; ++k) { sx += sh[k][m].x; sy += sh[k][m].y; }
         out[i] = make_double2(sx, sy);
     }
 }
 
-template <typename Real, int RW, int NT, bool STAGE>
-void launch_t(bn_solver* s, const cplx<Real>* G, const Real* beta) {
-    FusedArgs<Real> A;
+template <typename Real>
+void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.N = s->g.N;
     A.eps = s->eps;
-    A.G = G;
-    A.beta = beta;
+    A.G = sizeof(Real) == 4 ? (const cplx<Real>*)(const void*)s->Ghat32 : (const cplx<Real>*)(const void*)s->Ghat;
+    A.beta = sizeof(Real) == 4 ? (const Real*)(const void*)s->tabs->beta32 : (const Real*)(const void*)s->tabs->beta64;
     A.items = s->eps != 0.0 ? s->work.items : s->work_quad.items;
     A.count = s->eps != 0.0 ? s->work.count : s->work_quad.count;
     A.partials = s->partials;
     A.err = s->flags + 2;
-    A.sw = sizeof(Real) == 4 ? (const Real*)s->tabs->sw32 : (const Real*)s->tabs->sw64;
+    A.sw = sizeof(Real) == 4 ? (const Real*)(const void*)s->tabs->sw32 : (const Real*)(const void*)s->tabs->sw64;
     A.stamps = nullptr;
+}
+
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+void launch_t(bn_solver* s, const cplx<Real>* G, const Real* beta) {
+    FusedArgs<Real> A;
+    fill_args_t<Real>(s, A);
+    A.G = G;
+    A.beta = beta;
     if (s->prof && s->prof_slot < 8 && s->prof_stamps) {
         A.stamps = s->prof_stamps + 2 * s->prof_slot;
         cudaMemsetAsync(A.stamps, 0xFF, sizeof(unsigned long long), s->stream);
         cudaMemsetAsync(A.stamps + 1, 0, sizeof(unsigned long long), s->stream);
     }
-    const size_t smem = Layout2D<Real, RW, STAGE>::bytes(s->g.N, NT);
+    const size_t smem = Layout2D<Real, RW, STAGE, DB>::bytes(s->g.N, NT);
     const int grid = std::max(1, std::min(A.count, s->n_partials));
-    k_fused2d<Real, RW, NT, STAGE><<<grid, NT, smem, s->stream>>>(A);
-    k_sum_partials<<<(s->g.nModes + 31) / 32, 256, 0, s->stream>>>(s->g.nModes, grid, s->partials, s->Qhat);
+    k_fused2d<Real, RW, NT, STAGE, DB><<<grid, NT, smem, s->stream>>>(A);
+    k_sum_partials<<<(s->g.nModes + 7) / 8, 256, 0, s->stream>>>(s->g.nModes, grid, s->partials, s->Qhat);
     s->launches += 2;
 }
 
-template <typename Real, int RW, int NT, bool STAGE>
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
 void configure_one() {
-    cudaFuncSetAttribute(k_fused2d<Real, RW, NT, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_fused2d<Real, RW, NT, STAGE, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_fused2d_batch<Real, RW, NT, STAGE, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+}
+
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+void launch_group_t(cudaStream_t st, const void* d_jobs, const int* d_cta, int njobs, int total, int maxN) {
+    const size_t smem = Layout2D<Real, RW, STAGE, DB>::bytes(maxN, NT);
+    k_fused2d_batch<Real, RW, NT, STAGE, DB><<<total, NT, smem, st>>>((const FusedArgs<Real>*)d_jobs, d_cta, njobs);
 }
 
 }  // namespace
 
+// Double-buffered staging for mixed precision N <= 32 (3 CTAs/SM) or single buffer (4 CTAs/SM);
+// BN_FUSED_DB=0 selects the single buffer.
+static bool fused_db() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("BN_FUSED_DB");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Variants: mixed precision N <= 32: FP32, 8 outputs per thread, 256 threads, double-buffered
+// staging; mixed N = 64: single buffer (shared memory); FP64: 2 outputs per thread (DFMA-bound),
+// staged for N <= 32, read through L1 for N = 64.
 void configure_fused2d() {
-    configure_one<float, 8, 128, true>();
-    configure_one<float, 8, 256, true>();
-    configure_one<double, 2, 128, true>();
-    configure_one<double, 2, 256, false>();
+    configure_one<float, 8, 256, true, true>();
+    configure_one<float, 8, 256, true, false>();
+    configure_one<double, 2, 128, true, false>();
+    configure_one<double, 2, 256, false, false>();
 }
 
 size_t fused2d_smem(int N, int precision) {
-    if (precision == BN_MIXED) return N > 32 ? Layout2D<float, 8, true>::bytes(N, 256) : Layout2D<float, 8, true>::bytes(N, 128);
-    return N > 32 ? Layout2D<double, 2, false>::bytes(N, 256) : Layout2D<double, 2, true>::bytes(N, 128);
+    if (precision == BN_MIXED)
+        return N > 32 ? Layout2D<float, 8, true, false>::bytes(N, 256)
+                      : (fused_db() ? Layout2D<float, 8, true, true>::bytes(N, 256) : Layout2D<float, 8, true, false>::bytes(N, 256));
+    return N > 32 ? Layout2D<double, 2, false, false>::bytes(N, 256) : Layout2D<double, 2, true, false>::bytes(N, 128);
+}
+
+int fused2d_variant(const bn_solver* s) {
+    const bool big = s->g.N > 32;
+    if (s->opt.precision == BN_MIXED) return big ? 1 : 0;
+    return big ? 3 : 2;
+}
+
+void fill_fused_args(const bn_solver* s, void* out) {
+    if (s->opt.precision == BN_MIXED) fill_args_t<float>(s, *(FusedArgs<float>*)out);
+    else fill_args_t<double>(s, *(FusedArgs<double>*)out);
+}
+
+size_t fused2d_variant_smem(int variant, int N) {
+    switch (variant) {
+        case 0: return fused_db() ? Layout2D<float, 8, true, true>::bytes(N, 256) : Layout2D<float, 8, true, false>::bytes(N, 256);
+        case 1: return Layout2D<float, 8, true, false>::bytes(N, 256);
+        case 2: return Layout2D<double, 2, true, false>::bytes(N, 128);
+        default: return Layout2D<double, 2, false, false>::bytes(N, 256);
+    }
+}
+
+// One launch for a group of requests of the same variant; CTAs [d_cta[j], d_cta[j+1]) serve job j.
+void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,
+                          int maxN) {
+    switch (variant) {
+        case 0:
+            if (fused_db()) launch_group_t<float, 8, 256, true, true>(st, d_jobs, d_cta, njobs, total, maxN);
+            else launch_group_t<float, 8, 256, true, false>(st, d_jobs, d_cta, njobs, total, maxN);
+            break;
+        case 1: launch_group_t<float, 8, 256, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
+        case 2: launch_group_t<double, 2, 128, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
+        default: launch_group_t<double, 2, 256, false, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
+    }
 }
 
 // The 2-D operator: Q^ (s->Qhat) from the modes of the stage argument.
@@ -460,11 +614,12 @@ void launch_fused2d(bn_solver* s) {
     const bool mixed = s->opt.precision == BN_MIXED;
     const bool big = s->g.N > 32;
     if (mixed) {
-        if (big) launch_t<float, 8, 256, true>(s, s->Ghat32, s->tabs->beta32);
-        else launch_t<float, 8, 128, true>(s, s->Ghat32, s->tabs->beta32);
+        if (big) launch_t<float, 8, 256, true, false>(s, s->Ghat32, s->tabs->beta32);
+        else if (fused_db()) launch_t<float, 8, 256, true, true>(s, s->Ghat32, s->tabs->beta32);
+        else launch_t<float, 8, 256, true, false>(s, s->Ghat32, s->tabs->beta32);
     } else {
-        if (big) launch_t<double, 2, 256, false>(s, s->Ghat, s->tabs->beta64);
-        else launch_t<double, 2, 128, true>(s, s->Ghat, s->tabs->beta64);
+        if (big) launch_t<double, 2, 256, false, false>(s, s->Ghat, s->tabs->beta64);
+        else launch_t<double, 2, 128, true, false>(s, s->Ghat, s->tabs->beta64);
     }
 }
 

@@ -54,6 +54,24 @@ struct KernelTables {
     size_t bytes = 0;
 };
 
+// ---------------------------------------------------------------- fused 2-D operator arguments
+// One request of the fused 2-D kernel (bn_fused2d.cu).
+template <typename Real>
+struct FusedArgs {
+    int N;
+    double eps;              // 0: quadratic part only
+    const cplx<Real>* G;     // modes (N^2)
+    const Real* beta;        // [b][a] kernel-mode table
+    const int* items;        // b (flat extended index), descending work
+    int count;
+    double2* partials;       // [gridDim.x][N^2]
+    int* err;                // [0] set to 1 if a bounded wait gave up
+    unsigned long long* stamps;  // optional [2]: min start / max end %globaltimer (ns) over CTAs
+    const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
+};
+
+struct BatchPlan;
+
 // ---------------------------------------------------------------- triple-sum work list
 struct WorkList {
     int* items = nullptr;   // flat extended index of b, sorted by descending work
@@ -148,10 +166,26 @@ void launch_triple_sum(bn_solver* s);       // q1q from Ghat
 void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
 int triple_partials(const bn_solver* s);
 
+// batched stepping of 2-D solvers (bn_batch.cu)
+bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t st, BatchPlan** out, std::string* err);
+void destroy_plan(BatchPlan* p);
+bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts);
+bn_status replay_plan(BatchPlan* p, cudaStream_t st, int nsteps);
+long long plan_launches(const BatchPlan* p);
+bool plan_contains(const BatchPlan* p, const bn_solver* s);
+
 // fused 2-D operator (bn_fused2d.cu)
 void configure_fused2d();
 size_t fused2d_smem(int N, int precision);
 void launch_fused2d(bn_solver* s);   // s->Qhat from s->Ghat / s->Ghat32
+
+// batched launches (bn_fused2d.cu): variant 0 = mixed N <= 32, 1 = mixed N = 64,
+// 2 = FP64 N <= 32, 3 = FP64 N = 64
+int fused2d_variant(const bn_solver* s);
+void fill_fused_args(const bn_solver* s, void* out);   // FusedArgs<float> or <double> by precision
+size_t fused2d_variant_smem(int variant, int N);
+void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,
+                          int maxN);
 
 }  // namespace bn
 

@@ -55,3 +55,11 @@ def test_null_handles(lib):
     assert lib.bn_step_rk(None, 0.1, 1) == -1
     assert lib.bn_kernel_launches(None) == 0
     lib.bn_destroy_solver(None)
+
+
+def test_server_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.bn_server_create(0, 0, None, ctypes.byref(h)) == -1
+    assert lib.bn_server_submit(None, None, None, 0, None) == -1
+    assert lib.bn_server_poll(None, 1, None, None, 0, None, 0) == -1
+    lib.bn_server_destroy(None)

@@ -166,3 +166,24 @@ def test_conservation_projection(B):
     assert abs(Q.sum()) < 1e-13 * scale
     assert np.abs(np.tensordot(Q, v, axes=([0, 1], [0, 1]))).max() < 1e-13 * scale
     assert abs(np.sum(Q * np.sum(v * v, -1))) < 1e-13 * scale
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_modes_parity_2d_n64_sampled(B, precision, tol):
+    """Full-size 2-D N=64 (the largest serving size): GPU modes Q^_n against the oracle on a sampled
+    4x4 block of output modes (the oracle's direct sums are too slow for all 4096 outputs).  The
+    error is normalised by the classical gain modes of the same block."""
+    N, eps = 64, 1.0
+    f = I.two_gaussians(2, N, T6, 1.0, (1.5, 0.5), 0.8)
+    ora = O.Operator(2, N, T6, R6, 0, eps, M=2 * N)
+    Gh = ora.dft(f)
+    lo, cnt = -3, 4
+    Qh_o, gain_o, _, _ = ora.collision_modes(Gh, lo, cnt)
+    prec = B.FP64 if precision == "fp64" else B.MIXED
+    with B.Solver(2, N, T6, R6, B.MAXWELL, eps, precision=prec) as s:
+        s.set_state(f)
+        Qh_g = s.eval_collision_modes()
+    blk = Qh_g[lo + N // 2: lo + N // 2 + cnt, lo + N // 2: lo + N // 2 + cnt]
+    err = float(np.linalg.norm(blk - Qh_o) / np.linalg.norm(gain_o))
+    print(f"2-D N=64 {precision} sampled-mode error {err:.3e}")
+    assert err <= tol
