@@ -58,6 +58,22 @@ def lemma_terms_box(N: int, lo: int, cnt: int, cubic: bool) -> float:
     return float(q1.sum() ** 2 + (c1.sum() ** 2 if cubic else 0.0))
 
 
+def reduce_max_over_ranks(x: float, ws: int) -> float:
+    """Max of a per-rank float over all ranks (gloo all-reduce; identity for one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_max: float, ws: int) -> float:
+    """Weak-scaling throughput: the units all ranks processed divided by the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -213,13 +229,8 @@ def run_ours(args):
     ms, launches, prof, window = timed(solvers, args.steps, args.warmup, profile=True)
     clocks = clocks_sampler_stop(p, fh, clk_path, local, window)
     prof_boson = prof[1] if prof else None
-    total_ms = float(np.sum(ms))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * terms_step * args.steps / (total_ms * 1e-3)
+    total_ms = reduce_max_over_ranks(float(np.sum(ms)), ws)
+    value = whole_job_rate(terms_step * args.steps, total_ms * 1e-3, ws)
     ms_per_step = total_ms / args.steps
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
@@ -276,6 +287,10 @@ def run_ours(args):
     solves["solves_per_s_mixed"] = ws * 2.0 / solves["pair_solve_s_mixed"]
     solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
 
+    serving = None
+    if args.serving > 0:
+        serving = serving_sample(bn, I, args.serving, 200.0, args.serving_fp64)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(args.cpu_seconds)
@@ -297,11 +312,69 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "fp64": fp64,
             "solves": solves,
+            "serving": serving,
         }
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int):
+    """Continuous-batching server on a seeded stream of 2-D requests (the serving mix: N in {16, 32},
+    eps in {-1, 0, +1}, two-Gaussian data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2, mixed
+    precision), fed in real time from a host thread.  Reports p50/p99 time-to-solution, solves/s,
+    and the same requests (a stratified sample) solved one at a time in FP64 for solves/s and the
+    relative L2 difference of the final states."""
+    import threading
+    reqs = I.serving_requests(n=n_requests, rate=rate, Ns=(16, 32))
+    T = I.box_half_width(6.0)
+    f0s = [I.request_f0(r) for r in reqs]
+    ids = [None] * len(reqs)
+    with bn.Server(max_active=256) as srv:
+        def feeder():
+            t_start = time.perf_counter()
+            for k, r in enumerate(reqs):
+                delay = r["arrival"] - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                ids[k] = srv.submit(2, r["N"], T, r["R"], bn.MAXWELL, r["eps"], f0s[k], r["dt"], r["t_end"],
+                                    precision=bn.MIXED)
+        t0 = time.perf_counter()
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        srv.wait_idle(900)
+        wall = time.perf_counter() - t0
+        lat, results = [], []
+        for k, r in enumerate(reqs):
+            st, res, times = srv.poll(ids[k], r["N"] ** 2)
+            if st != 2:
+                raise RuntimeError(f"serving request {k} ended in state {st}")
+            lat.append(times[2] - times[0])
+            results.append(res)
+        stats = srv.stats()
+    # FP64 batch of one on a stratified sample (every k-th request)
+    step = max(1, len(reqs) // max(1, fp64_sample))
+    sample = list(range(0, len(reqs), step))[:fp64_sample]
+    t_fp = 0.0
+    rel = []
+    for k in sample:
+        r = reqs[k]
+        with bn.Solver(2, r["N"], T, r["R"], bn.MAXWELL, r["eps"], precision=bn.FP64) as s:
+            s.set_state(f0s[k])
+            a = time.perf_counter()
+            s.step_rk(r["dt"], int(round(r["t_end"] / r["dt"])))
+            ref = s.get_state().reshape(-1)
+            t_fp += time.perf_counter() - a
+        rel.append(float(np.linalg.norm(results[k] - ref) / np.linalg.norm(ref)))
+    lat = np.array(lat)
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "N": [16, 32], "precision": "mixed",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "solves_per_s": len(reqs) / wall, "wall_s": wall, "max_running": stats["max_active"],
+            "ticks": stats["ticks"],
+            "fp64_batch_of_one": {"requests": len(sample), "solves_per_s": len(sample) / t_fp,
+                                  "max_rel_l2_mixed_vs_fp64": max(rel)}}
 
 
 def cpu_baseline_sample(seconds: float):
@@ -375,6 +448,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=64, help="requests of the serving sample (0 = skip)")
+    ap.add_argument("--serving-fp64", type=int, default=6, help="requests re-solved one at a time in FP64")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
