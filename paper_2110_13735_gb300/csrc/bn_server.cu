@@ -89,6 +89,7 @@ struct bn_server {
     std::map<long long, ServerReq*> all;
     std::map<std::string, int> table_refs;   // operator key -> active requests using it
     long long next_id = 1;
+    int in_flight = 0;   // requests being admitted or retired outside the lock
     size_t bytes_in_use = 0;
     long long ticks = 0, admitted = 0, done = 0, failed = 0, max_seen_active = 0;
     Clock::time_point t0 = Clock::now();
@@ -124,6 +125,7 @@ void bn_server::retire(ServerReq* q, bool ok, const std::string& err) {
     }
     if (ok) done++;
     else failed++;
+    in_flight--;
     cv.notify_all();
 }
 
@@ -134,6 +136,7 @@ void bn_server::admit_locked(std::unique_lock<std::mutex>& lock) {
         const size_t need = solver_bytes(q->r) + (table_refs.count(key) ? 0 : table_bytes(q->r));
         if (bytes_in_use + need > budget && !active.empty()) break;   // wait for memory to free up
         pending.pop_front();
+        in_flight++;
         q->bytes = solver_bytes(q->r);
         bytes_in_use += need;
         table_refs[key]++;
@@ -146,7 +149,7 @@ void bn_server::admit_locked(std::unique_lock<std::mutex>& lock) {
             q->s = s;
             const std::string e = bn_last_error();
             lock.unlock();
-            retire(q, false, e);
+            retire(q, false, e);   // leaves in_flight to retire()
             lock.lock();
             continue;
         }
@@ -155,6 +158,7 @@ void bn_server::admit_locked(std::unique_lock<std::mutex>& lock) {
         q->t_admit = now();
         admitted++;
         active.push_back(q);
+        in_flight--;
         if ((long long)active.size() > max_seen_active) max_seen_active = (long long)active.size();
     }
 }
@@ -197,6 +201,7 @@ void bn_server::run() {
             if (q->steps_done >= q->steps_total) finished.push_back({q, true});
         }
         for (auto& fq : finished) active.erase(std::find(active.begin(), active.end(), fq.first));
+        in_flight += (int)finished.size();
         lock.unlock();
         for (auto& fq : finished) retire(fq.first, fq.second, fq.second ? "" : err);
         lock.lock();
@@ -285,7 +290,7 @@ bn_status bn_server_wait_idle(bn_server* S, double timeout_s) {
     if (!S) return sfail(BN_ERR_ARG, "null server");
     std::unique_lock<std::mutex> lock(S->mu);
     const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
-    while (!(S->pending.empty() && S->active.empty())) {
+    while (!(S->pending.empty() && S->active.empty() && S->in_flight == 0)) {
         if (S->cv.wait_until(lock, limit) == std::cv_status::timeout && Clock::now() >= limit)
             return sfail(BN_ERR_TIMEOUT, "server still busy at the timeout");
     }
