@@ -114,6 +114,31 @@ bn_status bn_eval_collision_device(bn_solver* s, const double* f_dev, double* Q_
  * prefactor), as interleaved (re, im) FP64 pairs: count = 2 N^d.  Synchronises. */
 bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count);
 
+/*
+ * Q_eps(f) of the device array f_dev into the device array Q_dev (both N^d FP64,
+ * on the solver's device), like bn_eval_collision_device but without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate while they evaluate -- cudaMalloc/cudaFree
+ * synchronise the whole device and fail when another allocator in the process
+ * (for instance a framework's caching allocator) has already reserved the
+ * memory -- and it also leaves the solver's own buffers untouched.
+ *
+ * Its working memory is one file-scope device array of 12 MiB that every
+ * device loading the library holds until the process exits; every 2-D solver
+ * (N <= 64) fits, larger needs are rejected with BN_ERR_ARG.  All calls in the
+ * process share that array and it keeps the last call's contents; each call
+ * clears what must start at zero.  Calls whose GPU work overlaps in time (other
+ * threads, other streams) race on it: serialise them.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), which is
+ * also when the driver loads the array onto that device; make that first call
+ * before any stream capture.  The solver's read-only kernel-mode
+ * tables, work lists and twiddles are used; the solver itself is not modified.
+ * 2-D solvers only (BN_ERR_UNSUPPORTED otherwise).  Runs on cuda_stream (NULL =
+ * legacy default stream) and returns when Q_dev holds the result.
+ */
+bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, double* Q_dev, size_t count,
+                                    void* cuda_stream);
+
 /* Advance the state by nsteps steps of size dt with the chosen integrator
  * (c = 1 in eq. Boltzmann_homo).  The steps run as one captured CUDA graph per
  * step.  If the state turns non-finite the call returns BN_ERR_NONFINITE and

@@ -66,6 +66,7 @@ def load(path: str | None = None):
     lib.bn_eval_collision.argtypes = [vp, dp, sz]
     lib.bn_eval_collision_device.argtypes = [vp, vp, vp, sz]
     lib.bn_eval_collision_modes.argtypes = [vp, dp, sz]
+    lib.bn_eval_collision_noalloc.argtypes = [vp, vp, vp, sz, vp]
     lib.bn_step_rk.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.bn_moments.argtypes = [vp, dp, sz]
     lib.bn_work_counts.argtypes = [vp, dp, sz]
@@ -185,6 +186,13 @@ class Solver:
         out = np.empty(2 * self.n_modes)
         _check(_lib.bn_eval_collision_modes(self._h, _dptr(out), out.size))
         return out.view(np.complex128).reshape(self.shape)
+
+    def eval_collision_noalloc(self, f_dev, Q_dev, stream=None):
+        """Q_eps(f_dev) into Q_dev without device allocation (include/bn.h: bn_eval_collision_noalloc)."""
+        raw = int(getattr(stream, "cuda_stream", stream)) if stream is not None else 0
+        _check(_lib.bn_eval_collision_noalloc(self._h, ctypes.c_void_p(f_dev.data_ptr()),
+                                              ctypes.c_void_p(Q_dev.data_ptr()), f_dev.numel(),
+                                              ctypes.c_void_p(raw) if raw else None))
 
     def eval_collision_device(self, f_dev, Q_dev):
         _check(_lib.bn_eval_collision_device(self._h, ctypes.c_void_p(f_dev.data_ptr()),

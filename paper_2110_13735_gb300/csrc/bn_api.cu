@@ -156,6 +156,10 @@ void harvest_profile(bn_solver* s, int slots) {
 
 }  // namespace
 
+namespace bn {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace bn
+
 extern "C" {
 
 bn_status bn_default_options(bn_options* opt) {

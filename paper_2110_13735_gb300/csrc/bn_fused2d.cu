@@ -575,6 +575,37 @@ size_t fused2d_smem(int N, int precision) {
     return N > 32 ? Layout2D<double, 2, false, false>::bytes(N, 256) : Layout2D<double, 2, true, false>::bytes(N, 128);
 }
 
+// The fused operator into caller-chosen scratch on a given stream (used by the no-allocation
+// entry point): G = the solver's precision copy of the modes, partials/Qhat/err in scratch.
+template <typename Real, int RW, int NT, bool STAGE, bool DB>
+void into_t(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err) {
+    FusedArgs<Real> A;
+    fill_args_t<Real>(s, A);
+    A.G = (const cplx<Real>*)G;
+    A.partials = partials;
+    A.err = err;
+    const size_t smem = Layout2D<Real, RW, STAGE, DB>::bytes(s->g.N, NT);
+    const int grid = std::max(1, std::min(A.count, s->n_partials));
+    k_fused2d<Real, RW, NT, STAGE, DB><<<grid, NT, smem, st>>>(A);
+    k_sum_partials<<<(s->g.nModes + 7) / 8, 256, 0, st>>>(s->g.nModes, grid, partials, Qhat);
+}
+
+void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err) {
+    switch (fused2d_variant(s)) {
+        case 0:
+            if (fused_db()) into_t<float, 8, 256, true, true>(s, st, G, partials, Qhat, err);
+            else into_t<float, 8, 256, true, false>(s, st, G, partials, Qhat, err);
+            break;
+        case 1: into_t<float, 8, 256, true, false>(s, st, G, partials, Qhat, err); break;
+        case 2: into_t<double, 2, 128, true, false>(s, st, G, partials, Qhat, err); break;
+        default: into_t<double, 2, 256, false, false>(s, st, G, partials, Qhat, err); break;
+    }
+}
+
+int fused2d_partials(const bn_solver* s) {
+    return std::max(1, std::min(s->eps != 0.0 ? s->work.count : s->work_quad.count, s->n_partials));
+}
+
 int fused2d_variant(const bn_solver* s) {
     const bool big = s->g.N > 32;
     if (s->opt.precision == BN_MIXED) return big ? 1 : 0;

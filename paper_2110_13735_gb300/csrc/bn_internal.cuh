@@ -159,6 +159,9 @@ void launch_heun_final(bn_solver* s, double* f, const double* y, const double* K
                        int* flags);
 void launch_moments(bn_solver* s, const double* f, double* out);
 void launch_conserve(bn_solver* s, double* Q);
+void launch_conserve_on(const bn_solver* s, double* Q, cudaStream_t st);
+void dft2_forward_into(const bn_solver* s, cudaStream_t st, const double* f, double2* work, double2* out, float2* out32);
+void dft2_inverse_real_into(const bn_solver* s, cudaStream_t st, const double2* in, double2* work, double* out);
 
 // sums (bn_sums.cu)
 void launch_pair_sums(bn_solver* s);        // S2, quad, red from Ghat
@@ -174,6 +177,9 @@ bn_status replay_plan(BatchPlan* p, cudaStream_t st, int nsteps);
 long long plan_launches(const BatchPlan* p);
 bool plan_contains(const BatchPlan* p, const bn_solver* s);
 
+// error message reported by bn_last_error() for the calling thread (bn_api.cu)
+void set_last_error(const std::string& msg);
+
 // fused 2-D operator (bn_fused2d.cu)
 void configure_fused2d();
 size_t fused2d_smem(int N, int precision);
@@ -182,6 +188,8 @@ void launch_fused2d(bn_solver* s);   // s->Qhat from s->Ghat / s->Ghat32
 // batched launches (bn_fused2d.cu): variant 0 = mixed N <= 32, 1 = mixed N = 64,
 // 2 = FP64 N <= 32, 3 = FP64 N = 64
 int fused2d_variant(const bn_solver* s);
+int fused2d_partials(const bn_solver* s);   // CTAs (partial sums) of the solver's fused launch
+void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err);
 void fill_fused_args(const bn_solver* s, void* out);   // FusedArgs<float> or <double> by precision
 size_t fused2d_variant_smem(int variant, int N);
 void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,

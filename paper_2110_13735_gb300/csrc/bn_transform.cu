@@ -282,6 +282,21 @@ void launch_dft_inverse_real(bn_solver* s, const double2* in, double* out, doubl
     s->launches++;
 }
 
+// 2-D transforms into caller-chosen buffers on a given stream (used by the no-allocation entry point).
+void dft2_forward_into(const bn_solver* s, cudaStream_t st, const double* f, double2* work, double2* out, float2* out32) {
+    const int N = s->g.N, n = s->g.nModes;
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, st>>>(nullptr, f, work, nullptr, nullptr, s->twiddle, N, n, 1, -1, 1.0);
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, st>>>(work, nullptr, out, out32, nullptr, s->twiddle, N, n, N, -1,
+                                                   1.0 / n);
+}
+
+void dft2_inverse_real_into(const bn_solver* s, cudaStream_t st, const double2* in, double2* work, double* out) {
+    const int N = s->g.N, n = s->g.nModes;
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, st>>>(in, nullptr, work, nullptr, nullptr, s->twiddle, N, n, N, +1, 1.0);
+    k_dft_axis<<<dft_blocks(n), kThreads, 0, st>>>(work, nullptr, nullptr, nullptr, out, s->twiddle, N, n, 1, +1,
+                                                   s->scale);
+}
+
 void launch_to_fp32(bn_solver* s, const double2* in, float2* out, int n) {
     k_to_fp32<<<blocks_for(n), kThreads, 0, s->stream>>>(in, out, n);
     s->launches++;
@@ -352,6 +367,46 @@ void launch_conserve(bn_solver* s, double* Q) {
     for (int i = 0; i < 25; ++i) ci.m[i] = inv[i];
     k_conserve<<<1, 1024, 0, s->stream>>>(d, N, s->T, ci, Q);
     s->launches++;
+}
+
+
+// The conservation projection on a given stream without touching the solver (no-allocation entry point).
+void launch_conserve_on(const bn_solver* s, double* Q, cudaStream_t st) {
+    const int d = s->g.d, N = s->g.N, nc = d + 2;
+    const double h = 2.0 * s->T / N;
+    // C C^T on the grid, then its inverse by Gauss-Jordan (host, FP64, (d+2)^2).
+    double G[25] = {0}, inv[25] = {0};
+    for (int idx = 0; idx < s->g.nModes; ++idx) {
+        double v[3] = {0, 0, 0};
+        int r = idx;
+        for (int i = d - 1; i >= 0; --i) { v[i] = h * (r % N - N / 2); r /= N; }
+        double psi[5];
+        psi[0] = 1.0;
+        for (int c = 0; c < d; ++c) psi[1 + c] = v[c];
+        psi[1 + d] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        for (int a = 0; a < nc; ++a)
+            for (int b = 0; b < nc; ++b) G[a * nc + b] += psi[a] * psi[b];
+    }
+    for (int a = 0; a < nc; ++a) inv[a * nc + a] = 1.0;
+    for (int c = 0; c < nc; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < nc; ++r)
+            if (std::fabs(G[r * nc + c]) > std::fabs(G[piv * nc + c])) piv = r;
+        for (int k = 0; k < nc; ++k) {
+            std::swap(G[c * nc + k], G[piv * nc + k]);
+            std::swap(inv[c * nc + k], inv[piv * nc + k]);
+        }
+        const double p = G[c * nc + c];
+        for (int k = 0; k < nc; ++k) { G[c * nc + k] /= p; inv[c * nc + k] /= p; }
+        for (int r = 0; r < nc; ++r) {
+            if (r == c) continue;
+            const double m = G[r * nc + c];
+            for (int k = 0; k < nc; ++k) { G[r * nc + k] -= m * G[c * nc + k]; inv[r * nc + k] -= m * inv[c * nc + k]; }
+        }
+    }
+    ConsInv ci;
+    for (int i = 0; i < 25; ++i) ci.m[i] = inv[i];
+    k_conserve<<<1, 1024, 0, st>>>(d, N, s->T, ci, Q);
 }
 
 }  // namespace bn
