@@ -130,6 +130,7 @@ struct Layout2D {
         b += nm * sizeof(cplx<Real>);                                        // Gs
         b += (size_t)N * (N + 2) * sizeof(cplx<Real>);                      // Pb (rows padded to even length)
         b += slot(N, nt) * (DB ? 2 : 1);                                     // beta rectangle(s) / split sums
+        b += 32 * sizeof(cplx<Real>);                                        // S(b) warp sums
         b += 16;                                                             // mbarrier
         return b;
     }
@@ -190,11 +191,15 @@ __device__ __forceinline__ void stage_rect(Real* Bs, const Real* __restrict__ be
     const ItemGeo<RW> g(ib, N);
     const int E = 2 * N, nExt = E * E;
     const Real* __restrict__ bsl = beta + (size_t)ib * nExt;
-    for (int q = threadIdx.x; q < g.A1 * g.A2; q += NT) {
-        const int r = q / g.A2, c = q % g.A2;
-        const int a1 = g.a1lo + r, a2 = g.a2lo + c;
-        const bool ok = a2 >= -N && a2 < N;
-        cp_async_elem(Bs + r * WS + c, bsl + (a1 + N) * E + (ok ? a2 + N : 0), ok);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = w; r < g.A1; r += NT / 32) {
+        const Real* __restrict__ src = bsl + (g.a1lo + r + N) * E + N;   // row a1, column a2 = 0
+        Real* dst = Bs + r * WS;
+        for (int c = lane; c < g.A2; c += 32) {
+            const int a2 = g.a2lo + c;
+            const bool ok = a2 >= -N && a2 < N;
+            cp_async_elem(dst + c, src + (ok ? a2 : 0), ok);
+        }
     }
 }
 
@@ -277,7 +282,8 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
     C* Pb = Gs + nm;
     unsigned char* slots = reinterpret_cast<unsigned char*>(Pb + N * (N + 2));
     const size_t slot_bytes = LY::slot(N, NT);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(slots + slot_bytes * (DB ? 2 : 1));
+    C* Sred = reinterpret_cast<C*>(slots + slot_bytes * (DB ? 2 : 1));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Sred + 32);
     const int tid = threadIdx.x, lane = tid & 31;
     const bool cubic = A.eps != 0.0;
     const Real eps_r = (Real)A.eps;
@@ -344,11 +350,14 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
         }
         const int S2e = (g.S2 + 1) & ~1;   // P_b row stride (even: 16-byte aligned rows)
         if (cubic) {
-            for (int q = tid; q < g.S1 * g.S2; q += NT) {
-                const int s1 = g.slo1 + q / g.S2, s2 = g.slo2 + q % g.S2;
-                const C x = Gs[(s1 + N / 2) * N + (s2 + N / 2)];
-                const C y = Gs[(g.b1 - s1 + N / 2) * N + (g.b2 - s2 + N / 2)];
-                Pb[(q / g.S2) * S2e + q % g.S2] = cmul(x, y);
+            for (int r = tid >> 5; r < g.S1; r += NT / 32) {
+                const int s1 = g.slo1 + r;
+                const C* __restrict__ gx = Gs + (s1 + N / 2) * N + N / 2;
+                const C* __restrict__ gy = Gs + (g.b1 - s1 + N / 2) * N + N / 2 + g.b2;
+                for (int c = lane; c < g.S2; c += 32) {
+                    const int s2 = g.slo2 + c;
+                    Pb[r * S2e + c] = cmul(gx[s2], gy[-s2]);
+                }
             }
             if (STAGE) {
                 if (DB) cp_async_wait<1>();   // this thread's copies of the current rectangle have landed
@@ -358,22 +367,28 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
         __syncthreads();   // [B] Pb and the staged rectangle are visible
 
         if (cubic) {
-            // S(b) = sum over box_s of W(b, s) P_b(s), reduced by every warp on its own (no barrier)
-            Real sr = 0, si = 0;
-            const Real* __restrict__ wrow = A.sw + (size_t)ib * nm;
-            for (int q = lane; q < g.S1 * g.S2; q += 32) {
-                const int s1 = g.slo1 + q / g.S2, s2 = g.slo2 + q % g.S2;
-                const Real w = __ldg(wrow + (s1 + N / 2) * N + (s2 + N / 2));
-                const C p = Pb[(q / g.S2) * S2e + q % g.S2];
-                sr = fma(w, p.x, sr);
-                si = fma(w, p.y, si);
-            }
+            // S(b) = sum over box_s of W(b, s) P_b(s): warp w takes the rows s_1 = slo1 + w, w + NW, ...;
+            // the warp sums are combined after the next barrier
+            {
+                Real sr = 0, si = 0;
+                const Real* __restrict__ wrow = A.sw + (size_t)ib * nm;
+                for (int r = tid >> 5; r < g.S1; r += NT / 32) {
+                    const Real* __restrict__ wr = wrow + (g.slo1 + r + N / 2) * N + N / 2;
+                    for (int c = lane; c < g.S2; c += 32) {
+                        const Real w = __ldg(wr + g.slo2 + c);
+                        const C p = Pb[r * S2e + c];
+                        sr = fma(w, p.x, sr);
+                        si = fma(w, p.y, si);
+                    }
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                si += __shfl_xor_sync(0xffffffffu, si, o);
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) Sred[tid >> 5] = cmake<C>(sr, si);
             }
-            const Real Sx = sr, Sy = si;
+            Real Sx = 0, Sy = 0;   // read from Sred after the barrier that follows the sweeps
 
             // C_b over (s_1 chunk, row, group) tasks; lanes of a warp share the s_1 chunk (P_b loads
             // are broadcasts) and differ in (row, group) (beta loads on distinct banks)
@@ -406,6 +421,10 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
                     }
                 }
                 if (J == 1) {
+                    __syncthreads();   // the warp sums of S(b) are visible
+                    Sx = 0;
+                    Sy = 0;
+                    for (int w = 0; w < NT / 32; ++w) { Sx += Sred[w].x; Sy += Sred[w].y; }
                     if (task < ntask) {
                         const int n1 = g.nlo1 + i, n20 = g.nlo2 + RW * gg;
 #pragma unroll
@@ -421,20 +440,24 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
                         for (int r = 0; r < RW; ++r) Cpart[(size_t)task * RW + r] = cmake<C>(ar[r], ai[r]);
                     }
                     __syncthreads();
-                    for (int o = tid; o < g.L1 * g.L2; o += NT) {
-                        const int ii = o / g.L2, c = o % g.L2, gq = c / RW, r = c % RW;
-                        Real cx = 0, cy = 0;
-                        for (int j = 0; j < J; ++j) {
-                            const C v = Cpart[((size_t)(j * base + ii * g.Gg + gq)) * RW + r];
-                            cx += v.x;
-                            cy += v.y;
+                    for (int w = 0; w < NT / 32; ++w) { Sx += Sred[w].x; Sy += Sred[w].y; }
+                    for (int ii = tid >> 5; ii < g.L1; ii += NT / 32) {
+                        for (int c = lane; c < g.L2; c += 32) {
+                            const int gq = c / RW, r = c % RW;
+                            Real cx = 0, cy = 0;
+                            for (int j = 0; j < J; ++j) {
+                                const C v = Cpart[((size_t)(j * base + ii * g.Gg + gq)) * RW + r];
+                                cx += v.x;
+                                cy += v.y;
+                            }
+                            epilogue(g.nlo1 + ii, g.nlo2 + c, cx, cy, Sx, Sy);
                         }
-                        epilogue(g.nlo1 + ii, g.nlo2 + c, cx, cy, Sx, Sy);
                     }
                 }
             }
         } else if (g.quad) {
-            for (int o = tid; o < g.L1 * g.L2; o += NT) epilogue(g.nlo1 + o / g.L2, g.nlo2 + o % g.L2, 0, 0, 0, 0);
+            for (int ii = tid >> 5; ii < g.L1; ii += NT / 32)
+                for (int c = lane; c < g.L2; c += 32) epilogue(g.nlo1 + ii, g.nlo2 + c, 0, 0, 0, 0);
         }
     }
     if (STAGE) cp_async_wait<0>();
