@@ -74,6 +74,10 @@ typedef struct {
     int integrator;   /* 0 = classical RK4, 1 = SSP-RK2 (Heun) */
     int quad3d;       /* 3-D theta rule: 0 = Gauss-Legendre in cos(theta),
                          1 = the printed sin(theta_p)-weighted rectangle rule */
+    double escalate_at; /* mixed precision only: when |eps| max f >= escalate_at after a
+                         bn_step_rk / bn_step_rk_batch call (near Fermi saturation or
+                         condensation onset), the solver switches to FP64 for the rest of its
+                         life; 0 = never */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
@@ -179,6 +183,11 @@ long long bn_kernel_launches(const bn_solver* s);
 bn_status bn_profile_enable(bn_solver* s, int enable);
 bn_status bn_profile_read(bn_solver* s, double* out, size_t count);
 
+/* Precision state: *precision = BN_FP64 or BN_MIXED now in use; *t_escalated = the
+ * time at which a mixed-precision solver switched to FP64 (-1 if it has not);
+ * *max_f = max_j f_j after the last step (|eps| max f is what escalate_at tests). */
+bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* bn_last_error(void);
 
@@ -188,6 +197,12 @@ const char* bn_last_error(void);
  * and precision; each must have a state.  All run on the stream of solvers[0].
  * Stops at the first non-finite solver (status BN_ERR_NONFINITE, *failed set
  * to its index, its state rolled back); others keep their progress.
+ * When two or more 2-D solvers share an integrator, one captured graph advances
+ * all of them and each operator evaluation is one launch of the fused kernel
+ * per precision group.  If profiling is enabled on solvers[0], the kernel span
+ * of those launches (first CTA start to last CTA end over every request of the
+ * evaluation, %globaltimer) is added to solvers[0]'s bn_profile_read out[2..3],
+ * one entry per evaluation, for every step of the call.
  */
 bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int nsteps, int* failed);
 

@@ -32,7 +32,7 @@ class BNError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
-                ("quad3d", ctypes.c_int)]
+                ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -70,6 +70,7 @@ def load(path: str | None = None):
     lib.bn_step_rk.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.bn_moments.argtypes = [vp, dp, sz]
     lib.bn_work_counts.argtypes = [vp, dp, sz]
+    lib.bn_precision_state.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
     lib.bn_kernel_launches.argtypes = [vp]
     lib.bn_kernel_launches.restype = ctypes.c_longlong
     lib.bn_last_error.restype = ctypes.c_char_p
@@ -106,10 +107,11 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0) -> Options:
+def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
+            escalate_at=0.0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
-    o.c_phi, o.integrator, o.quad3d = c_phi, integrator, quad3d
+    o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     return o
 
 
@@ -210,6 +212,12 @@ class Solver:
         out = np.empty(4)
         _check(_lib.bn_work_counts(self._h, _dptr(out), out.size))
         return out
+
+    def precision_state(self):
+        """(precision in use, time of the switch to FP64 or -1, max f after the last step)."""
+        p, t, m = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib.bn_precision_state(self._h, ctypes.byref(p), ctypes.byref(t), ctypes.byref(m)))
+        return p.value, t.value, m.value
 
     def kernel_launches(self) -> int:
         return int(_lib.bn_kernel_launches(self._h))

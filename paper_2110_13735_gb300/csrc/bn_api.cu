@@ -127,6 +127,25 @@ bn_status ensure_graph(bn_solver* s, double dt) {
 
 bool valid_solver(const bn_solver* s) { return s != nullptr; }
 
+// After a stepping call: read max f; switch a mixed-precision solver to FP64 for good when
+// |eps| max f reaches opt.escalate_at (its captured step graphs are rebuilt on the next call).
+void check_escalation(bn_solver* s) {
+    unsigned long long bits;
+    std::memcpy(&bits, s->flags_host + 4, sizeof bits);
+    double mf;
+    std::memcpy(&mf, &bits, sizeof mf);
+    if (s->flags_host[1] > 0) s->last_max_f = mf;
+    if (s->opt.precision == BN_MIXED && s->opt.escalate_at > 0 && std::fabs(s->eps) * s->last_max_f >= s->opt.escalate_at) {
+        s->opt.precision = BN_FP64;
+        s->t_escalated = s->t;
+        if (s->step_graph) {
+            cudaGraphExecDestroy(s->step_graph);
+            s->step_graph = nullptr;
+        }
+        drop_plans_with(s);
+    }
+}
+
 // Accumulate the durations of the triple-sum launches recorded by the last graph replay
 // or direct evaluation (the stream has been synchronised).
 void harvest_profile(bn_solver* s, int slots) {
@@ -209,6 +228,10 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(BN_ERR_ARG, "integrator must be 0 (RK4) or 1 (SSP-RK2)");
     }
+    if (!(s->opt.escalate_at >= 0.0) || !std::isfinite(s->opt.escalate_at)) {
+        delete s;
+        return fail(BN_ERR_ARG, "escalate_at must be finite and >= 0");
+    }
     if (s->opt.M <= 0) s->opt.M = 2 * N;
     if (s->opt.M1 <= 0) s->opt.M1 = N / 2;
     if (s->opt.M2 <= 0) s->opt.M2 = N / 2;
@@ -262,8 +285,8 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     alloc((void**)&s->partials, (size_t)s->n_partials * n * sizeof(double2));
     alloc((void**)&s->Qhat, n * sizeof(double2));
     alloc((void**)&s->moments, 16 * sizeof(double));
-    alloc((void**)&s->flags, 4 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->flags_host, 4 * sizeof(int));
+    alloc((void**)&s->flags, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->flags_host, 8 * sizeof(int));
     if (e != cudaSuccess) {
         bn_status r = cuda_fail(e, "device buffers");
         free_buffers(s);
@@ -272,7 +295,7 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return r;
     }
-    cudaMemsetAsync(s->flags, 0, 4 * sizeof(int), s->stream);
+    cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream);
     cudaMemsetAsync(s->Qhat, 0, n * sizeof(double2), s->stream);
     {
         // twiddles e^{-2 i pi m / N} in FP64 on the host (one table per solver)
@@ -392,17 +415,19 @@ bn_status bn_step_rk(bn_solver* s, double dt, int nsteps) {
     bn_status st = ensure_graph(s, dt);
     if (st != BN_OK) return st;
     cudaError_t e = cudaMemsetAsync(s->flags, 0, 2 * sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->flags + 4, 0, 2 * sizeof(int), s->stream);
     for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
         e = cudaGraphLaunch(s->step_graph, s->stream);
         s->launches += s->graph_launches;
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->flags_host, s->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_rk");
     harvest_profile(s, s->prof_slots_used);
     if (s->flags_host[2] != 0) return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during step_rk");
     const int committed = s->flags_host[1];
     s->t += committed * dt;
+    check_escalation(s);
     if (s->flags_host[0] != 0) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "state became non-finite at step %d of %d; state kept at t = %.17g", committed + 1,
@@ -437,6 +462,14 @@ bn_status bn_work_counts(const bn_solver* s, double* out, size_t count) {
 }
 
 long long bn_kernel_launches(const bn_solver* s) { return s ? s->launches : 0; }
+
+bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f) {
+    if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
+    if (precision) *precision = s->opt.precision;
+    if (t_escalated) *t_escalated = s->t_escalated;
+    if (max_f) *max_f = s->last_max_f;
+    return BN_OK;
+}
 
 bn_status bn_profile_enable(bn_solver* s, int enable) {
     if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
@@ -488,8 +521,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
         if (!(dts[i] > 0) || !std::isfinite(dts[i])) return fail(BN_ERR_ARG, "dt must be > 0");
         for (int j = 0; j < i; ++j)
             if (solvers[j] == solvers[i]) return fail(BN_ERR_ARG, "a solver appears twice in the batch");
-        if (solvers[i]->g.d != 2 || solvers[i]->opt.integrator != solvers[0]->opt.integrator || solvers[i]->prof)
-            shared = false;
+        if (solvers[i]->g.d != 2 || solvers[i]->opt.integrator != solvers[0]->opt.integrator) shared = false;
     }
     if (nsteps == 0) return BN_OK;
     cudaStream_t st0 = solvers[0]->stream;
@@ -503,18 +535,22 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
             cudaStreamWaitEvent(st0, ev, 0);
             cudaEventDestroy(ev);
         }
-    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(solvers[i]->flags + 4, 0, 2 * sizeof(int), st0);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
+    const bool timed = solvers[0]->prof;
+    bn::BatchPlan* plan = nullptr;
     if (shared) {
-        bn::BatchPlan* plan = nullptr;
         {
             std::lock_guard<std::mutex> lock(g_plan_mu);
             for (bn::BatchPlan* p : g_plans)
-                if (bn::plan_matches(p, solvers, n, dts)) { plan = p; break; }
+                if (bn::plan_matches(p, solvers, n, dts, timed)) { plan = p; break; }
         }
         if (!plan) {
             std::string err;
-            bn_status st = bn::build_plan(solvers, n, dts, st0, &plan, &err);
+            bn_status st = bn::build_plan(solvers, n, dts, timed, st0, &plan, &err);
             if (st != BN_OK) return fail(st, err);
             std::lock_guard<std::mutex> lock(g_plan_mu);
             g_plans.push_back(plan);
@@ -536,14 +572,23 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
             }
     }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st0);
+        e = cudaMemcpyAsync(solvers[i]->flags_host, solvers[i]->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
     if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
+    if (shared && timed) {
+        double ns = 0;
+        long long cnt = 0;
+        if (bn::plan_read_spans(plan, st0, &ns, &cnt)) {
+            solvers[0]->prof_ns_total += ns;
+            solvers[0]->prof_ns_count += cnt;
+        }
+    }
     bn_status result = BN_OK;
     for (int i = 0; i < n; ++i) {
         bn_solver* s = solvers[i];
         if (!shared) harvest_profile(s, s->prof_slots_used);
         s->t += s->flags_host[1] * dts[i];
+        check_escalation(s);
         if (s->flags_host[2] != 0 && result == BN_OK) {
             if (failed) *failed = i;
             result = fail(BN_ERR_TIMEOUT, "a bounded device wait gave up in the batch");

@@ -96,7 +96,21 @@ __global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stag
 }
 
 // Fixed-order sum of each job's partials into its Q^ (same order as the single-request kernel).
-__global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __restrict__ jobs) {
+// With `tm` (a timed plan), thread 0 of the first block also closes the timing of the fused
+// launches of this evaluation: tm[0..1] = (min start, max end) stamped by their CTAs are added to
+// the running total tm[2] and count tm[3], then reset for the next evaluation.  The fused kernels
+// have completed (stream order) and no other thread touches tm.
+__global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __restrict__ jobs,
+                                                            unsigned long long* __restrict__ tm) {
+    if (tm && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        const unsigned long long t0 = tm[0], t1 = tm[1];
+        if (t1 > t0) {
+            tm[2] += t1 - t0;
+            tm[3] += 1;
+        }
+        tm[0] = ~0ull;
+        tm[1] = 0;
+    }
     const ElemJob J = jobs[blockIdx.y];
     __shared__ double2 sh[32][8];
     const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
@@ -156,7 +170,15 @@ __global__ void k_heun_final_batch(const ElemJob* __restrict__ jobs) {
 __global__ void k_commit_batch(const ElemJob* __restrict__ jobs) {
     const ElemJob J = jobs[blockIdx.y];
     if (J.flags[0] != 0) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) J.f[i] = J.cand[i];
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) {
+        const double v = J.cand[i];
+        J.f[i] = v;
+        m = fmax(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(J.flags + 4), (unsigned long long)__double_as_longlong(m));
     if (blockIdx.x == 0 && threadIdx.x == 0) J.flags[1] += 1;
 }
 
@@ -175,6 +197,8 @@ struct BatchPlan {
     };
     std::vector<Group> groups;
     int maxN = 0, maxNm = 0;
+    bool timed = false;
+    unsigned long long* d_time = nullptr;   // [min start, max end, total ns, count] (timed plans)
     cudaGraphExec_t graph = nullptr;
     long long launches = 0;   // kernels per replay
 };
@@ -183,6 +207,7 @@ void destroy_plan(BatchPlan* p) {
     if (!p) return;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->d_elem);
+    cudaFree(p->d_time);
     for (auto& g : p->groups) {
         cudaFree(g.d_jobs);
         cudaFree(g.d_cta);
@@ -196,7 +221,7 @@ static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in) {
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
-    k_sum_partials_batch<<<dim3((p->maxNm + 7) / 8, nj), 256, 0, st>>>(p->d_elem);
+    k_sum_partials_batch<<<dim3((p->maxNm + 7) / 8, nj), 256, 0, st>>>(p->d_elem, p->d_time);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in);
     p->launches += 5 + (long long)p->groups.size();
@@ -209,10 +234,11 @@ static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in) {
         }
 }
 
-bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t st, BatchPlan** out,
+bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, cudaStream_t st, BatchPlan** out,
                      std::string* err) {
     BatchPlan* p = new BatchPlan();
     p->integrator = solvers[0]->opt.integrator;
+    p->timed = timed;
     std::vector<ElemJob> elem;
     std::map<int, std::vector<int>> by_variant;
     for (int i = 0; i < n; ++i) {
@@ -244,6 +270,11 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t
     }
     cudaError_t e = cudaMalloc(&p->d_elem, sizeof(ElemJob) * elem.size());
     if (e == cudaSuccess) e = cudaMemcpy(p->d_elem, elem.data(), sizeof(ElemJob) * elem.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && timed) {
+        const unsigned long long init[4] = {~0ull, 0ull, 0ull, 0ull};
+        e = cudaMalloc((void**)&p->d_time, sizeof init);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_time, init, sizeof init, cudaMemcpyHostToDevice);
+    }
     for (auto& kv : by_variant) {
         if (e != cudaSuccess) break;
         BatchPlan::Group g;
@@ -255,6 +286,8 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t
         for (size_t k = 0; k < kv.second.size(); ++k) {
             bn_solver* s = solvers[kv.second[k]];
             fill_fused_args(s, args.data() + asz * k);
+            if (mixed) reinterpret_cast<FusedArgs<float>*>(args.data() + asz * k)->stamps = p->d_time;
+            else reinterpret_cast<FusedArgs<double>*>(args.data() + asz * k)->stamps = p->d_time;
             cta.push_back(cta.back() + elem[kv.second[k]].nPart);
             g.maxN = std::max(g.maxN, s->g.N);
         }
@@ -316,8 +349,8 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t
     return BN_OK;
 }
 
-bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts) {
-    if (!p || (int)p->solvers.size() != n) return false;
+bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts, bool timed) {
+    if (!p || (int)p->solvers.size() != n || p->timed != timed) return false;
     for (int i = 0; i < n; ++i)
         if (p->solvers[i] != solvers[i] || p->dts[i] != dts[i]) return false;
     return true;
@@ -332,6 +365,19 @@ bn_status replay_plan(BatchPlan* p, cudaStream_t st, int nsteps) {
 }
 
 long long plan_launches(const BatchPlan* p) { return p ? p->launches : 0; }
+
+bool plan_read_spans(BatchPlan* p, cudaStream_t st, double* ns_total, long long* count) {
+    *ns_total = 0;
+    *count = 0;
+    if (!p || !p->d_time) return false;
+    unsigned long long h[4];
+    if (cudaMemcpyAsync(h, p->d_time, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return false;
+    if (cudaMemsetAsync(p->d_time + 2, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+    *ns_total = (double)h[2];
+    *count = (long long)h[3];
+    return true;
+}
 
 bool plan_contains(const BatchPlan* p, const bn_solver* s) {
     return p && std::find(p->solvers.begin(), p->solvers.end(), s) != p->solvers.end();

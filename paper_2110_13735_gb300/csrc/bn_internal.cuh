@@ -113,8 +113,10 @@ struct bn_solver {
     double2* partials = nullptr; // [n_partials][N^d]
     double2* Qhat = nullptr;     // combined modes
     double* moments = nullptr;   // d+6
-    int* flags = nullptr;        // [0]: non-finite, [1]: committed steps
-    int* flags_host = nullptr;   // pinned
+    int* flags = nullptr;        // [0] non-finite, [1] committed steps, [2] wait timeout, [4..5] max f (u64 bits)
+    int* flags_host = nullptr;   // pinned copy of the 8 flag words
+    double t_escalated = -1;     // time of the switch to FP64 (escalate_at), -1 if none
+    double last_max_f = 0;
 
     bool has_state = false;
     double t = 0;
@@ -170,9 +172,12 @@ void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
 int triple_partials(const bn_solver* s);
 
 // batched stepping of 2-D solvers (bn_batch.cu)
-bn_status build_plan(bn_solver** solvers, int n, const double* dts, cudaStream_t st, BatchPlan** out, std::string* err);
+bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, cudaStream_t st, BatchPlan** out,
+                     std::string* err);
 void destroy_plan(BatchPlan* p);
-bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts);
+bool plan_matches(const BatchPlan* p, bn_solver** solvers, int n, const double* dts, bool timed);
+// Summed fused-kernel spans (ns) and their count since the last read of a timed plan; resets them.
+bool plan_read_spans(BatchPlan* p, cudaStream_t st, double* ns_total, long long* count);
 bn_status replay_plan(BatchPlan* p, cudaStream_t st, int nsteps);
 long long plan_launches(const BatchPlan* p);
 bool plan_contains(const BatchPlan* p, const bn_solver* s);

@@ -104,10 +104,19 @@ __global__ void k_heun_final(int n, const double* __restrict__ f, const double* 
     if (bad) atomicOr(&flags[0], 1);
 }
 
-// f = candidate unless a non-finite value has been seen in this call; counts committed steps.
+// f = candidate unless a non-finite value has been seen in this call; counts committed steps and
+// records max f (as the bit pattern of a non-negative double, which orders like the value).
 __global__ void k_commit(int n, double* __restrict__ f, const double* __restrict__ cand, int* __restrict__ flags) {
     if (flags[0] != 0) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) f[i] = cand[i];
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = cand[i];
+        f[i] = v;
+        m = fmax(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(flags + 4), (unsigned long long)__double_as_longlong(m));
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[1] += 1;
 }
 

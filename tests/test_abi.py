@@ -50,6 +50,17 @@ def test_create_rejects_bad_arguments_without_a_device(lib, args, status):
     assert not h.value
 
 
+def test_create_rejects_bad_escalation_threshold(lib):
+    for bad in (-0.5, float("nan"), float("inf")):
+        o = B.options(precision=B.MIXED, escalate_at=bad)
+        h = ctypes.c_void_p()
+        st = lib.bn_create_solver(2, 16, 13.3, 6.0, 0, 1.0, ctypes.byref(o), None, ctypes.byref(h))
+        assert st == -1, bad
+        assert b"escalate_at" in lib.bn_last_error()
+        assert not h.value
+    assert lib.bn_precision_state(None, None, None, None) == -1
+
+
 def test_null_handles(lib):
     assert lib.bn_set_state(None, None, 0) == -1
     assert lib.bn_step_rk(None, 0.1, 1) == -1
