@@ -41,6 +41,7 @@ class _Params(ctypes.Structure):
         ("d", ctypes.c_int), ("N", ctypes.c_int), ("T", ctypes.c_double), ("R", ctypes.c_double),
         ("kernel", ctypes.c_int), ("eps", ctypes.c_double), ("M", ctypes.c_int),
         ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("c_phi", ctypes.c_double), ("quad3d", ctypes.c_int),
+        ("Q", ctypes.c_int),
     ]
 
 
@@ -89,9 +90,10 @@ class Operator:
     """One collision operator: dimension, modes, box, truncation, kernel, eps.
 
     ``T`` is the velocity box half-width (the paper's L), ``R`` the truncation
-    radius in velocity units (the paper's S = R, Sec. 4.1), ``kernel`` 0 for 2-D
-    Maxwell molecules and 1 for 3-D hard spheres, ``eps`` = +1 bosons, -1
-    fermions, 0 classical (alpha = -eps in the paper's notation).
+    radius in velocity units (the paper's S = R, Sec. 4.1), ``kernel`` 0 for
+    Maxwell molecules (2-D) and 1 for hard spheres (3-D, and 2-D by reading r5 of
+    the C source with ``Q`` Gauss-Legendre points per radius), ``eps`` = +1
+    bosons, -1 fermions, 0 classical (alpha = -eps in the paper's notation).
     """
     d: int
     N: int
@@ -104,8 +106,11 @@ class Operator:
     M2: int = 0
     c_phi: float = 0.0
     quad3d: int = 0
+    Q: int = 0
 
     def __post_init__(self):
+        if self.Q == 0:
+            self.Q = self.N + 8
         if self.M == 0:
             self.M = 2 * self.N
         if self.M1 == 0:
@@ -133,7 +138,7 @@ class Operator:
 
     def _p(self):
         return _Params(self.d, self.N, self.T, self.R, self.kernel, self.eps, self.M, self.M1,
-                       self.M2, self.c_phi, self.quad3d)
+                       self.M2, self.c_phi, self.quad3d, self.Q)
 
     @property
     def n_modes(self) -> int:

@@ -35,6 +35,14 @@
  *        printed sin(theta_p)-weighted rectangle rule.
  *   (r4) Q_j is the real part of the inverse transform of Q^ (I_N is not
  *        symmetric, so Q^ is not exactly Hermitian).
+ *   (r5) 2-D hard spheres (gamma=1, b=1) are not covered by the paper's
+ *        separable expansion: Btilde(z,y) = 2 C_Phi sqrt(|z|^2+|y|^2) couples
+ *        the two radii.  The kernel modes are its definition (Lemma of Sec. 2.3)
+ *        with z = rho e_theta, y = rho' e_{theta+pi/2} on [0,pi) x [-R,R]^2,
+ *        the same rectangle rule in theta (M points) as the Maxwell case and a
+ *        Gauss-Legendre rule with Q points on [-R,R] in each radius; summing
+ *        over the rho nodes first leaves a separable sum over (theta_p, rho'_j)
+ *        with P = M Q terms.  Default Q = N + 8.
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC bn_oracle.c -o libbn_oracle.so -lm
  */
@@ -62,6 +70,7 @@ typedef struct {
     int M1, M2;     /* 3-D angular points (theta, phi) */
     double c_phi;   /* C_Phi */
     int quad3d;     /* 0: Gauss-Legendre in cos(theta); 1: printed rectangle rule */
+    int Q;          /* 2-D hard spheres: Gauss-Legendre points per radius (reading r5) */
 } ora_params;
 
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
@@ -103,7 +112,10 @@ static void gauss_legendre(int n, double* x, double* w) {
 }
 
 /* Number of quadrature terms P and the constant C of eq. betadD. */
-int ora_num_terms(const ora_params* p) { return p->d == 2 ? p->M : p->M1 * p->M2; }
+int ora_num_terms(const ora_params* p) {
+    if (p->d == 2) return p->kernel == 1 ? p->M * p->Q : p->M;
+    return p->M1 * p->M2;
+}
 
 /*
  * alpha_p(a), alpha'_p(a) on the extended mode box a in [-N, N-1]^d
@@ -115,6 +127,40 @@ int ora_num_terms(const ora_params* p) { return p->d == 2 ? p->M : p->M1 * p->M2
 int ora_alpha_tables(const ora_params* p, double* alpha, double* alphap) {
     const int d = p->d, N = p->N, E = 2 * N, nE = ipow(E, d);
     const double Rxi = M_PI * p->R / p->T;   /* truncation radius on [-pi,pi]^d */
+    if (d == 2 && p->kernel == 1) {
+        /* 2-D hard spheres (reading r5):
+         *   beta(k,l) = 2 C_Phi int_0^pi dth int int_{[-R,R]^2} sqrt(rho^2+rho'^2)
+         *               e^{i rho k.e_th} e^{i rho' l.e_{th+pi/2}} drho drho'
+         * (the imaginary part vanishes on the symmetric nodes), so with the nodes
+         * (rho_i, w_i) and theta_q = q pi / M:
+         *   alpha_{q,j}(k) = (pi/M) 2 C_Phi w_j sum_i w_i sqrt(rho_i^2+rho_j^2) cos(rho_i k.e_q),
+         *   alpha'_{q,j}(l) = cos(rho_j l.e_{q+pi/2}). */
+        const int M = p->M, Qn = p->Q;
+        double* x = (double*)malloc(sizeof(double) * Qn);
+        double* w = (double*)malloc(sizeof(double) * Qn);
+        gauss_legendre(Qn, x, w);
+        for (int i = 0; i < Qn; ++i) { x[i] *= Rxi; w[i] *= Rxi; }
+        for (int q = 0; q < M; ++q) {
+            double th = q * M_PI / M;
+            double c = cos(th), s = sin(th);
+            double cp = cos(th + 0.5 * M_PI), sp = sin(th + 0.5 * M_PI);
+            for (int j = 0; j < Qn; ++j) {
+                size_t row = (size_t)(q * Qn + j) * nE;
+                for (int i0 = 0; i0 < E; ++i0)
+                    for (int i1 = 0; i1 < E; ++i1) {
+                        double a0 = i0 - N, a1 = i1 - N;
+                        int ia = i0 * E + i1;
+                        double ke = a0 * c + a1 * s, le = a0 * cp + a1 * sp;
+                        double h = 0.0;
+                        for (int i = 0; i < Qn; ++i) h += w[i] * sqrt(x[i] * x[i] + x[j] * x[j]) * cos(x[i] * ke);
+                        alpha[row + ia] = (M_PI / M) * 2.0 * p->c_phi * w[j] * h;
+                        alphap[row + ia] = cos(x[j] * le);
+                    }
+            }
+        }
+        free(x); free(w);
+        return 0;
+    }
     if (d == 2) {
         /* 2-D Maxwell (gamma=0, b=1): Btilde = 2 C_Phi, a = 2 C_Phi, b = 1;
          * alpha_p(k) = 2C_Phi phi(k.e_p), alpha'_p(l) = phi(l.e_{p+pi/2}), C = pi/M. */

@@ -29,11 +29,14 @@ def _integrand(G0, G1, G2, G3, alpha):
 
 
 def carleman_2d(Ghat, N, R, Btilde, alpha, xi, n_theta=128, n_rho=48):
+    """``Btilde`` is a constant (Maxwell molecules) or a function of (|x|, |y|) on the node grid
+    (hard spheres: 2 C_Phi sqrt(|x|^2 + |y|^2))."""
     K = _modes(2, N)
     g = np.asarray(Ghat).reshape(-1) * np.exp(1j * (K @ np.asarray(xi, float)))
     G0 = g.sum()
     x, w = np.polynomial.legendre.leggauss(n_rho)
     rho, wr = R * x, R * w
+    Bw = Btilde(np.abs(rho)[:, None], np.abs(rho)[None, :]) if callable(Btilde) else Btilde
     total = 0.0 + 0.0j
     for t in np.arange(n_theta) * np.pi / n_theta:
         e = np.array([np.cos(t), np.sin(t)])
@@ -43,8 +46,8 @@ def carleman_2d(Ghat, N, R, Btilde, alpha, xi, n_theta=128, n_rho=48):
         G1 = (A @ g)[:, None]
         G2 = (B @ g)[None, :]
         G3 = (A[:, None, :] * B[None, :, :]) @ g
-        total += wr @ _integrand(G0, G1, G2, G3, alpha) @ wr
-    return Btilde * (np.pi / n_theta) * total
+        total += wr @ (Bw * _integrand(G0, G1, G2, G3, alpha)) @ wr
+    return (np.pi / n_theta) * total
 
 
 def carleman_3d(Ghat, N, R, Btilde, alpha, xi, n_mu=16, n_phi=32, n_rho=12, n_r=12, n_t=32):

@@ -56,6 +56,21 @@ def test_beta_closed_forms_2d():
         assert op.beta_at((0, 0), k) == pytest.approx(exact, rel=1e-11, abs=1e-13)
 
 
+def test_beta_hard_spheres_2d_closed_form_and_order():
+    """2-D hard spheres (reading r5): beta(0,0) = 2 C_Phi pi int int_{[-R,R]^2} sqrt(x^2+y^2)
+    = 2 C_Phi pi (4 R^3 / 3)(sqrt 2 + asinh 1).  The tensor Gauss-Legendre rule meets it at
+    third order (the integrand has a conical point at the origin): the error falls ~8x per
+    doubling of Q and is below 1e-6 at Q = 96."""
+    exact = None
+    errs = []
+    for Q in (24, 48, 96):
+        op = O.Operator(2, 4, T6, R6, 1, 0.0, M=16, Q=Q)
+        exact = 2 * op.c_phi * math.pi * (4 * RXI ** 3 / 3) * (math.sqrt(2) + math.asinh(1))
+        errs.append(abs(op.beta_at((0, 0), (0, 0)) / exact - 1))
+    assert errs[2] < 1e-6
+    assert 5 < errs[0] / errs[1] < 12 and 5 < errs[1] / errs[2] < 12
+
+
 def test_beta_closed_forms_3d():
     """3-D hard spheres: beta(0,0) = 2 pi^2 R^4 Btilde, beta(k,0) = beta(0,k) =
     4 pi^2 R^2 Btilde (1-cos R|k|)/|k|^2 (Btilde = 4 C_Phi)."""
@@ -148,6 +163,27 @@ def test_brute_force_carleman_2d(eps):
         xi = rng.uniform(-np.pi, np.pi, 2)
         lemma = np.sum(Qh.reshape(-1) * np.exp(1j * (NN @ xi)))
         bf = carleman_2d(Gh, N, RXI, 2 * op.c_phi, -eps, xi)
+        assert abs(lemma - bf) <= 1e-11 * max(1.0, abs(bf))
+
+
+@pytest.mark.parametrize("eps", [0.0, 1.0, -1.0])
+def test_brute_force_carleman_2d_hard_spheres(eps):
+    """2-D hard spheres (reading r5), Btilde = 2 C_Phi sqrt(|x|^2+|y|^2): Lemma sums vs the
+    direct Carleman quadrature with the same radial rule.  Pins the (theta, rho') separable
+    form of the kernel modes, its weights and the square root."""
+    N = 8
+    op = O.Operator(2, N, T6, R6, 1, eps, M=64, Q=48)
+    Gh = _random_modes(2, N, 31 + int(10 * eps))
+    lo, cnt = -3 * N // 2, 3 * N - 2
+    Qh = op.collision_modes(Gh, lo, cnt)[0]
+    nn = np.arange(lo, lo + cnt)
+    NN = np.stack(np.meshgrid(nn, nn, indexing="ij"), -1).reshape(-1, 2)
+    rng = np.random.Generator(np.random.PCG64(5))
+    bt = lambda x, y: 2 * op.c_phi * np.sqrt(x * x + y * y)
+    for _ in range(2):
+        xi = rng.uniform(-np.pi, np.pi, 2)
+        lemma = np.sum(Qh.reshape(-1) * np.exp(1j * (NN @ xi)))
+        bf = carleman_2d(Gh, N, RXI, bt, -eps, xi, n_rho=48)
         assert abs(lemma - bf) <= 1e-11 * max(1.0, abs(bf))
 
 
@@ -307,6 +343,36 @@ def test_loss_term_gaussian_closed_form():
     _, _, loss3, _ = op3.eval_collision(f3, parts=True)
     exact3 = f3[8, 8, 8] * 4 * math.pi * op3.c_phi * rho * math.sqrt(8 * temp3 / math.pi)
     assert loss3[8, 8, 8] == pytest.approx(exact3, rel=2e-2)
+
+
+def test_loss_term_gaussian_closed_form_2d_hard_spheres():
+    """2-D hard spheres: Q^-(f)(0) = f(0) 2 pi C_Phi rho sqrt(pi T / 2) (the mean speed of a 2-D
+    Gaussian).  Pins gamma = 1 in (T/pi)^{d+gamma} for d = 2 and the hard-sphere beta(l,l).  The
+    tolerance 2e-2 covers the slower spectral convergence of the |v - v_*| weight on N = 16 (a
+    wrong gamma is off by T/pi ~ 4)."""
+    N, temp = 16, 3.0
+    op = O.Operator(2, N, T6, R6, 1, 0.0, M=32)
+    f = I.gaussian(2, N, T6, 1.0, temp)
+    _, _, loss, _ = op.eval_collision(f, parts=True)
+    exact = f[N // 2, N // 2] * 2 * math.pi * op.c_phi * math.sqrt(math.pi * temp / 2)
+    assert loss[N // 2, N // 2] == pytest.approx(exact, rel=2e-2)
+
+
+def test_hard_spheres_2d_mass_and_fermi_dirac_residual():
+    """The hard-sphere operator conserves mass to rounding, and a Fermi-Dirac equilibrium
+    (alpha = hbar^2, hbar = 3) is a near-zero of it with the right sign of eps only."""
+    d, hbar, L, sig = 2, 3.0, 6.0, 1.0
+    alpha = hbar ** d
+    z = EQ.fugacity(d, "FD", 1.0, sig, alpha)
+    Rv = 2 * L / (3 + math.sqrt(2))
+    op = O.Operator(2, 16, L, Rv, 1, -alpha, M=16)
+    f = EQ.quantum_maxwellian(op.velocities(), "FD", z, sig, alpha)
+    Q, gain, _, _ = op.eval_collision(f, parts=True)
+    assert abs(Q.sum()) <= 1e-13 * np.abs(gain).sum()
+    res = np.abs(Q).max()
+    assert res < 1e-1 * np.abs(gain).max()
+    wrong = O.Operator(2, 16, L, Rv, 1, alpha, M=16).eval_collision(f)
+    assert np.abs(wrong).max() > 10.0 * res
 
 
 # --------------------------------------------------------------------------- moments
