@@ -13,12 +13,13 @@
  *                      - alpha sum_{k+l+m=n} [beta(k+m,l+m) + beta(l,m)
  *                                             - beta(l+m,l) - beta(l,l+m)] G^_k G^_l G^_m
  *               with alpha = -eps, k,l,m,n in I_N, no wrap-around       (Lemma, Sec. 2.3; step 2(c))
- *   kernel      beta(a,b) = C sum_p alpha_p(a) alpha'_p(b)                (Sec. 2.5, eq. betadD)
+ *   kernel      beta(a,b) = C sum_p alpha_p(a) alpha'_p(b)                (Sec. 2.5, eq. betadD;
+ *               2-D hard spheres: the Lemma's definition of beta^R by quadrature)
  *   scaling     Q_eps(f)(v_j) = (T/pi)^{d+gamma} Re sum_n Q^_n exp(2 i pi n.j/N)   (Sec. 3.2)
  *
  * eps = +1 bosons, -1 fermions, 0 classical particles (any real eps is
- * accepted, e.g. eps = -hbar^d).  Kernels: 2-D Maxwell molecules (gamma = 0)
- * and 3-D hard spheres (gamma = 1), b == 1, truncation radius R in velocity
+ * accepted, e.g. eps = -hbar^d).  Kernels: 2-D Maxwell molecules (gamma = 0),
+ * 2-D and 3-D hard spheres (gamma = 1), b == 1, truncation radius R in velocity
  * units with R_xi = pi R / T satisfying R_xi (3 + sqrt 2) <= 2 pi (Sec. 4.1).
  *
  * Conventions (all entry points):
@@ -65,7 +66,9 @@ typedef enum { BN_FP64 = 0, BN_MIXED = 1 } bn_precision;
 
 typedef struct {
     int M;            /* 2-D angular points of eq. beta2D; 0 = default 2N */
-    int M1, M2;       /* 3-D (theta, phi) points of eq. beta3D; 0 = default N/2 each */
+    int M1, M2;       /* 3-D (theta, phi) points of eq. beta3D; 0 = default N/2 each.
+                         2-D hard spheres: M1 = Gauss-Legendre points per radius of the
+                         kernel-mode quadrature (default N + 8); M2 unused */
     int precision;    /* BN_FP64, or BN_MIXED: FP32 bulk pair/triple sums with
                          compensated accumulation, FP64 kernel modes, transforms,
                          combination, moments, conservation correction and state */
@@ -85,9 +88,9 @@ bn_status bn_default_options(bn_options* opt);
 
 /*
  * Create a solver for the operator (d, N, T, R, kernel, eps).  d in {2,3};
- * N even, 4 <= N <= 64 (2-D) or <= 48 (3-D); T > 0 the box half-width; R > 0
+ * N even, 4 <= N <= 64 (2-D) or <= 16 (3-D); T > 0 the box half-width; R > 0
  * the truncation radius (velocity units); kernel BN_MAXWELL (d = 2) or
- * BN_HARD_SPHERE (d = 3); opt may be NULL; cuda_stream is a cudaStream_t or
+ * BN_HARD_SPHERE (d = 2 or 3); opt may be NULL; cuda_stream is a cudaStream_t or
  * NULL.  Builds the kernel-mode tables in FP64 on the device (once per
  * solver; solvers with equal (d, N, R_xi, kernel, M, precision) share them).
  * On success *out owns the solver; release it with bn_destroy_solver.
@@ -185,7 +188,8 @@ bn_status bn_profile_read(bn_solver* s, double* out, size_t count);
 
 /* Precision state: *precision = BN_FP64 or BN_MIXED now in use; *t_escalated = the
  * time at which a mixed-precision solver switched to FP64 (-1 if it has not);
- * *max_f = max_j f_j after the last step (|eps| max f is what escalate_at tests). */
+ * *max_f = the largest max_j f_j at the end of any step of the last stepping call
+ * (|eps| max_f is what escalate_at tests after that call).  Any pointer may be NULL. */
 bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -200,8 +200,6 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     if (!(T > 0) || !(R > 0) || !std::isfinite(T) || !std::isfinite(R)) return fail(BN_ERR_ARG, "T and R must be > 0");
     if (!std::isfinite(eps)) return fail(BN_ERR_ARG, "eps must be finite");
     if (kernel != BN_MAXWELL && kernel != BN_HARD_SPHERE) return fail(BN_ERR_ARG, "unknown kernel");
-    if (d == 2 && kernel != BN_MAXWELL)
-        return fail(BN_ERR_UNSUPPORTED, "2-D hard spheres: the kernel is not separable (no formula in the paper)");
     if (d == 3 && kernel != BN_HARD_SPHERE) return fail(BN_ERR_UNSUPPORTED, "3-D supports hard spheres only");
     const double Rxi = M_PI * R / T;
     if (Rxi * (3.0 + std::sqrt(2.0)) > 2.0 * M_PI * (1.0 + 1e-12))
@@ -233,11 +231,17 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         return fail(BN_ERR_ARG, "escalate_at must be finite and >= 0");
     }
     if (s->opt.M <= 0) s->opt.M = 2 * N;
-    if (s->opt.M1 <= 0) s->opt.M1 = N / 2;
-    if (s->opt.M2 <= 0) s->opt.M2 = N / 2;
     if (s->opt.c_phi <= 0) s->opt.c_phi = d == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI);
-    if (d == 2) { s->opt.M1 = s->opt.M2 = 0; s->opt.quad3d = 0; }
-    else s->opt.M = 0;
+    if (d == 2) {
+        // 2-D hard spheres: M1 = Gauss-Legendre points per radius (default N + 8)
+        s->opt.M1 = kernel == BN_HARD_SPHERE ? (s->opt.M1 > 0 ? s->opt.M1 : N + 8) : 0;
+        s->opt.M2 = 0;
+        s->opt.quad3d = 0;
+    } else {
+        if (s->opt.M1 <= 0) s->opt.M1 = N / 2;
+        if (s->opt.M2 <= 0) s->opt.M2 = N / 2;
+        s->opt.M = 0;
+    }
     s->scale = std::pow(T / M_PI, d + (kernel == BN_HARD_SPHERE ? 1 : 0));
 
     cudaError_t e = cudaGetDevice(&s->device);

@@ -57,7 +57,8 @@ size_t solver_bytes(const bn_request& r) {
 // Bytes of the kernel-mode tables of an operator (mirrors acquire_tables).
 size_t table_bytes(const bn_request& r) {
     const size_t N = (size_t)r.N, nExt = r.d == 2 ? 4 * N * N : 8 * N * N * N, nm = r.d == 2 ? N * N : N * N * N;
-    const size_t P = r.d == 2 ? (size_t)(r.opt.M > 0 ? r.opt.M : 2 * r.N)
+    const size_t M2d = (size_t)(r.opt.M > 0 ? r.opt.M : 2 * r.N);
+    const size_t P = r.d == 2 ? (r.kernel == BN_HARD_SPHERE ? M2d * (size_t)(r.opt.M1 > 0 ? r.opt.M1 : r.N + 8) : M2d)
                               : (size_t)(r.opt.M1 > 0 ? r.opt.M1 : r.N / 2) * (r.opt.M2 > 0 ? r.opt.M2 : r.N / 2);
     size_t b = 2 * P * nExt * sizeof(double) + nExt * nExt * (sizeof(double) + sizeof(float));
     if (r.d == 2) b += nExt * nm * (sizeof(double) + sizeof(float));

@@ -39,10 +39,17 @@ __device__ __forceinline__ double psi3_d(double R, double q) {
     return 2.0 * M_PI * R * j1(x) / q;
 }
 
-// Quadrature node: direction e (2-D: e_theta, e2 unused) and weight (2-D: pi/M).
+// Quadrature node: direction e and weight.  2-D Maxwell: e_theta, e2 unused, w = pi/M.
+// 2-D hard spheres: e_theta, e2 = rho'_j, w = (pi/M) w_j.  3-D: e on the half sphere.
 struct Node { double e0, e1, e2, w; };
 
-__global__ void k_alpha_tables(int d, int N, int P, double Rxi, double c_phi, const Node* __restrict__ nodes,
+// alpha_p(a), alpha'_p(a) for every node p and a in the extended box.  2-D hard spheres
+// (gamma = 1, not covered by the separable expansion of Sec. 2.5): the kernel modes are the
+// Lemma's definition with Btilde = 2 C_Phi sqrt(rho^2 + rho'^2), z = rho e_theta,
+// y = rho' e_{theta+pi/2}, Gauss-Legendre nodes `rad` (x = rho_i, y = weight) on [-R, R] in
+// each radius; the sum over rho_i is taken here, leaving beta = sum over (theta, rho'_j).
+__global__ void k_alpha_tables(int d, int N, int P, double Rxi, double c_phi, int kernel, int nrad,
+                               const double2* __restrict__ rad, const Node* __restrict__ nodes,
                                double* __restrict__ alpha, double* __restrict__ alphap) {
     const int E = 2 * N;
     const int nExt = d == 2 ? E * E : E * E * E;
@@ -51,7 +58,19 @@ __global__ void k_alpha_tables(int d, int N, int P, double Rxi, double c_phi, co
          idx += (long long)gridDim.x * blockDim.x) {
         const int p = (int)(idx / nExt), ia = (int)(idx % nExt);
         const Node nd = nodes[p];
-        if (d == 2) {
+        if (d == 2 && kernel == 1) {
+            const double a0 = ia / E - N, a1 = ia % E - N;
+            const double ke = a0 * nd.e0 + a1 * nd.e1;
+            const double le = -a0 * nd.e1 + a1 * nd.e0;
+            const double rj2 = nd.e2 * nd.e2;
+            double h = 0.0;
+            for (int i = 0; i < nrad; ++i) {
+                const double2 r = rad[i];
+                h = fma(r.y * sqrt(fma(r.x, r.x, rj2)), cos(r.x * ke), h);
+            }
+            alpha[idx] = nd.w * 2.0 * c_phi * h;
+            alphap[idx] = cos(nd.e2 * le);
+        } else if (d == 2) {
             const double a0 = ia / E - N, a1 = ia % E - N;
             // alpha_p(k) = 2 C_Phi phi(k.e_p), alpha'_p(l) = phi(l.e_{p+pi/2}); C = pi/M folded into alpha.
             const double ke = a0 * nd.e0 + a1 * nd.e1;
@@ -69,18 +88,56 @@ __global__ void k_alpha_tables(int d, int N, int P, double Rxi, double c_phi, co
     }
 }
 
-// beta[ib][ia] = sum_p alpha_p(a) alpha'_p(b) (eq. betadD), FP64, plus an FP32 copy.
-__global__ void k_beta_table(int nExt, int P, const double* __restrict__ alpha, const double* __restrict__ alphap,
-                             double* __restrict__ beta64, float* __restrict__ beta32) {
-    const long long total = (long long)nExt * nExt;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int ib = (int)(idx / nExt), ia = (int)(idx % nExt);
-        double s = 0.0;
-        for (int p = 0; p < P; ++p) s = fma(alpha[(size_t)p * nExt + ia], alphap[(size_t)p * nExt + ib], s);
-        beta64[idx] = s;
-        beta32[idx] = (float)s;
+// beta[ib][ia] = sum_p alpha_p(a) alpha'_p(b) (eq. betadD), FP64, plus an FP32 copy.  A product
+// of the (P x nExt) tables over p: each 256-thread CTA forms a 64 x 64 tile of (b, a) with 4 x 4
+// entries per thread, staging 16 nodes of both tables per step in shared memory.  Every entry
+// sums over p in increasing order with FP64 fused multiply-adds.
+constexpr int kBT = 64, kBK = 16;
+__global__ void __launch_bounds__(256) k_beta_table(int nExt, int P, const double* __restrict__ alpha,
+                                                    const double* __restrict__ alphap, double* __restrict__ beta64,
+                                                    float* __restrict__ beta32) {
+    __shared__ double As[kBK][kBT];   // alpha_p(a), a in the tile
+    __shared__ double Bs[kBK][kBT];   // alpha'_p(b), b in the tile
+    const int a0 = blockIdx.x * kBT, b0 = blockIdx.y * kBT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int p0 = 0; p0 < P; p0 += kBK) {
+        for (int t = threadIdx.x; t < kBK * kBT; t += 256) {
+            const int k = t / kBT, c = t % kBT;
+            const bool okp = p0 + k < P;
+            As[k][c] = okp && a0 + c < nExt ? alpha[(size_t)(p0 + k) * nExt + a0 + c] : 0.0;
+            Bs[k][c] = okp && b0 + c < nExt ? alphap[(size_t)(p0 + k) * nExt + b0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) av[j] = As[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) bv[i] = Bs[k][ty + 16 * i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[j], bv[i], acc[i][j]);
+        }
+        __syncthreads();
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + ty + 16 * i, a = a0 + tx + 16 * j;
+            if (a < nExt && b < nExt) {
+                const size_t idx = (size_t)b * nExt + a;
+                beta64[idx] = acc[i][j];
+                beta32[idx] = (float)acc[i][j];
+            }
+        }
 }
 
 // Reducible weights W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b) for s, b-s in I_N (2-D),
@@ -134,7 +191,7 @@ std::string table_key(const bn_solver* s) {
     std::ostringstream os;
     os.precision(17);
     os << s->device << ":" << s->g.d << ":" << s->g.N << ":" << s->Rxi << ":" << s->kernel << ":";
-    if (s->g.d == 2) os << s->opt.M;
+    if (s->g.d == 2) os << s->opt.M << "r" << (s->kernel == BN_HARD_SPHERE ? s->opt.M1 : 0);
     else os << s->opt.M1 << "x" << s->opt.M2 << ":" << s->opt.quad3d;
     os << ":" << s->opt.c_phi;
     return os.str();
@@ -156,7 +213,18 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     t->g = s->g;
     const int d = s->g.d, nExt = s->g.nExt;
     std::vector<Node> nodes;
-    if (d == 2) {
+    std::vector<double2> rad;
+    if (d == 2 && s->kernel == BN_HARD_SPHERE) {
+        const int M = s->opt.M, Qr = s->opt.M1;
+        std::vector<double> x, w;
+        gauss_legendre_rule(Qr, x, w);
+        for (int i = 0; i < Qr; ++i) rad.push_back(make_double2(s->Rxi * x[i], s->Rxi * w[i]));
+        for (int p = 0; p < M; ++p) {
+            double th = p * M_PI / M;
+            for (int j = 0; j < Qr; ++j)
+                nodes.push_back(Node{std::cos(th), std::sin(th), rad[j].x, (M_PI / M) * rad[j].y});
+        }
+    } else if (d == 2) {
         const int M = s->opt.M;
         for (int p = 0; p < M; ++p) {
             double th = p * M_PI / M;
@@ -184,8 +252,10 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     t->P = (int)nodes.size();
     const size_t nAl = (size_t)t->P * nExt, nBeta = (size_t)nExt * nExt;
     Node* d_nodes = nullptr;
+    double2* d_rad = nullptr;
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&d_nodes, sizeof(Node) * nodes.size());
+    if (e == cudaSuccess && !rad.empty()) e = cudaMalloc(&d_rad, sizeof(double2) * rad.size());
     if (e == cudaSuccess) e = cudaMalloc(&t->alpha64, sizeof(double) * nAl);
     if (e == cudaSuccess) e = cudaMalloc(&t->alphap64, sizeof(double) * nAl);
     if (e == cudaSuccess) e = cudaMalloc(&t->beta64, sizeof(double) * nBeta);
@@ -196,6 +266,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
         cudaFree(d_nodes);
+        cudaFree(d_rad);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
         cudaFree(t->sw64); cudaFree(t->sw32);
         delete t;
@@ -204,9 +275,11 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     }
     t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw);
     cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
-    k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, d_nodes, t->alpha64,
-                                               t->alphap64);
-    k_beta_table<<<4096, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
+    if (d_rad) cudaMemcpyAsync(d_rad, rad.data(), sizeof(double2) * rad.size(), cudaMemcpyHostToDevice, s->stream);
+    k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, s->kernel, (int)rad.size(),
+                                               d_rad, d_nodes, t->alpha64, t->alphap64);
+    const dim3 gb((nExt + kBT - 1) / kBT, (nExt + kBT - 1) / kBT);
+    k_beta_table<<<gb, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
     s->launches += 2;
     if (nSw) {
         k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
@@ -214,6 +287,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     }
     e = cudaStreamSynchronize(s->stream);
     cudaFree(d_nodes);
+    cudaFree(d_rad);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);

@@ -38,7 +38,6 @@ def test_default_options_and_last_error(lib):
     ((2, 128, 13.3, 6.0, 0, 0.0), -8),     # N too large
     ((2, 16, 13.0, 6.0, 0, 0.0), -2),      # anti-aliasing violated (T < (3+sqrt2) R / 2)
     ((2, 16, -1.0, 6.0, 0, 0.0), -1),      # T
-    ((2, 16, 13.3, 6.0, 1, 0.0), -8),      # 2-D hard spheres
     ((3, 8, 13.3, 6.0, 0, 0.0), -8),       # 3-D Maxwell
     ((2, 16, 13.3, 6.0, 7, 0.0), -1),      # unknown kernel
     ((2, 16, 13.3, 6.0, 0, float("nan")), -1),

@@ -105,9 +105,10 @@ def test_server_admission_by_memory(B):
 
 
 def test_server_failed_request(B):
-    """A request the library rejects (2-D hard spheres) fails alone; the others complete."""
+    """A request the library rejects (box too small for R: the anti-aliasing condition fails at
+    solver creation) fails alone; the others complete."""
     with B.Server(max_active=4) as srv:
-        bad = srv.submit(2, 16, T6, R6, B.HARD_SPHERE, 1.0, _f0(16, 0), 0.01, 0.02)
+        bad = srv.submit(2, 16, 13.0, R6, B.MAXWELL, 1.0, _f0(16, 0), 0.01, 0.02)
         good = srv.submit(2, 16, T6, R6, B.MAXWELL, 1.0, _f0(16, 0), 0.01, 0.02)
         srv.wait_idle(300)
         assert srv.poll(bad)[0] == 3

@@ -72,6 +72,24 @@ def test_eval_parity_3d_fp64(B, N, eps):
     assert rel(Q_g, Q_o, gain) <= 1e-12
 
 
+@pytest.mark.parametrize("N,eps,kind,precision", [(8, -1.0, "rand", "fp64"), (16, 1.0, "gauss", "fp64"),
+                                                  (16, 0.0, "two", "fp64"), (10, 2.5, "rand", "fp64"),
+                                                  (16, -1.0, "two", "mixed"), (24, 1.0, "gauss", "mixed")])
+def test_eval_parity_2d_hard_spheres(B, N, eps, kind, precision):
+    """2-D hard spheres: kernel modes by quadrature of their definition (M = 2N angles, N + 8
+    Gauss-Legendre points per radius on both sides)."""
+    f = _f0(2, N, kind)
+    ora = O.Operator(2, N, T6, R6, 1, eps)
+    Q_o, gain, _, _ = ora.eval_collision(f, parts=True)
+    prec = B.FP64 if precision == "fp64" else B.MIXED
+    with B.Solver(2, N, T6, R6, B.HARD_SPHERE, eps, precision=prec) as s:
+        s.set_state(f)
+        Q_g = s.eval_collision()
+    err = rel(Q_g, Q_o, gain)
+    print(f"2-D hard spheres e_Q (N={N}, eps={eps}, {precision}) = {err:.3e}")
+    assert err <= (1e-12 if precision == "fp64" else 2e-6)
+
+
 @pytest.mark.parametrize("N,eps,kind", [(16, -1.0, "two"), (32, 1.0, "gauss")])
 def test_eval_mixed_precision_error(B, N, eps, kind):
     f = _f0(2, N, kind)
