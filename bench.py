@@ -252,6 +252,7 @@ def run_ours(args):
     # quadratic terms (0.1% of the work) are not counted.
     flops_launch = 4.0 * (2.0 * (N_MODES ** 3 - N_MODES) / 3.0) ** 2
     peak = SM_COUNT * FP32_LANES * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
+    kcfg = solvers[1].kernel_config()
     kern_ms, basis = None, None
     if prof and prof[3] > 0 and prof[2] > 0:
         kern_ms, basis = prof[2] / prof[3], "kernel %globaltimer span (first CTA start to last CTA end) of every launch in the timed steps"
@@ -259,7 +260,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": recorded_traffic(),
-                "kernel": "k_fused2d_batch<float,8,256> (whole 2-D operator, both requests of one evaluation)",
+                "kernel": f"k_mixed2d_batch<{kcfg[0]}> (whole 2-D operator, both requests of one evaluation; "
+                          f"{kcfg[0]} outputs/thread chosen by the autotuner, {kcfg[1]} CTAs per request)",
                 "launches_timed": int(prof[3]) if prof else 0, "ms_per_launch": kern_ms,
                 "timing": basis,
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts, max clock)"}
@@ -269,23 +271,27 @@ def run_ours(args):
         s.close()
 
     # ---- FP64 beside it (fewer steps)
-    solvers64, _ = make_pair(bn, I, bn.FP64, stream)
-    k64 = max(3, args.steps // 4)
-    ms64, _, _, _ = timed(solvers64, k64, min(args.warmup, 3))
-    for s in solvers64:
-        s.close()
-    ms64_step = float(np.mean(ms64))
-    fp64 = {"value": terms_step / (ms64_step * 1e-3) * ws, "unit": UNIT, "ms_per_step": ms64_step, "steps": k64}
+    fp64, ms64_step = None, None
+    if not args.no_fp64:
+        solvers64, _ = make_pair(bn, I, bn.FP64, stream)
+        k64 = max(3, args.steps // 4)
+        ms64, _, _, _ = timed(solvers64, k64, min(args.warmup, 3))
+        for s in solvers64:
+            s.close()
+        ms64_step = float(np.mean(ms64))
+        fp64 = {"value": terms_step / (ms64_step * 1e-3) * ws, "unit": UNIT, "ms_per_step": ms64_step, "steps": k64}
 
     steps_to_end = {k: int(round(v / DT)) for k, v in T_END.items()}
-    solves = {"pair_solve_s_mixed": ms_per_step * max(steps_to_end.values()) / 1e3,
-              "pair_solve_s_fp64": ms64_step * max(steps_to_end.values()) / 1e3}
+    solves = {"pair_solve_s_mixed": ms_per_step * max(steps_to_end.values()) / 1e3}
     solves["solves_per_s_mixed"] = ws * 2.0 / solves["pair_solve_s_mixed"]
-    solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
+    if ms64_step is not None:
+        solves["pair_solve_s_fp64"] = ms64_step * max(steps_to_end.values()) / 1e3
+        solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
 
     serving = None
     if args.serving > 0:
-        serving = serving_sample(bn, I, args.serving, 200.0, args.serving_fp64)
+        serving = serving_sample(bn, I, args.serving, 200.0, args.serving_fp64,
+                                 Ns=(16, 32, 64) if args.serving_n64 else (16, 32))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -316,14 +322,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int):
-    """Continuous-batching server on a seeded stream of 2-D requests (the serving mix: N in {16, 32},
-    eps in {-1, 0, +1}, two-Gaussian data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2, mixed
-    precision), fed in real time from a host thread.  Reports p50/p99 time-to-solution, solves/s,
-    and the same requests (a stratified sample) solved one at a time in FP64 for solves/s and the
-    relative L2 difference of the final states."""
+def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32)):
+    """Continuous-batching server on a seeded stream of 2-D requests (the serving mix: N in `Ns`,
+    eps in {-1, 0, +1}, Maxwell molecules or hard spheres, two-Gaussian data, Poisson arrivals at
+    `rate`/s, RK4 dt=0.01 to t=2, mixed precision), fed in real time from a host thread.  Reports
+    p50/p99 time-to-solution, solves/s, and the same requests (a stratified sample) solved one at a
+    time in FP64 for solves/s and the relative L2 difference of the final states."""
     import threading
-    reqs = I.serving_requests(n=n_requests, rate=rate, Ns=(16, 32))
+    reqs = I.serving_requests(n=n_requests, rate=rate, Ns=Ns, kernels=(0, 1))
     T = I.box_half_width(6.0)
     f0s = [I.request_f0(r) for r in reqs]
     ids = [None] * len(reqs)
@@ -334,7 +340,7 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int):
                 delay = r["arrival"] - (time.perf_counter() - t_start)
                 if delay > 0:
                     time.sleep(delay)
-                ids[k] = srv.submit(2, r["N"], T, r["R"], bn.MAXWELL, r["eps"], f0s[k], r["dt"], r["t_end"],
+                ids[k] = srv.submit(2, r["N"], T, r["R"], r["kernel"], r["eps"], f0s[k], r["dt"], r["t_end"],
                                     precision=bn.MIXED)
         t0 = time.perf_counter()
         th = threading.Thread(target=feeder)
@@ -357,7 +363,7 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int):
     rel = []
     for k in sample:
         r = reqs[k]
-        with bn.Solver(2, r["N"], T, r["R"], bn.MAXWELL, r["eps"], precision=bn.FP64) as s:
+        with bn.Solver(2, r["N"], T, r["R"], r["kernel"], r["eps"], precision=bn.FP64) as s:
             s.set_state(f0s[k])
             a = time.perf_counter()
             s.step_rk(r["dt"], int(round(r["t_end"] / r["dt"])))
@@ -365,12 +371,14 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int):
             t_fp += time.perf_counter() - a
         rel.append(float(np.linalg.norm(results[k] - ref) / np.linalg.norm(ref)))
     lat = np.array(lat)
-    return {"requests": len(reqs), "arrival_rate_per_s": rate, "N": [16, 32], "precision": "mixed",
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "N": list(Ns), "kernels": ["maxwell", "hard_sphere"],
+            "eps": [-1, 0, 1], "precision": "mixed",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "solves_per_s": len(reqs) / wall, "wall_s": wall, "max_running": stats["max_active"],
             "ticks": stats["ticks"],
             "fp64_batch_of_one": {"requests": len(sample), "solves_per_s": len(sample) / t_fp,
-                                  "max_rel_l2_mixed_vs_fp64": max(rel)}}
+                                  "max_rel_l2_mixed_vs_fp64": max(rel),
+                                  "median_rel_l2_mixed_vs_fp64": float(np.median(rel))}}
 
 
 def cpu_baseline_sample(seconds: float):
@@ -446,6 +454,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=64, help="requests of the serving sample (0 = skip)")
     ap.add_argument("--serving-fp64", type=int, default=6, help="requests re-solved one at a time in FP64")
+    ap.add_argument("--serving-n64", action="store_true", help="include N=64 requests in the serving mix")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -81,6 +81,9 @@ typedef struct {
                          bn_step_rk / bn_step_rk_batch call (near Fermi saturation or
                          condensation onset), the solver switches to FP64 for the rest of its
                          life; 0 = never */
+    int mixed_rw;     /* mixed precision, d = 2, N <= 32: outputs per thread of the fused
+                         kernel's sweep, 8 or 16; 0 = chosen by the autotuner (both timed
+                         on the solver's stream at creation, cached per device and N) */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
@@ -191,6 +194,12 @@ bn_status bn_profile_read(bn_solver* s, double* out, size_t count);
  * *max_f = the largest max_j f_j at the end of any step of the last stepping call
  * (|eps| max_f is what escalate_at tests after that call).  Any pointer may be NULL. */
 bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f);
+
+/* Kernel configuration of the operator: out[0] = outputs per thread of the fused
+ * sweep (mixed 2-D N <= 32: 8 or 16; else 0), out[1] = CTAs (partial sums) per
+ * launch, out[2], out[3] = the autotuner's time per launch in ms of 8 and 16
+ * outputs per thread (0 when not timed: forced, cached, or not applicable). */
+bn_status bn_kernel_config(const bn_solver* s, double* out, size_t count);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* bn_last_error(void);

@@ -31,8 +31,9 @@ struct ElemJob {
     double2* work_c;
     const double2* tw;
     double2* Qhat;
-    double2* partials;
+    double2* partials;  // FP64 pairs, or FP32 (sum, compensation) quadruples when part32
     int nPart;
+    int part32;
     double dt, scale;
 };
 
@@ -112,10 +113,14 @@ __global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __res
         tm[1] = 0;
     }
     const ElemJob J = jobs[blockIdx.y];
+    if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
+    if (J.part32) {
+        sum_partials_f32_block(J.nm, J.nPart, reinterpret_cast<const float4*>(J.partials), J.Qhat, blockIdx.x);
+        return;
+    }
     __shared__ double2 sh[32][8];
     const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
     const int i = blockIdx.x * 8 + m;
-    if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
     double x = 0, y = 0;
     if (i < J.nm) {
         for (int c = w; c < J.nPart; c += 32) {
@@ -191,7 +196,7 @@ struct BatchPlan {
     int integrator = 0;
     ElemJob* d_elem = nullptr;
     struct Group {
-        int variant = 0, njobs = 0, total = 0, maxN = 0;
+        int variant = 0, njobs = 0, total = 0, maxN = 0, maxCount = 0;
         void* d_jobs = nullptr;
         int* d_cta = nullptr;
     };
@@ -220,6 +225,11 @@ static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in) {
     const dim3 gw((p->maxNm * 32 + kThreads - 1) / kThreads, nj);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
+    for (auto& g : p->groups)
+        if (g.variant == 0 && g.maxCount > 0) {
+            launch_mixed2d_sred_group(st, g.d_jobs, g.njobs, g.maxCount);
+            p->launches++;
+        }
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
     k_sum_partials_batch<<<dim3((p->maxNm + 7) / 8, nj), 256, 0, st>>>(p->d_elem, p->d_time);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
@@ -261,6 +271,7 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         J.Qhat = s->Qhat;
         J.partials = s->partials;
         J.nPart = std::max(1, std::min(s->eps != 0.0 ? s->work.count : s->work_quad.count, s->n_partials));
+        J.part32 = fused2d_partials_f32(s) ? 1 : 0;
         J.dt = dts[i];
         J.scale = s->scale;
         elem.push_back(J);
@@ -290,6 +301,7 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
             else reinterpret_cast<FusedArgs<double>*>(args.data() + asz * k)->stamps = p->d_time;
             cta.push_back(cta.back() + elem[kv.second[k]].nPart);
             g.maxN = std::max(g.maxN, s->g.N);
+            g.maxCount = std::max(g.maxCount, s->eps != 0.0 ? s->work.count : 0);
         }
         g.njobs = (int)kv.second.size();
         g.total = cta.back();

@@ -23,6 +23,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "bn_internal.cuh"
 
@@ -535,6 +538,22 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.err = s->flags + 2;
     A.sw = sizeof(Real) == 4 ? (const Real*)(const void*)s->tabs->sw32 : (const Real*)(const void*)s->tabs->sw64;
     A.stamps = nullptr;
+    A.Sb = s->S2;
+    A.meta = s->work.meta[s->mixed_rw == 16 ? 1 : 0];
+}
+
+// Mixed precision N <= 32 (variant 0): the S(b) kernel, k_mixed2d and the FP32-compensated
+// partial sum (bn_fused2d_mixed.cu).
+void launch_mixed(bn_solver* s) {
+    FusedArgs<float> A;
+    fill_args_t<float>(s, A);
+    if (s->prof && s->prof_slot < 8 && s->prof_stamps) {
+        A.stamps = s->prof_stamps + 2 * s->prof_slot;
+        cudaMemsetAsync(A.stamps, 0xFF, sizeof(unsigned long long), s->stream);
+        cudaMemsetAsync(A.stamps + 1, 0, sizeof(unsigned long long), s->stream);
+    }
+    const int grid = std::max(1, std::min(A.count, s->n_partials));
+    s->launches += launch_mixed2d(A, grid, s->mixed_rw, s->Qhat, s->stream);
 }
 
 template <typename Real, int RW, int NT, bool STAGE, bool DB>
@@ -585,6 +604,7 @@ static bool fused_db() {
 // staging; mixed N = 64: single buffer (shared memory); FP64: 2 outputs per thread (DFMA-bound),
 // staged for N <= 32, read through L1 for N = 64.
 void configure_fused2d() {
+    configure_mixed2d();
     configure_one<float, 8, 256, true, true>();
     configure_one<float, 8, 256, true, false>();
     configure_one<double, 2, 128, true, false>();
@@ -592,9 +612,7 @@ void configure_fused2d() {
 }
 
 size_t fused2d_smem(int N, int precision) {
-    if (precision == BN_MIXED)
-        return N > 32 ? Layout2D<float, 8, true, false>::bytes(N, 256)
-                      : (fused_db() ? Layout2D<float, 8, true, true>::bytes(N, 256) : Layout2D<float, 8, true, false>::bytes(N, 256));
+    if (precision == BN_MIXED) return N > 32 ? Layout2D<float, 8, true, false>::bytes(N, 256) : mixed2d_smem(N, 8);
     return N > 32 ? Layout2D<double, 2, false, false>::bytes(N, 256) : Layout2D<double, 2, true, false>::bytes(N, 128);
 }
 
@@ -613,12 +631,20 @@ void into_t(const bn_solver* s, cudaStream_t st, const void* G, double2* partial
     k_sum_partials<<<(s->g.nModes + 7) / 8, 256, 0, st>>>(s->g.nModes, grid, partials, Qhat);
 }
 
-void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err) {
+void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err,
+                  void* sb) {
     switch (fused2d_variant(s)) {
         case 0:
-            if (fused_db()) into_t<float, 8, 256, true, true>(s, st, G, partials, Qhat, err);
-            else into_t<float, 8, 256, true, false>(s, st, G, partials, Qhat, err);
+        case 4: {
+            FusedArgs<float> A;
+            fill_args_t<float>(s, A);
+            A.G = (const float2*)G;
+            A.partials = partials;
+            A.err = err;
+            A.Sb = sb;
+            launch_mixed2d(A, std::max(1, std::min(A.count, s->n_partials)), s->mixed_rw, Qhat, st);
             break;
+        }
         case 1: into_t<float, 8, 256, true, false>(s, st, G, partials, Qhat, err); break;
         case 2: into_t<double, 2, 128, true, false>(s, st, G, partials, Qhat, err); break;
         default: into_t<double, 2, 256, false, false>(s, st, G, partials, Qhat, err); break;
@@ -629,9 +655,90 @@ int fused2d_partials(const bn_solver* s) {
     return std::max(1, std::min(s->eps != 0.0 ? s->work.count : s->work_quad.count, s->n_partials));
 }
 
+// ------------------------------------------------------------------ autotuner (mixed N <= 32)
+// The kernel's outputs per thread (8: 3 CTAs per SM; 16: 2 CTAs per SM, fewer warp units and a
+// longer register window, more padding on small boxes) is chosen per (device, N) by timing both
+// on the solver's stream: each candidate runs twice untimed and three times timed (CUDA events)
+// on the solver's own tables and buffers; the faster wins and is cached for the process.
+// opt.mixed_rw forces a choice (8 or 16) without timing.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune;
+}  // namespace
+
+bn_status tune_mixed2d(bn_solver* s, std::string* err) {
+    s->mixed_rw = 8;
+    if (s->g.d != 2 || s->opt.precision != BN_MIXED || s->g.N > 32) return BN_OK;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (sms <= 0) sms = 152;
+    auto parts = [&](int rw) {
+        return std::max(1, std::min(s->work.count, mixed2d_ctas_per_sm(s->g.N, rw) * sms));
+    };
+    int choice = 0;
+    if (s->opt.mixed_rw == 8 || s->opt.mixed_rw == 16) {
+        choice = s->opt.mixed_rw;
+    } else {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find({s->device, s->g.N});
+        if (it != g_tune.end()) choice = it->second;
+    }
+    if (choice == 0) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        choice = 8;
+        for (int v = 0; v < 2; ++v) {
+            const int rw = v == 0 ? 8 : 16;
+            FusedArgs<float> A;
+            s->mixed_rw = rw;
+            fill_args_t<float>(s, A);
+            A.items = s->work.items;   // the full cubic work list (timing does not depend on eps or values)
+            A.count = s->work.count;
+            A.meta = s->work.meta[v];
+            A.eps = 1.0;
+            const int grid = std::min(parts(rw), s->n_partials);
+            for (int i = 0; i < 2; ++i) launch_mixed2d_kernel(A, grid, rw, s->stream);
+            cudaEventRecord(e0, s->stream);
+            for (int i = 0; i < 3; ++i) launch_mixed2d_kernel(A, grid, rw, s->stream);
+            cudaEventRecord(e1, s->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                cudaGetLastError();
+                *err = std::string("autotuner: ") + cudaGetErrorString(e);
+                return BN_ERR_CUDA;
+            }
+            s->tune_ms[v] = ms / 3.0f;
+            if (ms < best) {
+                best = ms;
+                choice = rw;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream);
+        s->launches += 10;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[{s->device, s->g.N}] = choice;
+    }
+    s->mixed_rw = choice;
+    s->n_partials = std::min(s->n_partials, parts(choice));
+    return BN_OK;
+}
+
+bool fused2d_partials_f32(const bn_solver* s) {
+    return s->g.d == 2 && (fused2d_variant(s) == 0 || fused2d_variant(s) == 4);
+}
+
+// 0: mixed N <= 32 with 8 outputs per thread, 4: with 16; 1: mixed N > 32; 2, 3: FP64.
 int fused2d_variant(const bn_solver* s) {
     const bool big = s->g.N > 32;
-    if (s->opt.precision == BN_MIXED) return big ? 1 : 0;
+    if (s->opt.precision == BN_MIXED) return big ? 1 : (s->mixed_rw == 16 ? 4 : 0);
     return big ? 3 : 2;
 }
 
@@ -642,7 +749,8 @@ void fill_fused_args(const bn_solver* s, void* out) {
 
 size_t fused2d_variant_smem(int variant, int N) {
     switch (variant) {
-        case 0: return fused_db() ? Layout2D<float, 8, true, true>::bytes(N, 256) : Layout2D<float, 8, true, false>::bytes(N, 256);
+        case 0: return mixed2d_smem(N, 8);
+        case 4: return mixed2d_smem(N, 16);
         case 1: return Layout2D<float, 8, true, false>::bytes(N, 256);
         case 2: return Layout2D<double, 2, true, false>::bytes(N, 128);
         default: return Layout2D<double, 2, false, false>::bytes(N, 256);
@@ -653,10 +761,8 @@ size_t fused2d_variant_smem(int variant, int N) {
 void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,
                           int maxN) {
     switch (variant) {
-        case 0:
-            if (fused_db()) launch_group_t<float, 8, 256, true, true>(st, d_jobs, d_cta, njobs, total, maxN);
-            else launch_group_t<float, 8, 256, true, false>(st, d_jobs, d_cta, njobs, total, maxN);
-            break;
+        case 0: launch_mixed2d_group(st, 8, d_jobs, d_cta, njobs, total, maxN); break;
+        case 4: launch_mixed2d_group(st, 16, d_jobs, d_cta, njobs, total, maxN); break;
         case 1: launch_group_t<float, 8, 256, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
         case 2: launch_group_t<double, 2, 128, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
         default: launch_group_t<double, 2, 256, false, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
@@ -669,8 +775,7 @@ void launch_fused2d(bn_solver* s) {
     const bool big = s->g.N > 32;
     if (mixed) {
         if (big) launch_t<float, 8, 256, true, false>(s, s->Ghat32, s->tabs->beta32);
-        else if (fused_db()) launch_t<float, 8, 256, true, true>(s, s->Ghat32, s->tabs->beta32);
-        else launch_t<float, 8, 256, true, false>(s, s->Ghat32, s->tabs->beta32);
+        else launch_mixed(s);
     } else {
         if (big) launch_t<double, 2, 256, false, false>(s, s->Ghat, s->tabs->beta64);
         else launch_t<double, 2, 128, true, false>(s, s->Ghat, s->tabs->beta64);

@@ -1,0 +1,512 @@
+// bn_fused2d_mixed.cu -- the 2-D operator in mixed precision for N <= 32 (Mouton & Rey, Lemma of
+// Sec. 2.3 combined as in Sec. 3.3 step 2(c)): FP32 sums with compensated accumulation.
+//
+// Same factorisation as the FP64 kernel (bn_fused2d.cu): with b = l + m and s = l,
+//   Q^_n = sum_b G^_{n-b} D_b(n),
+//   D_b(n) = eps [C_b(n) + S(b)] + [b in I_N] (beta(n-b, b) - beta(b,b)) G^_b,
+//   C_b(n) = sum_{s in box_s(b)} beta(n-s, b) P_b(s),   P_b(s) = G^_s G^_{b-s},
+//   S(b)   = sum_{s in box_s(b)} W(b, s) P_b(s),        W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b).
+//
+// Organisation (one CTA walks a static share of the b values, heaviest first):
+//  * S(b) for every b comes from a separate small kernel (one warp per b), so the operator kernel
+//    has no global-memory dependency chain per b.
+//  * The beta rectangle (box_n - box_s) of the next b is copied into shared memory asynchronously
+//    and its P_b formed while the current b is swept: one CTA barrier per b.
+//  * The sweep is split into warp units.  A unit is 32/J (output row, group of 8 outputs along n_2)
+//    tasks times J chunks of the s_1 range (J in {1, 2, 4, 8}, chosen per b to balance the warps);
+//    the J partial sums of a task meet by warp shuffles, so no shared-memory reduction or extra
+//    barrier is needed, and the lanes of the chunks share the epilogue.
+//  * Each thread keeps 8 outputs in registers; along s_2 the weights beta(n-s, b) slide through a
+//    register window (one shared load of beta, one of P_b, 16 FFMA per step).
+//  * G^_{n-b} D_b(n) is added to an FP32 (sum, compensation) pair per output in shared memory
+//    (Kahan); each CTA writes both words, and the partials of all CTAs are summed in FP32 with
+//    compensation in a fixed order, the 32 group sums in FP64 (deterministic).
+#include <algorithm>
+#include <cstdint>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+namespace {
+
+constexpr int kNT = 256;            // threads per CTA
+constexpr int kNW = kNT / 32;       // warps per CTA
+constexpr uint32_t kWait = 1u << 22;  // polls of the bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bulk (TMA engine) copy of `bytes` (multiple of 16, both ends 16-byte aligned) completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWait; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp4(float* dst, const float* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(su32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Shared-memory layout for N and RW outputs per thread: Q sums, Q compensations, G^, two P_b
+// buffers, two beta rectangles, a ring of three item records and the copy barrier.
+template <int RW>
+struct MixedLayout {
+    // beta row stride: >= the widest rectangle (RW ceil(N/RW) + N columns) and == 1 (mod 32), so
+    // that consecutive rows of the lanes of a warp fall on distinct banks
+    static __host__ __device__ int ws(int N) {
+        const int w = RW * ((N + RW - 1) / RW) + N;
+        return 32 * ((w - 1 + 31) / 32) + 1;
+    }
+    // P_b row stride (complex entries): odd, so that rows of different s_1 chunks read in one
+    // 64-bit load fall on different banks
+    static __host__ __device__ int ps(int N) { return N | 1; }
+    static __host__ __device__ size_t bslot(int N) { return ((size_t)2 * N * ws(N) * 4 + 15) / 16 * 16; }
+    static __host__ __device__ size_t pslot(int N) { return ((size_t)N * ps(N) * 8 + 15) / 16 * 16; }
+    static __host__ __device__ size_t bytes(int N) {
+        return (size_t)N * N * sizeof(float2) * 3 + 2 * pslot(N) + 2 * bslot(N) + 3 * sizeof(ItemMeta) + 16;
+    }
+};
+
+// Boxes of one b (flat extended index ib): outputs n (n, n-b in I_N), inner s (s, b-s in I_N)
+// and the beta rectangle a = n - s, with one spare column on the left.
+struct Geo {
+    int b1, b2, nlo1, L1, nlo2, L2, slo1, S1, slo2, S2, Gg, A1, a1lo, A2, a2lo;
+    bool quad;
+    __device__ __forceinline__ Geo(int ib, int N) {
+        const int E = 2 * N, h = N / 2;
+        b1 = ib / E - N;
+        b2 = ib % E - N;
+        nlo1 = max(-h, b1 - h);
+        L1 = min(h - 1, b1 + h - 1) - nlo1 + 1;
+        nlo2 = max(-h, b2 - h);
+        L2 = min(h - 1, b2 + h - 1) - nlo2 + 1;
+        slo1 = max(-h, b1 - h + 1);
+        S1 = min(h - 1, b1 + h) - slo1 + 1;
+        slo2 = max(-h, b2 - h + 1);
+        S2 = min(h - 1, b2 + h) - slo2 + 1;
+        quad = b1 >= -h && b1 < h && b2 >= -h && b2 < h;
+        Gg = (L2 + 7) / 8;
+        A1 = L1 + S1 - 1;
+        a1lo = nlo1 - slo1 - S1 + 1;
+        A2 = 8 * Gg + S2;
+        a2lo = nlo2 - slo2 - S2;
+    }
+};
+
+// Asynchronous copy of the beta rectangle of one b into Bs (rows by warp, columns by lane); columns
+// whose a_2 falls outside [-N, N) are zero-filled.
+__device__ __forceinline__ void stage_beta(float* Bs, const float* __restrict__ beta, const ItemMeta& m, int N, int WS) {
+    const int E = 2 * N, A1 = m.A1, A2 = m.A2, lane = threadIdx.x & 31;
+    const int clo = -N - m.a2lo, chi = N - m.a2lo;   // valid columns [clo, chi)
+    const float* __restrict__ src0 = beta + (size_t)m.ib * E * E + (m.a1lo + N) * E + N + m.a2lo;
+    for (int r = threadIdx.x >> 5; r < A1; r += kNW) {
+        const float* __restrict__ src = src0 + r * E;
+        float* dst = Bs + r * WS;
+        for (int c = lane; c < A2; c += 32) {
+            const bool ok = c >= clo && c < chi;
+            cp4(dst + c, ok ? src + c : src0, ok);
+        }
+    }
+}
+
+// P_b(s) = G^_s G^_{b-s} over box_s(b), rows s_1 with stride PS.
+__device__ __forceinline__ void build_P(float2* Pb, const float2* Gs, const ItemMeta& m, int N, int PS) {
+    const int h = N / 2, lane = threadIdx.x & 31, S1 = m.S1, S2 = m.S2;
+    for (int r = threadIdx.x >> 5; r < S1; r += kNW) {
+        const int s1 = m.slo1 + r;
+        const float2* gx = Gs + (s1 + h) * N + h + m.slo2;
+        const float2* gy = Gs + (m.b1 - s1 + h) * N + h + m.b2 - m.slo2;
+        float2* dst = Pb + r * PS;
+        for (int c = lane; c < S2; c += 32) dst[c] = cmulf(gx[c], gy[-c]);
+    }
+}
+
+// One s_1 row of the Toeplitz product: ar/ai[r] += sum_{s2} beta[c0 + r - s2] P[s2], the weights in a
+// register window whose slots rotate (slot of column x is x mod RW): per step one shared load of
+// beta, one of P and 2 RW FFMA.  Columns read: c0 - S2 + 1 .. c0 + RW - 1.
+template <int kRW>
+__device__ __forceinline__ void row_sweep(const float* __restrict__ brow, int c0, const float2* __restrict__ prow,
+                                          int S2, float (&ar)[kRW], float (&ai)[kRW]) {
+    float w[kRW];
+#pragma unroll
+    for (int r = 0; r < kRW; ++r) w[r] = brow[c0 + r];
+    int sl = 0;
+    for (; sl + kRW <= S2; sl += kRW) {
+#pragma unroll
+        for (int kk = 0; kk < kRW; ++kk) {
+            if (kk == 0) {
+                if (sl > 0) w[0] = brow[c0 - sl];
+            } else {
+                w[kRW - kk] = brow[c0 - sl - kk];
+            }
+            const float2 p = prow[sl + kk];
+#pragma unroll
+            for (int r = 0; r < kRW; ++r) {
+                const float wr = w[(r - kk + kRW) % kRW];
+                ar[r] = fmaf(wr, p.x, ar[r]);
+                ai[r] = fmaf(wr, p.y, ai[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kRW; ++kk) {
+        if (sl + kk >= S2) break;
+        if (kk == 0) {
+            if (sl > 0) w[0] = brow[c0 - sl];
+        } else {
+            w[kRW - kk] = brow[c0 - sl - kk];
+        }
+        const float2 p = prow[sl + kk];
+#pragma unroll
+        for (int r = 0; r < kRW; ++r) {
+            const float wr = w[(r - kk + kRW) % kRW];
+            ar[r] = fmaf(wr, p.x, ar[r]);
+            ai[r] = fmaf(wr, p.y, ai[r]);
+        }
+    }
+}
+
+// Metadata of item `item` into a shared ring slot (4 threads, 16 bytes each, asynchronous).
+__device__ __forceinline__ void fetch_meta(ItemMeta* slot, const ItemMeta* __restrict__ meta, int item, int count) {
+    if (item < count && threadIdx.x < 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(su32(reinterpret_cast<int4*>(slot) + threadIdx.x)),
+                     "l"(reinterpret_cast<const int4*>(meta + item) + threadIdx.x)
+                     : "memory");
+}
+
+template <int kRW>
+__device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, int nblk) {
+    using Lay = MixedLayout<kRW>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int N = A.N, E = 2 * N, nm = N * N, h = N / 2;
+    const int WS = Lay::ws(N), PS = Lay::ps(N);
+    float2* Qs = reinterpret_cast<float2*>(smem_raw);
+    float2* Qc = Qs + nm;
+    float2* Gs = Qc + nm;
+    unsigned char* p = reinterpret_cast<unsigned char*>(Gs + nm);
+    float2* const P0 = reinterpret_cast<float2*>(p);                       // P_b buffer k at P0 + k pstep
+    const int pstep = (int)(Lay::pslot(N) / sizeof(float2));
+    p += 2 * Lay::pslot(N);
+    float* const B0 = reinterpret_cast<float*>(p);                         // rectangle k at B0 + k bstep
+    const int bstep = (int)(Lay::bslot(N) / sizeof(float));
+    p += 2 * Lay::bslot(N);
+    ItemMeta* ring = reinterpret_cast<ItemMeta*>(p);                       // 3 slots
+    uint64_t* bar = reinterpret_cast<uint64_t*>(p + 3 * sizeof(ItemMeta));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool cubic = A.eps != 0.0;
+    const float eps_r = (float)A.eps;
+    const float2* __restrict__ Sb = reinterpret_cast<const float2*>(A.Sb);
+    const ItemMeta* __restrict__ meta = reinterpret_cast<const ItemMeta*>(A.meta);
+    if (A.stamps && tid == 0) atomicMin(&A.stamps[0], now_ns());
+
+    if (!cubic) {
+        // quadratic part only (b in I_N): each thread owns the outputs n == tid (mod NT) for every
+        // b, so no barrier is needed between b values
+        if (tid == 0) {
+            bar_init(bar);
+            bulk_load(Gs, A.G, (uint32_t)(nm * sizeof(float2)), bar);
+        }
+        for (int i = tid; i < nm; i += kNT) {
+            Qs[i] = make_float2(0.f, 0.f);
+            Qc[i] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const bool landed = bar_wait(bar, 0);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicOr(A.err, 1);
+            bar_wait(bar, 0);
+            return;
+        }
+        for (int item = blk; item < A.count; item += nblk) {
+            const int ib = A.items[item], b1 = ib / E - N, b2 = ib % E - N;
+            const float* __restrict__ bsl = A.beta + (size_t)ib * E * E;
+            const float wbb = __ldg(bsl + (b1 + N) * E + (b2 + N));
+            const float2 gb = Gs[(b1 + h) * N + (b2 + h)];
+            for (int on = tid; on < nm; on += kNT) {
+                const int n1 = on / N - h, n2 = on % N - h;
+                const int k1 = n1 - b1, k2 = n2 - b2;
+                if (k1 < -h || k1 >= h || k2 < -h || k2 >= h) continue;
+                const float wq = __ldg(bsl + (k1 + N) * E + (k2 + N)) - wbb;
+                const float2 x = cmulf(Gs[(k1 + h) * N + (k2 + h)], make_float2(wq * gb.x, wq * gb.y));
+                kahan(Qs[on].x, Qc[on].x, x.x);
+                kahan(Qs[on].y, Qc[on].y, x.y);
+            }
+        }
+    } else {
+        // G^ -> shared memory (one bulk copy); the metadata of the first two items and the first
+        // rectangle are requested at the same time
+        if (tid == 0) {
+            bar_init(bar);
+            bulk_load(Gs, A.G, (uint32_t)(nm * sizeof(float2)), bar);
+        }
+        fetch_meta(ring + 0, meta, blk, A.count);
+        fetch_meta(ring + 1, meta, blk + nblk, A.count);
+        cp_commit();
+        for (int i = tid; i < nm; i += kNT) {
+            Qs[i] = make_float2(0.f, 0.f);
+            Qc[i] = make_float2(0.f, 0.f);
+        }
+        cp_wait_all();
+        __syncthreads();
+        if (blk < A.count) stage_beta(B0, A.beta, ring[0], N, WS);
+        cp_commit();
+        const bool landed = bar_wait(bar, 0);
+        if (__syncthreads_or(!landed)) {
+            // the copy did not complete in time: record it, wait (bounded) for the copies in flight, give up
+            if (tid == 0) atomicOr(A.err, 1);
+            bar_wait(bar, 0);
+            cp_wait_all();
+            return;
+        }
+        if (blk < A.count) build_P(P0, Gs, ring[0], N, PS);
+        cp_wait_all();
+        __syncthreads();
+
+        int k = 0, slot = 0;
+        for (int item = blk; item < A.count; item += nblk) {
+            const ItemMeta& m = ring[slot];
+            const int nslot = slot == 2 ? 0 : slot + 1, n2slot = nslot == 2 ? 0 : nslot + 1;
+            // the buffers and ring slot of the previous b are free (barrier at its end): fill them
+            fetch_meta(ring + n2slot, meta, item + 2 * nblk, A.count);
+            if (item + nblk < A.count) {
+                stage_beta(B0 + (k ^ 1) * bstep, A.beta, ring[nslot], N, WS);
+                build_P(P0 + (k ^ 1) * pstep, Gs, ring[nslot], N, PS);
+            }
+            cp_commit();
+            const float2 S = Sb[m.ib];
+            const float* __restrict__ Bs = B0 + k * bstep;
+            const float2* __restrict__ Pb = P0 + k * pstep;
+            const int b1 = m.b1, b2 = m.b2, nlo1 = m.nlo1, nlo2 = m.nlo2, slo1 = m.slo1, S1 = m.S1, S2 = m.S2;
+            const int Gg = m.Gg, a1lo = m.a1lo, a2lo = m.a2lo, J = m.J, tpw = m.tpw, base = m.base;
+            const int n2end = nlo2 + m.L2;
+            const bool quad = m.quad != 0;
+            float wbb = 0.f;
+            float2 gb = make_float2(0.f, 0.f);
+            if (quad) {
+                wbb = Bs[(b1 - a1lo) * WS + (b2 - a2lo)];
+                gb = Gs[(b1 + h) * N + (b2 + h)];
+            }
+            const int jl = lane / tpw, t = lane & (tpw - 1);
+            const int s1b = slo1 + jl * m.chunk, s1e = min(slo1 + S1, s1b + m.chunk);
+            const int bshift = b1 * N + b2;   // flat offset of n - b from n
+            for (int u = warp; u < m.units; u += kNW) {
+                const int tau = u * tpw + t;
+                const bool valid = tau < base;
+                const int irow = valid ? (tau * m.ginv) >> 16 : 0;
+                const int gg = valid ? tau - irow * Gg : 0;
+                float ar[kRW], ai[kRW];
+#pragma unroll
+                for (int r = 0; r < kRW; ++r) {
+                    ar[r] = 0.f;
+                    ai[r] = 0.f;
+                }
+                const int n1 = nlo1 + irow;
+                if (valid) {
+                    const int c0 = kRW * gg + S2;
+                    const float* brow = Bs + (n1 - a1lo - s1b) * WS;
+                    const float2* prow = Pb + (s1b - slo1) * PS;
+                    for (int s1 = s1b; s1 < s1e; ++s1, brow -= WS, prow += PS)
+                        row_sweep<kRW>(brow, c0, prow, S2, ar, ai);
+                }
+                // the J chunk sums of a task (lanes t + tpw j) meet by butterfly shuffles
+                for (int mk = tpw; mk < 32; mk <<= 1) {
+#pragma unroll
+                    for (int r = 0; r < kRW; ++r) {
+                        ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], mk);
+                        ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], mk);
+                    }
+                }
+                if (valid) {
+                    const int n20 = nlo2 + kRW * gg;
+                    const float* qrow = Bs + (n1 - b1 - a1lo) * WS - b2 - a2lo;
+                    const int on0 = (n1 + h) * N + h;
+#pragma unroll
+                    for (int r = 0; r < kRW; ++r) {
+                        const int n2 = n20 + r;
+                        if ((r & (J - 1)) != jl || n2 >= n2end) continue;
+                        float2 D = make_float2(eps_r * (ar[r] + S.x), eps_r * (ai[r] + S.y));
+                        if (quad) {
+                            const float wq = qrow[n2] - wbb;
+                            D.x = fmaf(wq, gb.x, D.x);
+                            D.y = fmaf(wq, gb.y, D.y);
+                        }
+                        const int on = on0 + n2;
+                        const float2 x = cmulf(Gs[on - bshift], D);
+                        kahan(Qs[on].x, Qc[on].x, x.x);
+                        kahan(Qs[on].y, Qc[on].y, x.y);
+                    }
+                }
+            }
+            cp_wait_all();
+            __syncthreads();
+            k ^= 1;
+            slot = nslot;
+        }
+    }
+    __syncthreads();
+    float4* out = reinterpret_cast<float4*>(A.partials) + (size_t)blk * nm;
+    for (int i = tid; i < nm; i += kNT) {
+        const float2 v = Qs[i], c = Qc[i];
+        out[i] = make_float4(v.x, v.y, c.x, c.y);
+    }
+    if (A.stamps) {
+        __syncthreads();
+        if (tid == 0) atomicMax(&A.stamps[1], now_ns());
+    }
+}
+
+// RW = 8: 80 registers, 3 CTAs per SM; RW = 16: 2 CTAs per SM.
+template <int RW>
+__global__ void __launch_bounds__(kNT, RW == 8 ? 3 : 2) k_mixed2d(FusedArgs<float> A) {
+    mixed_body<RW>(A, blockIdx.x, gridDim.x);
+}
+
+// Many requests in one launch: CTAs [cta_begin[j], cta_begin[j+1]) serve request j with its own CTA
+// count, so that its result does not depend on the rest of the batch.
+template <int RW>
+__global__ void __launch_bounds__(kNT, RW == 8 ? 3 : 2) k_mixed2d_batch(const FusedArgs<float>* __restrict__ jobs,
+                                                                        const int* __restrict__ cta_begin, int njobs) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cta_begin[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const FusedArgs<float> A = jobs[lo];
+    mixed_body<RW>(A, blockIdx.x - cta_begin[lo], cta_begin[lo + 1] - cta_begin[lo]);
+}
+
+// S(b) for every item of one request: one warp per b, FP32 products, lane sums combined by shuffles.
+__device__ __forceinline__ void sred_body(const FusedArgs<float>& A, int item) {
+    if (item >= A.count || A.eps == 0.0) return;
+    const int N = A.N, nm = N * N, h = N / 2, lane = threadIdx.x & 31;
+    const int ib = A.items[item];
+    const Geo g(ib, N);
+    const float* __restrict__ wrow = A.sw + (size_t)ib * nm;
+    const float2* __restrict__ G = A.G;
+    float sr = 0.f, si = 0.f;
+    for (int r = 0; r < g.S1; ++r) {
+        const int s1 = g.slo1 + r;
+        for (int c = lane; c < g.S2; c += 32) {
+            const int s2 = g.slo2 + c;
+            const float w = __ldg(wrow + (s1 + h) * N + (s2 + h));
+            const float2 P = cmulf(G[(s1 + h) * N + (s2 + h)], G[(g.b1 - s1 + h) * N + (g.b2 - s2 + h)]);
+            sr = fmaf(w, P.x, sr);
+            si = fmaf(w, P.y, si);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) reinterpret_cast<float2*>(A.Sb)[ib] = make_float2(sr, si);
+}
+
+__global__ void __launch_bounds__(256) k_sred2d(FusedArgs<float> A) {
+    sred_body(A, blockIdx.x * 8 + (threadIdx.x >> 5));
+}
+__global__ void __launch_bounds__(256) k_sred2d_batch(const FusedArgs<float>* __restrict__ jobs) {
+    sred_body(jobs[blockIdx.y], blockIdx.x * 8 + (threadIdx.x >> 5));
+}
+
+}  // namespace
+
+namespace {
+__global__ void __launch_bounds__(256) k_sum_partials_f32(int nm, int nPart, const float4* __restrict__ partials,
+                                                          double2* __restrict__ out) {
+    sum_partials_f32_block(nm, nPart, partials, out, blockIdx.x);
+}
+}  // namespace
+
+size_t mixed2d_smem(int N, int rw) { return rw == 16 ? MixedLayout<16>::bytes(N) : MixedLayout<8>::bytes(N); }
+
+void configure_mixed2d() {
+    cudaFuncSetAttribute(k_mixed2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_mixed2d_batch<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_mixed2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_mixed2d_batch<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+int mixed2d_ctas_per_sm(int N, int rw) {
+    int n = 0;
+    const size_t smem = mixed2d_smem(N, rw);
+    if (rw == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mixed2d<16>, kNT, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mixed2d<8>, kNT, smem);
+    cudaGetLastError();
+    return std::max(1, n);
+}
+
+void launch_mixed2d_sred(const FusedArgs<float>& A, cudaStream_t st) {
+    if (A.eps != 0.0 && A.count > 0) k_sred2d<<<(A.count + 7) / 8, 256, 0, st>>>(A);
+}
+
+void launch_mixed2d_kernel(const FusedArgs<float>& A, int grid, int rw, cudaStream_t st) {
+    if (rw == 16) k_mixed2d<16><<<grid, kNT, MixedLayout<16>::bytes(A.N), st>>>(A);
+    else k_mixed2d<8><<<grid, kNT, MixedLayout<8>::bytes(A.N), st>>>(A);
+}
+
+int launch_mixed2d(const FusedArgs<float>& A, int grid, int rw, double2* Qhat, cudaStream_t st) {
+    const int nm = A.N * A.N;
+    int launches = 2;
+    if (A.eps != 0.0 && A.count > 0) {
+        launch_mixed2d_sred(A, st);
+        ++launches;
+    }
+    launch_mixed2d_kernel(A, grid, rw, st);
+    k_sum_partials_f32<<<(nm + 7) / 8, 256, 0, st>>>(nm, grid, reinterpret_cast<const float4*>(A.partials), Qhat);
+    return launches;
+}
+
+void launch_mixed2d_sred_group(cudaStream_t st, const void* d_jobs, int njobs, int maxCount) {
+    k_sred2d_batch<<<dim3((maxCount + 7) / 8, njobs), 256, 0, st>>>(static_cast<const FusedArgs<float>*>(d_jobs));
+}
+
+void launch_mixed2d_group(cudaStream_t st, int rw, const void* d_jobs, const int* d_cta, int njobs, int total,
+                          int maxN) {
+    const FusedArgs<float>* jobs = static_cast<const FusedArgs<float>*>(d_jobs);
+    if (rw == 16) k_mixed2d_batch<16><<<total, kNT, MixedLayout<16>::bytes(maxN), st>>>(jobs, d_cta, njobs);
+    else k_mixed2d_batch<8><<<total, kNT, MixedLayout<8>::bytes(maxN), st>>>(jobs, d_cta, njobs);
+}
+
+}  // namespace bn

@@ -68,16 +68,86 @@ struct FusedArgs {
     int* err;                // [0] set to 1 if a bounded wait gave up
     unsigned long long* stamps;  // optional [2]: min start / max end %globaltimer (ns) over CTAs
     const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
+    void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the S(b) kernel
+    const void* meta;        // mixed N <= 32: ItemMeta per item (same order as items)
 };
+
+// Fixed-order sum of the FP32 (sum, compensation) partials of the mixed 2-D kernel into Q^: a
+// block of 256 threads owns the 8 modes [8 bx, 8 bx + 8); each of 32 thread groups adds the
+// partials c = w, w + 32, ... with FP32 compensated (Kahan) summation, and the 32 group results
+// are combined in FP64 in order (deterministic).
+__device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+__device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const float4* __restrict__ partials,
+                                                       double2* __restrict__ out, int bx) {
+    __shared__ double2 sh[32][8];
+    const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
+    const int i = bx * 8 + m;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    if (i < nm) {
+        for (int c = w; c < nPart; c += 32) {
+            const float4 v = partials[(size_t)c * nm + i];
+            kahan_add_f(sx, cx, v.x);
+            kahan_add_f(sx, cx, -v.z);
+            kahan_add_f(sy, cy, v.y);
+            kahan_add_f(sy, cy, -v.w);
+        }
+    }
+    sh[w][m] = make_double2((double)sx - (double)cx, (double)sy - (double)cy);
+    __syncthreads();
+    if (threadIdx.x < 8 && i < nm) {
+        double ox = 0, oy = 0;
+        for (int k = 0; k < 32; ++k) {
+            ox += sh[k][m].x;
+            oy += sh[k][m].y;
+        }
+        out[i] = make_double2(ox, oy);
+    }
+}
 
 struct BatchPlan;
 
 // ---------------------------------------------------------------- triple-sum work list
+// Geometry of one b of the 2-D mixed kernel, derived once on the host (64 bytes):
+// outputs n in box_n(b) = [nlo, nlo + L), inner s in box_s(b) = [slo, slo + S) per dimension,
+// the beta rectangle a = n - s staged as rows [a1lo, a1lo + A1) x columns [a2lo, a2lo + A2) (one
+// spare column on the left), Gg groups of 8 outputs along n_2, and the warp split of the sweep:
+// J chunks of the s_1 range (chunk rows each), tpw = 32 / J tasks per warp unit, `units` warp
+// units covering base = L1 Gg tasks; ginv = ceil(2^16 / Gg) (task -> row by multiply-shift).
+struct ItemMeta {
+    int ib, ginv;
+    short b1, b2, nlo1, nlo2, L2, slo1, S1, slo2, S2, Gg, A1, A2, a1lo, a2lo, quad, J, tpw, chunk, units, base;
+    short pad[8];
+};
+static_assert(sizeof(ItemMeta) == 64, "ItemMeta is 64 bytes");
+
 struct WorkList {
     int* items = nullptr;   // flat extended index of b, sorted by descending work
     int count = 0;
     double terms = 0;       // sum over items of |box_n| |box_s|
+    ItemMeta* meta[2] = {nullptr, nullptr};   // 2-D: per item (same order) for the mixed kernel, RW = 8, 16
 };
+
+// The warp split of one b for a CTA of `warps` warps (shared by the host metadata and tests).
+inline void choose_split_host(int base, int S1, int warps, int* J, int* chunk, int* units) {
+    int bestJ = 1, best = 0x7fffffff;
+    for (int j = 1; j <= 8; j <<= 1) {
+        const int tpw = 32 / j;
+        const int u = (base + tpw - 1) / tpw;
+        const int cost = ((u + warps - 1) / warps) * ((S1 + j - 1) / j);
+        if (cost < best) {
+            best = cost;
+            bestJ = j;
+        }
+    }
+    *J = bestJ;
+    *chunk = (S1 + bestJ - 1) / bestJ;
+    *units = (base + 32 / bestJ - 1) / (32 / bestJ);
+}
 
 }  // namespace bn
 
@@ -95,6 +165,8 @@ struct bn_solver {
     bn::WorkList work;           // b with non-empty triple-sum boxes (eps != 0)
     bn::WorkList work_quad;      // b in I_N (quadratic part only, eps == 0)
     int n_partials = 0;          // CTAs of the triple-sum kernel (rows of the partial buffer)
+    int mixed_rw = 8;            // outputs per thread of the mixed 2-D kernel (N <= 32)
+    float tune_ms[2] = {0, 0};   // autotuner timings of RW = 8, 16 (0 = not timed)
 
     // device buffers
     double* f = nullptr;         // state, N^d
@@ -172,6 +244,23 @@ void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
 int triple_partials(const bn_solver* s);
 
 // batched stepping of 2-D solvers (bn_batch.cu)
+// mixed-precision 2-D kernel for N <= 32 (bn_fused2d_mixed.cu)
+// rw = outputs per thread (8 or 16)
+size_t mixed2d_smem(int N, int rw);
+void configure_mixed2d();
+int mixed2d_ctas_per_sm(int N, int rw);
+void launch_mixed2d_sred(const FusedArgs<float>& A, cudaStream_t st);
+void launch_mixed2d_kernel(const FusedArgs<float>& A, int grid, int rw, cudaStream_t st);
+int launch_mixed2d(const FusedArgs<float>& A, int grid, int rw, double2* Qhat, cudaStream_t st);   // returns launches
+void launch_mixed2d_sred_group(cudaStream_t st, const void* d_jobs, int njobs, int maxCount);
+void launch_mixed2d_group(cudaStream_t st, int rw, const void* d_jobs, const int* d_cta, int njobs, int total,
+                          int maxN);
+// Chooses the outputs per thread of the mixed 2-D kernel for this solver (option, cache, or timing
+// both candidates on the solver's stream) and sets s->mixed_rw and s->n_partials.
+bn_status tune_mixed2d(bn_solver* s, std::string* err);
+// true when the fused partials of this solver are FP32 (sum, compensation) pairs
+bool fused2d_partials_f32(const bn_solver* s);
+
 bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, cudaStream_t st, BatchPlan** out,
                      std::string* err);
 void destroy_plan(BatchPlan* p);
@@ -194,7 +283,9 @@ void launch_fused2d(bn_solver* s);   // s->Qhat from s->Ghat / s->Ghat32
 // 2 = FP64 N <= 32, 3 = FP64 N = 64
 int fused2d_variant(const bn_solver* s);
 int fused2d_partials(const bn_solver* s);   // CTAs (partial sums) of the solver's fused launch
-void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err);
+// sb: scratch of nExt float2 for S(b) (mixed N <= 32; may alias nothing else)
+void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err,
+                  void* sb);
 void fill_fused_args(const bn_solver* s, void* out);   // FusedArgs<float> or <double> by precision
 size_t fused2d_variant_smem(int variant, int N);
 void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,

@@ -376,6 +376,40 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
     }
     cudaMemcpy(s->work.items, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(s->work_quad.items, qflat.data(), sizeof(int) * qflat.size(), cudaMemcpyHostToDevice);
+    for (int v = 0; d == 2 && v < 2; ++v) {
+        // per-item geometry of the mixed kernel (8 warps per CTA, RW = 8 or 16 outputs per thread)
+        const int RW = v == 0 ? 8 : 16;
+        std::vector<ItemMeta> meta(flat.size());
+        const int h = N / 2;
+        for (size_t i = 0; i < flat.size(); ++i) {
+            const int ib = flat[i], b1 = ib / E - N, b2 = ib % E - N;
+            const int nlo1 = std::max(-h, b1 - h), L1 = std::min(h - 1, b1 + h - 1) - nlo1 + 1;
+            const int nlo2 = std::max(-h, b2 - h), L2 = std::min(h - 1, b2 + h - 1) - nlo2 + 1;
+            const int slo1 = std::max(-h, b1 - h + 1), S1 = std::min(h - 1, b1 + h) - slo1 + 1;
+            const int slo2 = std::max(-h, b2 - h + 1), S2 = std::min(h - 1, b2 + h) - slo2 + 1;
+            const int Gg = (L2 + RW - 1) / RW, base = L1 * Gg;
+            int J, chunk, units;
+            choose_split_host(base, S1, 8, &J, &chunk, &units);
+            ItemMeta m{};
+            m.ib = ib;
+            m.ginv = (65536 + Gg - 1) / Gg;
+            m.b1 = (short)b1; m.b2 = (short)b2;
+            m.nlo1 = (short)nlo1; m.nlo2 = (short)nlo2; m.L2 = (short)L2;
+            m.slo1 = (short)slo1; m.S1 = (short)S1; m.slo2 = (short)slo2; m.S2 = (short)S2;
+            m.Gg = (short)Gg; m.A1 = (short)(L1 + S1 - 1); m.A2 = (short)(RW * Gg + S2);
+            m.a1lo = (short)(nlo1 - slo1 - S1 + 1); m.a2lo = (short)(nlo2 - slo2 - S2);
+            m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
+            m.J = (short)J; m.tpw = (short)(32 / J); m.chunk = (short)chunk; m.units = (short)units;
+            m.base = (short)base;
+            meta[i] = m;
+        }
+        if (cudaMalloc(&s->work.meta[v], sizeof(ItemMeta) * meta.size()) != cudaSuccess) {
+            cudaGetLastError();
+            *err = "work list allocation failed";
+            return BN_ERR_NOMEM;
+        }
+        cudaMemcpy(s->work.meta[v], meta.data(), sizeof(ItemMeta) * meta.size(), cudaMemcpyHostToDevice);
+    }
     s->work.count = (int)flat.size();
     s->work.terms = total;
     s->work_quad.count = (int)qflat.size();
