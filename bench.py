@@ -147,10 +147,10 @@ def recorded_traffic():
     return None
 
 
-def make_pair(bn, I, precision, stream):
+def make_pair(bn, I, precision, stream, mixed_rw=0):
     T = I.box_half_width(R_TRUNC)
-    bkw = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 0.0, stream=stream, precision=precision)
-    bos = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 1.0, stream=stream, precision=precision)
+    bkw = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 0.0, stream=stream, precision=precision, mixed_rw=mixed_rw)
+    bos = bn.Solver(2, N_MODES, T, R_TRUNC, bn.MAXWELL, 1.0, stream=stream, precision=precision, mixed_rw=mixed_rw)
     f_bkw = I.config1_bkw_f0(N_MODES, R_TRUNC)
     f_bos = I.config1_boson_f0(N_MODES, R_TRUNC)
     bkw.set_state(f_bkw)
@@ -219,7 +219,7 @@ def run_ours(args):
         return ms, launches, prof, (t_wall0, t_wall1)
 
     # ---- mixed precision (the headline)
-    solvers, f0 = make_pair(bn, I, bn.MIXED, stream)
+    solvers, f0 = make_pair(bn, I, bn.MIXED, stream, args.mixed_rw)
     clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                             f".clocks_rank{rank}.csv")
     p, fh = clocks_sampler_start(clk_path)
@@ -456,6 +456,8 @@ def main():
     ap.add_argument("--serving-fp64", type=int, default=6, help="requests re-solved one at a time in FP64")
     ap.add_argument("--serving-n64", action="store_true", help="include N=64 requests in the serving mix")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg (profiling runs)")
+    ap.add_argument("--mixed-rw", type=int, default=0, choices=[0, 8, 16],
+                    help="outputs per thread of the mixed kernel (0 = autotuner; profiling runs fix it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -47,8 +47,13 @@ __device__ __forceinline__ double2 warp_sum2(double sr, double si) {
 }
 
 __device__ __forceinline__ double2 tw_at(const double2* tw, int k, int j, int N, int sign) {
-    int m = (k * j) % N;
-    if (m < 0) m += N;
+    int m;
+    if ((N & (N - 1)) == 0) {
+        m = (k * j) & (N - 1);
+    } else {
+        m = (k * j) % N;
+        if (m < 0) m += N;
+    }
     double2 w = __ldg(tw + m);
     if (sign > 0) w.y = -w.y;
     return w;
@@ -59,7 +64,11 @@ __device__ __forceinline__ double2 tw_at(const double2* tw, int k, int j, int N,
 //   1: work_c along n_1 -> Ghat (and Ghat32), scale N^-2      (forward)
 //   2: Qhat along n_1 -> work_c                               (inverse)
 //   3: work_c along n_2 -> Qv = scale * Re                    (inverse)
-__global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stage_in) {
+// In pass 3 the Runge-Kutta update of the same entry can follow (rk: 0 none; 1 RK4 stage
+// acc = (first ? 0 : acc) + w_acc K, y = f + c dt K; 2 RK4 final, candidate = f + dt/6 (acc + K);
+// 3 SSP-RK2 final, candidate = (f + y + dt K) / 2), non-finite candidates flagged.
+__global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stage_in, int rk = 0, double w_acc = 0.0,
+                            double c_next = 0.0, int first = 0) {
     const ElemJob J = jobs[blockIdx.y];
     const int N = J.N, nm = J.nm, lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -90,7 +99,17 @@ __global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stag
                 J.Ghat[idx] = make_double2(sum.x * sc, sum.y * sc);
                 if (J.Ghat32) J.Ghat32[idx] = make_float2((float)(sum.x * sc), (float)(sum.y * sc));
             } else {
-                J.Qv[idx] = sum.x * J.scale;
+                const double K = sum.x * J.scale;
+                J.Qv[idx] = K;
+                if (rk == 1) {
+                    J.kacc[idx] = first ? w_acc * K : fma(w_acc, K, J.kacc[idx]);
+                    J.y[idx] = fma(c_next * J.dt, K, J.f[idx]);
+                } else if (rk >= 2) {
+                    const double v = rk == 2 ? fma(J.dt / 6.0, J.kacc[idx] + K, J.f[idx])
+                                             : 0.5 * (J.f[idx] + fma(J.dt, K, J.y[idx]));
+                    J.cand[idx] = v;
+                    if (!isfinite(v)) atomicOr(&J.flags[0], 1);
+                }
             }
         }
     }
@@ -113,11 +132,12 @@ __global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __res
         tm[1] = 0;
     }
     const ElemJob J = jobs[blockIdx.y];
-    if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
     if (J.part32) {
+        if (blockIdx.x * kPartModes >= J.nm) return;   // uniform per block
         sum_partials_f32_block(J.nm, J.nPart, reinterpret_cast<const float4*>(J.partials), J.Qhat, blockIdx.x);
         return;
     }
+    if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
     __shared__ double2 sh[32][8];
     const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
     const int i = blockIdx.x * 8 + m;
@@ -220,20 +240,23 @@ void destroy_plan(BatchPlan* p) {
     delete p;
 }
 
-static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in) {
+// One evaluation of every request's operator; with rk != 0 (no request projects Q) the RK update
+// that follows is fused into the last transform pass (arguments as for k_dft_batch).
+static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in, int rk = 0, double w_acc = 0.0,
+                                double c_next = 0.0, int first = 0) {
     const int nj = (int)p->solvers.size();
     const dim3 gw((p->maxNm * 32 + kThreads - 1) / kThreads, nj);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
     for (auto& g : p->groups)
-        if (g.variant == 0 && g.maxCount > 0) {
+        if ((g.variant == 0 || g.variant == 4) && g.maxCount > 0) {
             launch_mixed2d_sred_group(st, g.d_jobs, g.njobs, g.maxCount);
             p->launches++;
         }
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
-    k_sum_partials_batch<<<dim3((p->maxNm + 7) / 8, nj), 256, 0, st>>>(p->d_elem, p->d_time);
+    k_sum_partials_batch<<<dim3((p->maxNm + kPartModes - 1) / kPartModes, nj), 256, 0, st>>>(p->d_elem, p->d_time);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
-    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in);
+    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in, rk, w_acc, c_next, first);
     p->launches += 5 + (long long)p->groups.size();
     for (bn_solver* s : p->solvers)
         if (s->opt.conserve) {
@@ -327,25 +350,39 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
     }
     const int nj = n;
     const dim3 ge((p->maxNm + kThreads - 1) / kThreads, nj);
+    bool fuse_rk = true;   // the projection of Q must run between the transform and the RK update
+    for (int i = 0; i < n; ++i)
+        if (solvers[i]->opt.conserve) fuse_rk = false;
     if (p->integrator == 0) {
         const double wacc[4] = {1.0, 2.0, 2.0, 1.0}, cnext[3] = {0.5, 0.5, 1.0};
         for (int stage = 0; stage < 4; ++stage) {
+            if (fuse_rk) {
+                record_batched_eval(p, st, stage == 0 ? 0 : 1, stage < 3 ? 1 : 2, stage < 3 ? wacc[stage] : 0.0,
+                                    stage < 3 ? cnext[stage] : 0.0, stage == 0);
+                continue;
+            }
             record_batched_eval(p, st, stage == 0 ? 0 : 1);
             if (stage < 3) {
                 k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, wacc[stage], cnext[stage], stage == 0);
                 p->launches++;
             }
         }
-        k_rk_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
+        if (!fuse_rk) {
+            k_rk_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
+            p->launches++;
+        }
+    } else if (fuse_rk) {
+        record_batched_eval(p, st, 0, 1, 0.0, 1.0, 1);
+        record_batched_eval(p, st, 1, 3);
     } else {
         record_batched_eval(p, st, 0);
         k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, 0.0, 1.0, 1);
         record_batched_eval(p, st, 1);
         k_heun_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
-        p->launches++;
+        p->launches += 2;
     }
     k_commit_batch<<<ge, kThreads, 0, st>>>(p->d_elem);
-    p->launches += 2;
+    p->launches += 1;
     e = cudaStreamEndCapture(st, &graph);
     if (e == cudaSuccess) {
         e = cudaGraphInstantiate(&p->graph, graph, 0);

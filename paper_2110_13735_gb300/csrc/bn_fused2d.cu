@@ -540,6 +540,7 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.stamps = nullptr;
     A.Sb = s->S2;
     A.meta = s->work.meta[s->mixed_rw == 16 ? 1 : 0];
+    A.dq = s->tabs->dq32;
 }
 
 // Mixed precision N <= 32 (variant 0): the S(b) kernel, k_mixed2d and the FP32-compensated

@@ -259,14 +259,13 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
         }
         for (int item = blk; item < A.count; item += nblk) {
             const int ib = A.items[item], b1 = ib / E - N, b2 = ib % E - N;
-            const float* __restrict__ bsl = A.beta + (size_t)ib * E * E;
-            const float wbb = __ldg(bsl + (b1 + N) * E + (b2 + N));
+            const float* __restrict__ dqb = A.dq + (size_t)((b1 + h) * N + (b2 + h)) * E * E;
             const float2 gb = Gs[(b1 + h) * N + (b2 + h)];
             for (int on = tid; on < nm; on += kNT) {
                 const int n1 = on / N - h, n2 = on % N - h;
                 const int k1 = n1 - b1, k2 = n2 - b2;
                 if (k1 < -h || k1 >= h || k2 < -h || k2 >= h) continue;
-                const float wq = __ldg(bsl + (k1 + N) * E + (k2 + N)) - wbb;
+                const float wq = __ldg(dqb + (k1 + N) * E + (k2 + N));
                 const float2 x = cmulf(Gs[(k1 + h) * N + (k2 + h)], make_float2(wq * gb.x, wq * gb.y));
                 kahan(Qs[on].x, Qc[on].x, x.x);
                 kahan(Qs[on].y, Qc[on].y, x.y);
@@ -320,11 +319,11 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
             const int Gg = m.Gg, a1lo = m.a1lo, a2lo = m.a2lo, J = m.J, tpw = m.tpw, base = m.base;
             const int n2end = nlo2 + m.L2;
             const bool quad = m.quad != 0;
-            float wbb = 0.f;
             float2 gb = make_float2(0.f, 0.f);
+            const float* __restrict__ dqb = A.dq;
             if (quad) {
-                wbb = Bs[(b1 - a1lo) * WS + (b2 - a2lo)];
                 gb = Gs[(b1 + h) * N + (b2 + h)];
+                dqb += (size_t)((b1 + h) * N + (b2 + h)) * E * E + (N - b1) * E + (N - b2);   // dq at a = n - b: [n1 E + n2]
             }
             const int jl = lane / tpw, t = lane & (tpw - 1);
             const int s1b = slo1 + jl * m.chunk, s1e = min(slo1 + S1, s1b + m.chunk);
@@ -341,6 +340,11 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                     ai[r] = 0.f;
                 }
                 const int n1 = nlo1 + irow;
+                if (valid && quad) {
+                    // the quadratic weights of this task's outputs are needed after the sweep
+                    const float* pf = dqb + n1 * E + nlo2 + kRW * gg;
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
+                }
                 if (valid) {
                     const int c0 = kRW * gg + S2;
                     const float* brow = Bs + (n1 - a1lo - s1b) * WS;
@@ -358,7 +362,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                 }
                 if (valid) {
                     const int n20 = nlo2 + kRW * gg;
-                    const float* qrow = Bs + (n1 - b1 - a1lo) * WS - b2 - a2lo;
+                    const float* qrow = dqb + n1 * E;
                     const int on0 = (n1 + h) * N + h;
 #pragma unroll
                     for (int r = 0; r < kRW; ++r) {
@@ -366,7 +370,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                         if ((r & (J - 1)) != jl || n2 >= n2end) continue;
                         float2 D = make_float2(eps_r * (ar[r] + S.x), eps_r * (ai[r] + S.y));
                         if (quad) {
-                            const float wq = qrow[n2] - wbb;
+                            const float wq = __ldg(qrow + n2);
                             D.x = fmaf(wq, gb.x, D.x);
                             D.y = fmaf(wq, gb.y, D.y);
                         }
@@ -416,21 +420,42 @@ __global__ void __launch_bounds__(kNT, RW == 8 ? 3 : 2) k_mixed2d_batch(const Fu
     mixed_body<RW>(A, blockIdx.x - cta_begin[lo], cta_begin[lo + 1] - cta_begin[lo]);
 }
 
-// S(b) for every item of one request: one warp per b, FP32 products, lane sums combined by shuffles.
-__device__ __forceinline__ void sred_body(const FusedArgs<float>& A, int item) {
-    if (item >= A.count || A.eps == 0.0) return;
+// S(b) for the items [8 blockIdx.x, 8 blockIdx.x + 8) of one request: the CTA stages G^ (N <= 32) in
+// shared memory, then each warp takes one b; lanes run along s_2 and four rows s_1 are in flight at
+// once (independent loads of W); the lane sums meet by shuffles.
+__device__ __forceinline__ void sred_body(const FusedArgs<float>& A, int item0) {
+    __shared__ float2 Gsh[32 * 32];
+    if (item0 >= A.count || A.eps == 0.0) return;   // uniform per CTA
     const int N = A.N, nm = N * N, h = N / 2, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) Gsh[i] = A.G[i];
+    __syncthreads();
+    const int item = item0 + (threadIdx.x >> 5);
+    if (item >= A.count) return;
     const int ib = A.items[item];
     const Geo g(ib, N);
-    const float* __restrict__ wrow = A.sw + (size_t)ib * nm;
-    const float2* __restrict__ G = A.G;
+    const float* __restrict__ wrow = A.sw + (size_t)ib * nm + h * N + h + g.slo2;
     float sr = 0.f, si = 0.f;
-    for (int r = 0; r < g.S1; ++r) {
-        const int s1 = g.slo1 + r;
-        for (int c = lane; c < g.S2; c += 32) {
-            const int s2 = g.slo2 + c;
-            const float w = __ldg(wrow + (s1 + h) * N + (s2 + h));
-            const float2 P = cmulf(G[(s1 + h) * N + (s2 + h)], G[(g.b1 - s1 + h) * N + (g.b2 - s2 + h)]);
+    if (lane < g.S2) {
+        const int s2 = g.slo2 + lane;
+        const float2* gs = Gsh + h * N + h + s2;                   // G^_(s1, s2) at gs[s1 N]
+        const float2* gm = Gsh + (g.b1 + h) * N + h + g.b2 - s2;   // G^_(b - s) at gm[-s1 N]
+        int r = 0;
+        for (; r + 4 <= g.S1; r += 4) {
+            float w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = __ldg(wrow + (g.slo1 + r + q) * N + lane);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int s1 = g.slo1 + r + q;
+                const float2 P = cmulf(gs[s1 * N], gm[-s1 * N]);
+                sr = fmaf(w[q], P.x, sr);
+                si = fmaf(w[q], P.y, si);
+            }
+        }
+        for (; r < g.S1; ++r) {
+            const int s1 = g.slo1 + r;
+            const float w = __ldg(wrow + s1 * N + lane);
+            const float2 P = cmulf(gs[s1 * N], gm[-s1 * N]);
             sr = fmaf(w, P.x, sr);
             si = fmaf(w, P.y, si);
         }
@@ -443,11 +468,9 @@ __device__ __forceinline__ void sred_body(const FusedArgs<float>& A, int item) {
     if (lane == 0) reinterpret_cast<float2*>(A.Sb)[ib] = make_float2(sr, si);
 }
 
-__global__ void __launch_bounds__(256) k_sred2d(FusedArgs<float> A) {
-    sred_body(A, blockIdx.x * 8 + (threadIdx.x >> 5));
-}
+__global__ void __launch_bounds__(256) k_sred2d(FusedArgs<float> A) { sred_body(A, blockIdx.x * 8); }
 __global__ void __launch_bounds__(256) k_sred2d_batch(const FusedArgs<float>* __restrict__ jobs) {
-    sred_body(jobs[blockIdx.y], blockIdx.x * 8 + (threadIdx.x >> 5));
+    sred_body(jobs[blockIdx.y], blockIdx.x * 8);
 }
 
 }  // namespace
@@ -494,7 +517,8 @@ int launch_mixed2d(const FusedArgs<float>& A, int grid, int rw, double2* Qhat, c
         ++launches;
     }
     launch_mixed2d_kernel(A, grid, rw, st);
-    k_sum_partials_f32<<<(nm + 7) / 8, 256, 0, st>>>(nm, grid, reinterpret_cast<const float4*>(A.partials), Qhat);
+    k_sum_partials_f32<<<(nm + kPartModes - 1) / kPartModes, 256, 0, st>>>(
+        nm, grid, reinterpret_cast<const float4*>(A.partials), Qhat);
     return launches;
 }
 

@@ -51,6 +51,7 @@ struct KernelTables {
     float* beta32 = nullptr;      // same, rounded to FP32
     double* sw64 = nullptr;       // 2-D: [b (ext)][s in I_N] = beta(s,b-s) - beta(b,s) - beta(s,b) (0 off box_s(b))
     float* sw32 = nullptr;
+    float* dq32 = nullptr;        // 2-D: [b in I_N][a (ext)] = beta(a, b) - beta(b, b), formed in FP64, rounded once
     size_t bytes = 0;
 };
 
@@ -70,12 +71,14 @@ struct FusedArgs {
     const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
     void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the S(b) kernel
     const void* meta;        // mixed N <= 32: ItemMeta per item (same order as items)
+    const float* dq;         // mixed N <= 32: quadratic weights beta(a, b) - beta(b, b), [b in I_N][a]
 };
 
 // Fixed-order sum of the FP32 (sum, compensation) partials of the mixed 2-D kernel into Q^: a
-// block of 256 threads owns the 8 modes [8 bx, 8 bx + 8); each of 32 thread groups adds the
-// partials c = w, w + 32, ... with FP32 compensated (Kahan) summation, and the 32 group results
-// are combined in FP64 in order (deterministic).
+// block of 256 threads owns the kPartModes modes [kPartModes bx, kPartModes (bx + 1)); each of its
+// 256 / kPartModes thread groups adds the partials c = w, w + groups, ... with FP32 compensated
+// (Kahan) summation, and the group results meet in a fixed FP64 tree (deterministic).
+constexpr int kPartModes = 2;
 __device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -84,12 +87,13 @@ __device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
 }
 __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const float4* __restrict__ partials,
                                                        double2* __restrict__ out, int bx) {
-    __shared__ double2 sh[32][8];
-    const int m = threadIdx.x & 7, w = threadIdx.x >> 3;
-    const int i = bx * 8 + m;
+    constexpr int G = 256 / kPartModes;
+    __shared__ double2 sh[256];
+    const int m = threadIdx.x % kPartModes, w = threadIdx.x / kPartModes;
+    const int i = bx * kPartModes + m;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     if (i < nm) {
-        for (int c = w; c < nPart; c += 32) {
+        for (int c = w; c < nPart; c += G) {
             const float4 v = partials[(size_t)c * nm + i];
             kahan_add_f(sx, cx, v.x);
             kahan_add_f(sx, cx, -v.z);
@@ -97,16 +101,16 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
             kahan_add_f(sy, cy, -v.w);
         }
     }
-    sh[w][m] = make_double2((double)sx - (double)cx, (double)sy - (double)cy);
+    sh[threadIdx.x] = make_double2((double)sx - (double)cx, (double)sy - (double)cy);
     __syncthreads();
-    if (threadIdx.x < 8 && i < nm) {
-        double ox = 0, oy = 0;
-        for (int k = 0; k < 32; ++k) {
-            ox += sh[k][m].x;
-            oy += sh[k][m].y;
+    for (int st = G / 2; st >= 1; st >>= 1) {
+        if (w < st) {
+            const double2 a = sh[threadIdx.x], b = sh[threadIdx.x + st * kPartModes];
+            sh[threadIdx.x] = make_double2(a.x + b.x, a.y + b.y);
         }
-        out[i] = make_double2(ox, oy);
+        __syncthreads();
     }
+    if (w == 0 && i < nm) out[i] = sh[m];
 }
 
 struct BatchPlan;

@@ -162,6 +162,21 @@ __global__ void k_sw_table(int N, const double* __restrict__ beta, double* __res
     }
 }
 
+// Quadratic weights dq(b, a) = beta(a, b) - beta(b, b) for b in I_N (2-D), the difference taken in
+// FP64 and rounded to FP32 once (the FP32 difference of two rounded weights would carry the
+// rounding of beta itself, which is far larger than the difference for a near b).
+__global__ void k_dq_table(int N, const double* __restrict__ beta, float* __restrict__ dq32) {
+    const int E = 2 * N, nExt = E * E, h = N / 2;
+    const long long total = (long long)N * N * nExt;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(idx / nExt), ia = (int)(idx % nExt);
+        const int b1 = q / N - h, b2 = q % N - h;
+        const int ib = (b1 + N) * E + (b2 + N);
+        dq32[idx] = (float)(beta[(size_t)ib * nExt + ia] - beta[(size_t)ib * nExt + ib]);
+    }
+}
+
 // Gauss-Legendre rule on [-1, 1]: Newton iteration on P_n from Tricomi's initial guesses.
 void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
     x.assign(n, 0.0);
@@ -263,17 +278,19 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     const size_t nSw = d == 2 ? (size_t)nExt * s->g.nModes : 0;
     if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw64, sizeof(double) * nSw);
     if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw32, sizeof(float) * nSw);
+    const size_t nDq = d == 2 ? (size_t)s->g.nModes * nExt : 0;
+    if (e == cudaSuccess && nDq) e = cudaMalloc(&t->dq32, sizeof(float) * nDq);
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
         cudaFree(d_nodes);
         cudaFree(d_rad);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
-        cudaFree(t->sw64); cudaFree(t->sw32);
+        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32);
         delete t;
         cudaGetLastError();
         return BN_ERR_NOMEM;
     }
-    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw);
+    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw) + sizeof(float) * nDq;
     cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
     if (d_rad) cudaMemcpyAsync(d_rad, rad.data(), sizeof(double2) * rad.size(), cudaMemcpyHostToDevice, s->stream);
     k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, s->kernel, (int)rad.size(),
@@ -283,6 +300,8 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     s->launches += 2;
     if (nSw) {
         k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
+        k_dq_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->dq32);
+        s->launches++;
         s->launches++;
     }
     e = cudaStreamSynchronize(s->stream);
@@ -292,7 +311,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
-        cudaFree(t->sw64); cudaFree(t->sw32);
+        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32);
         delete t;
         return BN_ERR_CUDA;
     }
@@ -313,6 +332,7 @@ void release_tables(KernelTables* t) {
     cudaFree(t->beta32);
     cudaFree(t->sw64);
     cudaFree(t->sw32);
+    cudaFree(t->dq32);
     delete t;
 }
 
