@@ -322,14 +322,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32)):
-    """Continuous-batching server on a seeded stream of 2-D requests (the serving mix: N in `Ns`,
-    eps in {-1, 0, +1}, Maxwell molecules or hard spheres, two-Gaussian data, Poisson arrivals at
-    `rate`/s, RK4 dt=0.01 to t=2, mixed precision), fed in real time from a host thread.  Reports
-    p50/p99 time-to-solution, solves/s, and the same requests (a stratified sample) solved one at a
-    time in FP64 for solves/s and the relative L2 difference of the final states."""
+def serving_run(bn, I, reqs, escalate_at: float):
+    """Continuous-batching server on a seeded stream of 2-D requests fed in real time from a host
+    thread (mixed precision; with escalate_at > 0 a request switches to FP64 once |eps| max f
+    reaches it).  Returns (latencies, final states, wall seconds, server stats)."""
     import threading
-    reqs = I.serving_requests(n=n_requests, rate=rate, Ns=Ns, kernels=(0, 1))
     T = I.box_half_width(6.0)
     f0s = [I.request_f0(r) for r in reqs]
     ids = [None] * len(reqs)
@@ -341,12 +338,12 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16
                 if delay > 0:
                     time.sleep(delay)
                 ids[k] = srv.submit(2, r["N"], T, r["R"], r["kernel"], r["eps"], f0s[k], r["dt"], r["t_end"],
-                                    precision=bn.MIXED)
+                                    precision=bn.MIXED, escalate_at=escalate_at)
         t0 = time.perf_counter()
         th = threading.Thread(target=feeder)
         th.start()
         th.join()
-        srv.wait_idle(900)
+        srv.wait_idle(1800)
         wall = time.perf_counter() - t0
         lat, results = [], []
         for k, r in enumerate(reqs):
@@ -356,29 +353,40 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16
             lat.append(times[2] - times[0])
             results.append(res)
         stats = srv.stats()
-    # FP64 batch of one on a stratified sample (every k-th request)
+    return np.array(lat), results, wall, stats
+
+
+def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32), escalations=(0.0, 0.55)):
+    """The serving mix (N in `Ns`, eps in {-1, 0, +1}, Maxwell molecules or hard spheres, two-Gaussian
+    data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2) through the continuous-batching server,
+    once per escalation threshold, against a stratified sample of the same requests solved one at a
+    time in FP64 (solves/s and the relative L2 difference of the final states)."""
+    reqs = I.serving_requests(n=n_requests, rate=rate, Ns=Ns, kernels=(0, 1))
+    T = I.box_half_width(6.0)
     step = max(1, len(reqs) // max(1, fp64_sample))
     sample = list(range(0, len(reqs), step))[:fp64_sample]
     t_fp = 0.0
-    rel = []
+    refs = {}
     for k in sample:
         r = reqs[k]
         with bn.Solver(2, r["N"], T, r["R"], r["kernel"], r["eps"], precision=bn.FP64) as s:
-            s.set_state(f0s[k])
+            s.set_state(I.request_f0(r))
             a = time.perf_counter()
             s.step_rk(r["dt"], int(round(r["t_end"] / r["dt"])))
-            ref = s.get_state().reshape(-1)
+            refs[k] = s.get_state().reshape(-1)
             t_fp += time.perf_counter() - a
-        rel.append(float(np.linalg.norm(results[k] - ref) / np.linalg.norm(ref)))
-    lat = np.array(lat)
-    return {"requests": len(reqs), "arrival_rate_per_s": rate, "N": list(Ns), "kernels": ["maxwell", "hard_sphere"],
-            "eps": [-1, 0, 1], "precision": "mixed",
+    out = {"requests": len(reqs), "arrival_rate_per_s": rate, "N": list(Ns), "kernels": ["maxwell", "hard_sphere"],
+           "eps": [-1, 0, 1], "fp64_batch_of_one": {"requests": len(sample), "solves_per_s": len(sample) / t_fp}}
+    for esc in escalations:
+        lat, results, wall, stats = serving_run(bn, I, reqs, esc)
+        rel = [float(np.linalg.norm(results[k] - refs[k]) / np.linalg.norm(refs[k])) for k in sample]
+        out["mixed" if esc == 0.0 else f"mixed_escalate_at_{esc:g}"] = {
+            "precision": "mixed" if esc == 0.0 else f"mixed, FP64 once |eps| max f >= {esc:g}",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "solves_per_s": len(reqs) / wall, "wall_s": wall, "max_running": stats["max_active"],
-            "ticks": stats["ticks"],
-            "fp64_batch_of_one": {"requests": len(sample), "solves_per_s": len(sample) / t_fp,
-                                  "max_rel_l2_mixed_vs_fp64": max(rel),
-                                  "median_rel_l2_mixed_vs_fp64": float(np.median(rel))}}
+            "ticks": stats["ticks"], "max_rel_l2_vs_fp64": max(rel), "median_rel_l2_vs_fp64": float(np.median(rel)),
+            "within_1e-6": int(sum(x <= 1e-6 for x in rel))}
+    return out
 
 
 def cpu_baseline_sample(seconds: float):
@@ -453,7 +461,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=64, help="requests of the serving sample (0 = skip)")
-    ap.add_argument("--serving-fp64", type=int, default=6, help="requests re-solved one at a time in FP64")
+    ap.add_argument("--serving-fp64", type=int, default=12, help="requests re-solved one at a time in FP64")
     ap.add_argument("--serving-n64", action="store_true", help="include N=64 requests in the serving mix")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg (profiling runs)")
     ap.add_argument("--mixed-rw", type=int, default=0, choices=[0, 8, 16],

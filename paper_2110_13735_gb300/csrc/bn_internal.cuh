@@ -78,7 +78,7 @@ struct FusedArgs {
 // block of 256 threads owns the kPartModes modes [kPartModes bx, kPartModes (bx + 1)); each of its
 // 256 / kPartModes thread groups adds the partials c = w, w + groups, ... with FP32 compensated
 // (Kahan) summation, and the group results meet in a fixed FP64 tree (deterministic).
-constexpr int kPartModes = 2;
+constexpr int kPartModes = 4;
 __device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -93,7 +93,20 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
     const int i = bx * kPartModes + m;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     if (i < nm) {
-        for (int c = w; c < nPart; c += G) {
+        int c = w;
+        for (; c + 3 * G < nPart; c += 4 * G) {   // four loads in flight, added in order
+            float4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = partials[(size_t)(c + q * G) * nm + i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                kahan_add_f(sx, cx, v[q].x);
+                kahan_add_f(sx, cx, -v[q].z);
+                kahan_add_f(sy, cy, v[q].y);
+                kahan_add_f(sy, cy, -v[q].w);
+            }
+        }
+        for (; c < nPart; c += G) {
             const float4 v = partials[(size_t)c * nm + i];
             kahan_add_f(sx, cx, v.x);
             kahan_add_f(sx, cx, -v.z);
