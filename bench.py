@@ -41,6 +41,7 @@ N_MODES, R_TRUNC, DT = 32, 6.0, 0.005
 T_END = {"bkw": 5.0 - 1.0, "boson": 5.0}   # integration spans of the two solves
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP64_PEAK_TF = 1.25   # nominal dense FP64 of one GB300
 
 
 def lemma_terms(d: int, N: int, cubic: bool) -> float:
@@ -275,11 +276,18 @@ def run_ours(args):
     if not args.no_fp64:
         solvers64, _ = make_pair(bn, I, bn.FP64, stream)
         k64 = max(3, args.steps // 4)
-        ms64, _, _, _ = timed(solvers64, k64, min(args.warmup, 3))
+        ms64, _, prof64, _ = timed(solvers64, k64, min(args.warmup, 3), profile=True)
         for s in solvers64:
             s.close()
         ms64_step = float(np.mean(ms64))
         fp64 = {"value": terms_step / (ms64_step * 1e-3) * ws, "unit": UNIT, "ms_per_step": ms64_step, "steps": k64}
+        if prof64 and prof64[3] > 0 and prof64[2] > 0:
+            k64_ms = prof64[2] / prof64[3]
+            a64 = flops_launch / (k64_ms * 1e-3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "kernel": "k_fused2d_batch<double,2,128> (both requests)",
+                                "ms_per_launch": k64_ms, "achieved": a64, "peak": FP64_PEAK_TF, "unit": "TFLOP/s",
+                                "frac": a64 / FP64_PEAK_TF,
+                                "peak_basis": "nominal GB300 FP64 (no measured FP64 figure on this pool)"}
 
     steps_to_end = {k: int(round(v / DT)) for k, v in T_END.items()}
     solves = {"pair_solve_s_mixed": ms_per_step * max(steps_to_end.values()) / 1e3}

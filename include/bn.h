@@ -82,8 +82,11 @@ typedef struct {
                          condensation onset), the solver switches to FP64 for the rest of its
                          life; 0 = never */
     int mixed_rw;     /* mixed precision, d = 2, N <= 32: outputs per thread of the fused
-                         kernel's sweep, 8 or 16; 0 = chosen by the autotuner (both timed
-                         on the solver's stream at creation, cached per device and N) */
+                         kernel's sweep, 8 or 16; 0 = chosen by the autotuner (the variants
+                         timed on the solver's stream at creation, cached per device and N;
+                         the per-b orientation choice is tuned in either case) */
+    int mixed_variant; /* mixed 2-D N <= 32: 0 = as mixed_rw says; 1..4 forces the kernel
+                         variant (8, 8 oriented, 16, 16 oriented outputs per thread) */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
@@ -197,8 +200,10 @@ bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escal
 
 /* Kernel configuration of the operator: out[0] = outputs per thread of the fused
  * sweep (mixed 2-D N <= 32: 8 or 16; else 0), out[1] = CTAs (partial sums) per
- * launch, out[2], out[3] = the autotuner's time per launch in ms of 8 and 16
- * outputs per thread (0 when not timed: forced, cached, or not applicable). */
+ * launch, out[2] = 1 if the sweep orientation is chosen per b (else the register
+ * window always runs along n_2), out[3..6] = the autotuner's time per launch in ms
+ * of the variants (8, 8 oriented, 16, 16 oriented; 0 when not timed: cached, excluded
+ * by opt.mixed_rw, or not applicable).  count >= 7. */
 bn_status bn_kernel_config(const bn_solver* s, double* out, size_t count);
 
 /* Message of the last failed call on this thread ("" if none). */

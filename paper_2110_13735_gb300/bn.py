@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
-                ("mixed_rw", ctypes.c_int)]
+                ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -110,11 +110,11 @@ def _dptr(a: np.ndarray):
 
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
-            escalate_at=0.0, mixed_rw=0) -> Options:
+            escalate_at=0.0, mixed_rw=0, mixed_variant=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
-    o.mixed_rw = mixed_rw
+    o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
     return o
 
 
@@ -217,10 +217,11 @@ class Solver:
         return out
 
     def kernel_config(self):
-        """(outputs per thread, CTAs per launch, tuner ms for 8, tuner ms for 16)."""
-        out = np.zeros(4)
-        _check(_lib.bn_kernel_config(self._h, _dptr(out), 4))
-        return int(out[0]), int(out[1]), float(out[2]), float(out[3])
+        """(outputs per thread, CTAs per launch, oriented (0/1), tuner ms of the variants
+        (8, 8 oriented, 16, 16 oriented))."""
+        out = np.zeros(7)
+        _check(_lib.bn_kernel_config(self._h, _dptr(out), 7))
+        return int(out[0]), int(out[1]), int(out[2]), tuple(float(x) for x in out[3:])
 
     def precision_state(self):
         """(precision in use, time of the switch to FP64 or -1, max f after the last step)."""

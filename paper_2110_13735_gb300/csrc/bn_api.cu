@@ -44,7 +44,7 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 void free_buffers(bn_solver* s) {
     void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->twiddle, s->S2, s->quad,
                     s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items, s->work_quad.items,
-                    s->work.meta[0], s->work.meta[1]};
+                    s->work.meta[0], s->work.meta[1], s->work.meta[2], s->work.meta[3]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
@@ -234,6 +234,10 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     if (s->opt.mixed_rw != 0 && s->opt.mixed_rw != 8 && s->opt.mixed_rw != 16) {
         delete s;
         return fail(BN_ERR_ARG, "mixed_rw must be 0, 8 or 16");
+    }
+    if (s->opt.mixed_variant < 0 || s->opt.mixed_variant > 4) {
+        delete s;
+        return fail(BN_ERR_ARG, "mixed_variant must be in 0..4");
     }
     if (s->opt.M <= 0) s->opt.M = 2 * N;
     if (s->opt.c_phi <= 0) s->opt.c_phi = d == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI);
@@ -481,12 +485,12 @@ bn_status bn_work_counts(const bn_solver* s, double* out, size_t count) {
 long long bn_kernel_launches(const bn_solver* s) { return s ? s->launches : 0; }
 
 bn_status bn_kernel_config(const bn_solver* s, double* out, size_t count) {
-    if (!valid_solver(s) || !out || count < 4) return fail(BN_ERR_ARG, "null solver/out or count < 4");
+    if (!valid_solver(s) || !out || count < 7) return fail(BN_ERR_ARG, "null solver/out or count < 7");
     const bool mixed2d = s->g.d == 2 && s->opt.precision == BN_MIXED && s->g.N <= 32;
     out[0] = mixed2d ? s->mixed_rw : 0;
     out[1] = s->n_partials;
-    out[2] = s->tune_ms[0];
-    out[3] = s->tune_ms[1];
+    out[2] = mixed2d ? (s->mixed_v & 1) : 0;
+    for (int v = 0; v < 4; ++v) out[3 + v] = s->tune_ms[v];
     return BN_OK;
 }
 

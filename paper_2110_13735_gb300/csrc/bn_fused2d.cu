@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include "bn_internal.cuh"
 
@@ -539,8 +540,9 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.sw = sizeof(Real) == 4 ? (const Real*)(const void*)s->tabs->sw32 : (const Real*)(const void*)s->tabs->sw64;
     A.stamps = nullptr;
     A.Sb = s->S2;
-    A.meta = s->work.meta[s->mixed_rw == 16 ? 1 : 0];
+    A.meta = s->work.meta[s->mixed_v];
     A.dq = s->tabs->dq32;
+    A.betaT = s->tabs->beta32T;
 }
 
 // Mixed precision N <= 32 (variant 0): the S(b) kernel, k_mixed2d and the FP32-compensated
@@ -657,18 +659,21 @@ int fused2d_partials(const bn_solver* s) {
 }
 
 // ------------------------------------------------------------------ autotuner (mixed N <= 32)
-// The kernel's outputs per thread (8: 3 CTAs per SM; 16: 2 CTAs per SM, fewer warp units and a
-// longer register window, more padding on small boxes) is chosen per (device, N) by timing both
-// on the solver's stream: each candidate runs twice untimed and three times timed (CUDA events)
-// on the solver's own tables and buffers; the faster wins and is cached for the process.
-// opt.mixed_rw forces a choice (8 or 16) without timing.
+// Four variants of the kernel: 8 or 16 outputs per thread (8: 3 CTAs per SM; 16: 2 CTAs per SM,
+// fewer warp units and a longer register window, more padding on small boxes), each with the
+// register window always along n_2 or with the orientation chosen per b by the host's mapping
+// model.  The variant is chosen per (device, N, forced RW) by timing the candidates on the
+// solver's stream: each runs twice untimed and three times timed (CUDA events) on the solver's own
+// tables and buffers; the fastest wins and is cached for the process.  opt.mixed_rw forces the
+// outputs per thread (the orientation is still timed); opt.mixed_variant forces a variant.
 namespace {
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tune;
+std::map<std::tuple<int, int, int>, int> g_tune;
 }  // namespace
 
 bn_status tune_mixed2d(bn_solver* s, std::string* err) {
     s->mixed_rw = 8;
+    s->mixed_v = 0;
     if (s->g.d != 2 || s->opt.precision != BN_MIXED || s->g.N > 32) return BN_OK;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -676,28 +681,28 @@ bn_status tune_mixed2d(bn_solver* s, std::string* err) {
     auto parts = [&](int rw) {
         return std::max(1, std::min(s->work.count, mixed2d_ctas_per_sm(s->g.N, rw) * sms));
     };
-    int choice = 0;
-    if (s->opt.mixed_rw == 8 || s->opt.mixed_rw == 16) {
-        choice = s->opt.mixed_rw;
-    } else {
+    const int forced = (s->opt.mixed_rw == 8 || s->opt.mixed_rw == 16) ? s->opt.mixed_rw : 0;
+    const auto key = std::make_tuple(s->device, s->g.N, forced);
+    int choice = s->opt.mixed_variant > 0 ? s->opt.mixed_variant - 1 : -1;
+    if (choice < 0) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune.find({s->device, s->g.N});
+        auto it = g_tune.find(key);
         if (it != g_tune.end()) choice = it->second;
     }
-    if (choice == 0) {
+    if (choice < 0) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        choice = 8;
-        for (int v = 0; v < 2; ++v) {
-            const int rw = v == 0 ? 8 : 16;
+        const int v0 = forced == 16 ? 2 : 0, v1 = forced == 8 ? 2 : 4;
+        for (int v = v0; v < v1; ++v) {
+            const int rw = v < 2 ? 8 : 16;
             FusedArgs<float> A;
             s->mixed_rw = rw;
+            s->mixed_v = v;
             fill_args_t<float>(s, A);
             A.items = s->work.items;   // the full cubic work list (timing does not depend on eps or values)
             A.count = s->work.count;
-            A.meta = s->work.meta[v];
             A.eps = 1.0;
             const int grid = std::min(parts(rw), s->n_partials);
             for (int i = 0; i < 2; ++i) launch_mixed2d_kernel(A, grid, rw, s->stream);
@@ -717,18 +722,19 @@ bn_status tune_mixed2d(bn_solver* s, std::string* err) {
             s->tune_ms[v] = ms / 3.0f;
             if (ms < best) {
                 best = ms;
-                choice = rw;
+                choice = v;
             }
+            s->launches += 5;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream);
-        s->launches += 10;
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[{s->device, s->g.N}] = choice;
+        g_tune[key] = choice;
     }
-    s->mixed_rw = choice;
-    s->n_partials = std::min(s->n_partials, parts(choice));
+    s->mixed_v = choice;
+    s->mixed_rw = choice < 2 ? 8 : 16;
+    s->n_partials = std::min(s->n_partials, parts(s->mixed_rw));
     return BN_OK;
 }
 

@@ -133,31 +133,45 @@ struct Geo {
     }
 };
 
-// Asynchronous copy of the beta rectangle of one b into Bs (rows by warp, columns by lane); columns
-// whose a_2 falls outside [-N, N) are zero-filled.
-__device__ __forceinline__ void stage_beta(float* Bs, const float* __restrict__ beta, const ItemMeta& m, int N, int WS) {
-    const int E = 2 * N, A1 = m.A1, A2 = m.A2, lane = threadIdx.x & 31;
-    const int clo = -N - m.a2lo, chi = N - m.a2lo;   // valid columns [clo, chi)
-    const float* __restrict__ src0 = beta + (size_t)m.ib * E * E + (m.a1lo + N) * E + N + m.a2lo;
-    for (int r = threadIdx.x >> 5; r < A1; r += kNW) {
+// Asynchronous copy of the beta rectangle of one b into Bs (rows a_u by warp, columns a_w by lane)
+// from the table whose rows run along u (beta for orient 0, the swapped table for orient 1);
+// columns whose a_w falls outside [-N, N) are zero-filled.
+__device__ __forceinline__ void stage_beta(float* Bs, const float* __restrict__ beta, const float* __restrict__ betaT,
+                                           const ItemMeta& m, int N, int WS) {
+    const int E = 2 * N, Au = m.Au, Aw = m.Aw, lane = threadIdx.x & 31;
+    const int clo = -N - m.a_wlo, chi = N - m.a_wlo;   // valid columns [clo, chi)
+    const float* __restrict__ src0 =
+        (m.orient ? betaT : beta) + (size_t)m.ib * E * E + (m.a_ulo + N) * E + N + m.a_wlo;
+    for (int r = threadIdx.x >> 5; r < Au; r += kNW) {
         const float* __restrict__ src = src0 + r * E;
         float* dst = Bs + r * WS;
-        for (int c = lane; c < A2; c += 32) {
+        for (int c = lane; c < Aw; c += 32) {
             const bool ok = c >= clo && c < chi;
             cp4(dst + c, ok ? src + c : src0, ok);
         }
     }
 }
 
-// P_b(s) = G^_s G^_{b-s} over box_s(b), rows s_1 with stride PS.
+// P_b(s) = G^_s G^_{b-s} over box_s(b): rows s_u, columns s_w, stride PS.  Lanes run along the
+// dimension that is contiguous in G^ (s_w for orient 0, s_u for orient 1).
 __device__ __forceinline__ void build_P(float2* Pb, const float2* Gs, const ItemMeta& m, int N, int PS) {
-    const int h = N / 2, lane = threadIdx.x & 31, S1 = m.S1, S2 = m.S2;
-    for (int r = threadIdx.x >> 5; r < S1; r += kNW) {
-        const int s1 = m.slo1 + r;
-        const float2* gx = Gs + (s1 + h) * N + h + m.slo2;
-        const float2* gy = Gs + (m.b1 - s1 + h) * N + h + m.b2 - m.slo2;
-        float2* dst = Pb + r * PS;
-        for (int c = lane; c < S2; c += 32) dst[c] = cmulf(gx[c], gy[-c]);
+    const int h = N / 2, lane = threadIdx.x & 31, Su = m.Su, Sw = m.Sw;
+    if (!m.orient) {
+        for (int r = threadIdx.x >> 5; r < Su; r += kNW) {
+            const int s1 = m.slo_u + r;
+            const float2* gx = Gs + (s1 + h) * N + h + m.slo_w;
+            const float2* gy = Gs + (m.b1 - s1 + h) * N + h + m.b2 - m.slo_w;
+            float2* dst = Pb + r * PS;
+            for (int c = lane; c < Sw; c += 32) dst[c] = cmulf(gx[c], gy[-c]);
+        }
+    } else {
+        // u = dimension 2, w = dimension 1: s = (slo_w + c, slo_u + r)
+        for (int c = threadIdx.x >> 5; c < Sw; c += kNW) {
+            const int s1 = m.slo_w + c;
+            const float2* gx = Gs + (s1 + h) * N + h + m.slo_u;
+            const float2* gy = Gs + (m.b1 - s1 + h) * N + h + m.b2 - m.slo_u;
+            for (int r = lane; r < Su; r += 32) Pb[r * PS + c] = cmulf(gx[r], gy[-r]);
+        }
     }
 }
 
@@ -287,7 +301,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
         }
         cp_wait_all();
         __syncthreads();
-        if (blk < A.count) stage_beta(B0, A.beta, ring[0], N, WS);
+        if (blk < A.count) stage_beta(B0, A.beta, A.betaT, ring[0], N, WS);
         cp_commit();
         const bool landed = bar_wait(bar, 0);
         if (__syncthreads_or(!landed)) {
@@ -308,73 +322,99 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
             // the buffers and ring slot of the previous b are free (barrier at its end): fill them
             fetch_meta(ring + n2slot, meta, item + 2 * nblk, A.count);
             if (item + nblk < A.count) {
-                stage_beta(B0 + (k ^ 1) * bstep, A.beta, ring[nslot], N, WS);
+                stage_beta(B0 + (k ^ 1) * bstep, A.beta, A.betaT, ring[nslot], N, WS);
                 build_P(P0 + (k ^ 1) * pstep, Gs, ring[nslot], N, PS);
             }
             cp_commit();
             const float2 S = Sb[m.ib];
             const float* __restrict__ Bs = B0 + k * bstep;
             const float2* __restrict__ Pb = P0 + k * pstep;
-            const int b1 = m.b1, b2 = m.b2, nlo1 = m.nlo1, nlo2 = m.nlo2, slo1 = m.slo1, S1 = m.S1, S2 = m.S2;
-            const int Gg = m.Gg, a1lo = m.a1lo, a2lo = m.a2lo, J = m.J, tpw = m.tpw, base = m.base;
-            const int n2end = nlo2 + m.L2;
+            const int orient = m.orient, b1 = m.b1, b2 = m.b2;
+            const int nlo_u = m.nlo_u, nlo_w = m.nlo_w, slo_u = m.slo_u, Su = m.Su, Sw = m.Sw;
+            const int Gg = m.Gg, a_ulo = m.a_ulo, J = m.J, tpw = m.tpw, base = m.base;
+            const int nwend = nlo_w + m.Lw;
+            const int su = orient ? 1 : N, sw = orient ? N : 1;   // flat strides of u and w (modes)
+            const int eu = orient ? 1 : E, ew = orient ? E : 1;   // and in the extended box
             const bool quad = m.quad != 0;
             float2 gb = make_float2(0.f, 0.f);
             const float* __restrict__ dqb = A.dq;
             if (quad) {
                 gb = Gs[(b1 + h) * N + (b2 + h)];
-                dqb += (size_t)((b1 + h) * N + (b2 + h)) * E * E + (N - b1) * E + (N - b2);   // dq at a = n - b: [n1 E + n2]
+                dqb += (size_t)((b1 + h) * N + (b2 + h)) * E * E + (N - b1) * E + (N - b2);   // dq at a = n - b
             }
-            const int jl = lane / tpw, t = lane & (tpw - 1);
-            const int s1b = slo1 + jl * m.chunk, s1e = min(slo1 + S1, s1b + m.chunk);
+            const int jl = lane / tpw, t = lane - jl * tpw;
+            const int s1b = slo_u + jl * m.chunk, s1e = min(slo_u + Su, s1b + m.chunk);
             const int bshift = b1 * N + b2;   // flat offset of n - b from n
             for (int u = warp; u < m.units; u += kNW) {
                 const int tau = u * tpw + t;
-                const bool valid = tau < base;
-                const int irow = valid ? (tau * m.ginv) >> 16 : 0;
-                const int gg = valid ? tau - irow * Gg : 0;
+                const bool valid = jl < J && tau < base;
+                int irow = 0, gg = 0;
+                if (valid) {
+                    if (orient) {   // row fastest
+                        gg = (tau * m.linv) >> 16;
+                        irow = tau - gg * m.Lu;
+                    } else {        // group fastest
+                        irow = (tau * m.ginv) >> 16;
+                        gg = tau - irow * Gg;
+                    }
+                }
                 float ar[kRW], ai[kRW];
 #pragma unroll
                 for (int r = 0; r < kRW; ++r) {
                     ar[r] = 0.f;
                     ai[r] = 0.f;
                 }
-                const int n1 = nlo1 + irow;
+                const int n_u = nlo_u + irow;
+                const int nw0 = nlo_w + kRW * gg;
                 if (valid && quad) {
                     // the quadratic weights of this task's outputs are needed after the sweep
-                    const float* pf = dqb + n1 * E + nlo2 + kRW * gg;
+                    const float* pf = dqb + n_u * eu + nw0 * ew;
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(pf));
                 }
                 if (valid) {
-                    const int c0 = kRW * gg + S2;
-                    const float* brow = Bs + (n1 - a1lo - s1b) * WS;
-                    const float2* prow = Pb + (s1b - slo1) * PS;
+                    const int c0 = kRW * gg + Sw;
+                    const float* brow = Bs + (n_u - a_ulo - s1b) * WS;
+                    const float2* prow = Pb + (s1b - slo_u) * PS;
                     for (int s1 = s1b; s1 < s1e; ++s1, brow -= WS, prow += PS)
-                        row_sweep<kRW>(brow, c0, prow, S2, ar, ai);
+                        row_sweep<kRW>(brow, c0, prow, Sw, ar, ai);
                 }
-                // the J chunk sums of a task (lanes t + tpw j) meet by butterfly shuffles
-                for (int mk = tpw; mk < 32; mk <<= 1) {
+                // the J chunk sums of a task (lanes t + tpw j) meet by shuffles: a butterfly when
+                // J is a power of two (tpw J = 32), else in the order j = 0 .. J-1
+                if ((J & (J - 1)) == 0) {
+                    for (int mk = tpw; mk < 32; mk <<= 1) {
+#pragma unroll
+                        for (int r = 0; r < kRW; ++r) {
+                            ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], mk);
+                            ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], mk);
+                        }
+                    }
+                } else {
 #pragma unroll
                     for (int r = 0; r < kRW; ++r) {
-                        ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], mk);
-                        ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], mk);
+                        float xr = 0.f, xi = 0.f;
+                        for (int j = 0; j < J; ++j) {
+                            xr += __shfl_sync(0xffffffffu, ar[r], t + tpw * j);
+                            xi += __shfl_sync(0xffffffffu, ai[r], t + tpw * j);
+                        }
+                        ar[r] = xr;
+                        ai[r] = xi;
                     }
                 }
                 if (valid) {
-                    const int n20 = nlo2 + kRW * gg;
-                    const float* qrow = dqb + n1 * E;
-                    const int on0 = (n1 + h) * N + h;
+                    const float* qrow = dqb + n_u * eu;
+                    const int on0 = (n_u + h) * su + h * sw;
+                    int rj = 0;   // r mod J
 #pragma unroll
-                    for (int r = 0; r < kRW; ++r) {
-                        const int n2 = n20 + r;
-                        if ((r & (J - 1)) != jl || n2 >= n2end) continue;
+                    for (int r = 0; r < kRW; ++r, rj = rj + 1 == J ? 0 : rj + 1) {
+                        const int n_w = nw0 + r;
+                        if (rj != jl || n_w >= nwend) continue;
                         float2 D = make_float2(eps_r * (ar[r] + S.x), eps_r * (ai[r] + S.y));
                         if (quad) {
-                            const float wq = __ldg(qrow + n2);
+                            const float wq = __ldg(qrow + n_w * ew);
                             D.x = fmaf(wq, gb.x, D.x);
                             D.y = fmaf(wq, gb.y, D.y);
                         }
-                        const int on = on0 + n2;
+                        const int on = on0 + n_w * sw;
                         const float2 x = cmulf(Gs[on - bshift], D);
                         kahan(Qs[on].x, Qc[on].x, x.x);
                         kahan(Qs[on].y, Qc[on].y, x.y);

@@ -49,6 +49,7 @@ struct KernelTables {
     double* alphap64 = nullptr;   // [P][nExt]
     double* beta64 = nullptr;     // [nExt(b)][nExt(a)] = beta(a, b)  (b-major)
     float* beta32 = nullptr;      // same, rounded to FP32
+    float* beta32T = nullptr;     // 2-D N <= 32: [b][a2][a1] (the FP32 table with the two a axes swapped)
     double* sw64 = nullptr;       // 2-D: [b (ext)][s in I_N] = beta(s,b-s) - beta(b,s) - beta(s,b) (0 off box_s(b))
     float* sw32 = nullptr;
     float* dq32 = nullptr;        // 2-D: [b in I_N][a (ext)] = beta(a, b) - beta(b, b), formed in FP64, rounded once
@@ -72,6 +73,7 @@ struct FusedArgs {
     void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the S(b) kernel
     const void* meta;        // mixed N <= 32: ItemMeta per item (same order as items)
     const float* dq;         // mixed N <= 32: quadratic weights beta(a, b) - beta(b, b), [b in I_N][a]
+    const float* betaT;      // mixed N <= 32: [b][a2][a1]
 };
 
 // Fixed-order sum of the FP32 (sum, compensation) partials of the mixed 2-D kernel into Q^: a
@@ -129,16 +131,21 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
 struct BatchPlan;
 
 // ---------------------------------------------------------------- triple-sum work list
-// Geometry of one b of the 2-D mixed kernel, derived once on the host (64 bytes):
-// outputs n in box_n(b) = [nlo, nlo + L), inner s in box_s(b) = [slo, slo + S) per dimension,
-// the beta rectangle a = n - s staged as rows [a1lo, a1lo + A1) x columns [a2lo, a2lo + A2) (one
-// spare column on the left), Gg groups of 8 outputs along n_2, and the warp split of the sweep:
-// J chunks of the s_1 range (chunk rows each), tpw = 32 / J tasks per warp unit, `units` warp
-// units covering base = L1 Gg tasks; ginv = ceil(2^16 / Gg) (task -> row by multiply-shift).
+// Geometry of one b of the 2-D mixed kernel, derived once on the host (64 bytes).  The sweep runs
+// its register window along dimension w and splits dimension u (orient 0: u = 1, w = 2; orient 1:
+// u = 2, w = 1, chosen per b for the better warp mapping).  Outputs n in box_n(b) = [nlo, nlo + L),
+// inner s in box_s(b) = [slo, slo + S) per dimension; the beta rectangle a = n - s is staged as rows
+// [a_ulo, a_ulo + Au) x columns [a_wlo, a_wlo + Aw) (one spare column on the left); Gg groups of RW
+// outputs along w; the warp split: J chunks of the s_u range (chunk rows each), tpw = 32 / J tasks
+// per warp unit (lanes >= J tpw idle), `units` warp units covering base = L_u Gg tasks, numbered with
+// the group fastest (orient 0) or the row fastest (orient 1) so that the lanes of a warp touch
+// distinct shared-memory banks; ginv = ceil(2^16 / Gg), linv = ceil(2^16 / L_u) (division by
+// multiply-shift).
 struct ItemMeta {
-    int ib, ginv;
-    short b1, b2, nlo1, nlo2, L2, slo1, S1, slo2, S2, Gg, A1, A2, a1lo, a2lo, quad, J, tpw, chunk, units, base;
-    short pad[8];
+    int ib, ginv, linv;
+    short orient, b1, b2, nlo_u, nlo_w, Lu, Lw, slo_u, Su, slo_w, Sw, Gg, Au, Aw, a_ulo, a_wlo, quad, J, tpw, chunk,
+        units, base;
+    short pad[4];
 };
 static_assert(sizeof(ItemMeta) == 64, "ItemMeta is 64 bytes");
 
@@ -146,24 +153,30 @@ struct WorkList {
     int* items = nullptr;   // flat extended index of b, sorted by descending work
     int count = 0;
     double terms = 0;       // sum over items of |box_n| |box_s|
-    ItemMeta* meta[2] = {nullptr, nullptr};   // 2-D: per item (same order) for the mixed kernel, RW = 8, 16
+    // 2-D: per item (same order) for the mixed kernel: RW = 8, 8 with the per-b orientation choice,
+    // 16, 16 with orientation
+    ItemMeta* meta[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
-// The warp split of one b for a CTA of `warps` warps (shared by the host metadata and tests).
-inline void choose_split_host(int base, int S1, int warps, int* J, int* chunk, int* units) {
+// The warp split of one b for a CTA of `warps` warps: J in {1, 2, 4, 8} chunks of the S_u rows,
+// tpw = 32 / J tasks per warp unit; minimises rounds x chunk (sweep rows per lane).  Returns that
+// cost.  (Other J would balance the warps a little better by the row count, but their ordered
+// shuffle reduction and idle lanes cost more than they save.)
+inline int choose_split_host(int base, int Su, int warps, int* J, int* chunk, int* units) {
     int bestJ = 1, best = 0x7fffffff;
     for (int j = 1; j <= 8; j <<= 1) {
         const int tpw = 32 / j;
         const int u = (base + tpw - 1) / tpw;
-        const int cost = ((u + warps - 1) / warps) * ((S1 + j - 1) / j);
+        const int cost = ((u + warps - 1) / warps) * ((Su + j - 1) / j);
         if (cost < best) {
             best = cost;
             bestJ = j;
         }
     }
     *J = bestJ;
-    *chunk = (S1 + bestJ - 1) / bestJ;
+    *chunk = (Su + bestJ - 1) / bestJ;
     *units = (base + 32 / bestJ - 1) / (32 / bestJ);
+    return best;
 }
 
 }  // namespace bn
@@ -183,7 +196,8 @@ struct bn_solver {
     bn::WorkList work_quad;      // b in I_N (quadratic part only, eps == 0)
     int n_partials = 0;          // CTAs of the triple-sum kernel (rows of the partial buffer)
     int mixed_rw = 8;            // outputs per thread of the mixed 2-D kernel (N <= 32)
-    float tune_ms[2] = {0, 0};   // autotuner timings of RW = 8, 16 (0 = not timed)
+    int mixed_v = 0;             // its metadata variant (index into work.meta)
+    float tune_ms[4] = {0, 0, 0, 0};   // autotuner timings of the four variants (0 = not timed)
 
     // device buffers
     double* f = nullptr;         // state, N^d

@@ -62,6 +62,7 @@ size_t table_bytes(const bn_request& r) {
                               : (size_t)(r.opt.M1 > 0 ? r.opt.M1 : r.N / 2) * (r.opt.M2 > 0 ? r.opt.M2 : r.N / 2);
     size_t b = 2 * P * nExt * sizeof(double) + nExt * nExt * (sizeof(double) + sizeof(float));
     if (r.d == 2) b += nExt * nm * (sizeof(double) + 2 * sizeof(float));   // reducible and quadratic weights
+    if (r.d == 2 && r.N <= 32) b += nExt * nExt * sizeof(float);          // transposed FP32 table
     return b;
 }
 

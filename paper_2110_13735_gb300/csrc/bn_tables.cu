@@ -177,6 +177,18 @@ __global__ void k_dq_table(int N, const double* __restrict__ beta, float* __rest
     }
 }
 
+// FP32 table with the a axes swapped: betaT[b][a2][a1] = beta[b][a1][a2] (2-D).
+__global__ void k_beta_transpose(int N, const float* __restrict__ beta32, float* __restrict__ beta32T) {
+    const int E = 2 * N, nExt = E * E;
+    const long long total = (long long)nExt * nExt;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long ib = idx / nExt;
+        const int ia = (int)(idx % nExt), a2 = ia / E, a1 = ia % E;   // destination [a2][a1]
+        beta32T[idx] = beta32[ib * nExt + a1 * E + a2];
+    }
+}
+
 // Gauss-Legendre rule on [-1, 1]: Newton iteration on P_n from Tricomi's initial guesses.
 void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
     x.assign(n, 0.0);
@@ -280,17 +292,19 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw32, sizeof(float) * nSw);
     const size_t nDq = d == 2 ? (size_t)s->g.nModes * nExt : 0;
     if (e == cudaSuccess && nDq) e = cudaMalloc(&t->dq32, sizeof(float) * nDq);
+    const size_t nBT = d == 2 && s->g.N <= 32 ? nBeta : 0;
+    if (e == cudaSuccess && nBT) e = cudaMalloc(&t->beta32T, sizeof(float) * nBT);
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
         cudaFree(d_nodes);
         cudaFree(d_rad);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
-        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32);
+        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
         delete t;
         cudaGetLastError();
         return BN_ERR_NOMEM;
     }
-    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw) + sizeof(float) * nDq;
+    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw) + sizeof(float) * (nDq + nBT);
     cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
     if (d_rad) cudaMemcpyAsync(d_rad, rad.data(), sizeof(double2) * rad.size(), cudaMemcpyHostToDevice, s->stream);
     k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, s->kernel, (int)rad.size(),
@@ -302,6 +316,10 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
         k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
         k_dq_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->dq32);
         s->launches++;
+        if (nBT) {
+            k_beta_transpose<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta32, t->beta32T);
+            s->launches++;
+        }
         s->launches++;
     }
     e = cudaStreamSynchronize(s->stream);
@@ -311,7 +329,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
-        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32);
+        cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
         delete t;
         return BN_ERR_CUDA;
     }
@@ -333,6 +351,7 @@ void release_tables(KernelTables* t) {
     cudaFree(t->sw64);
     cudaFree(t->sw32);
     cudaFree(t->dq32);
+    cudaFree(t->beta32T);
     delete t;
 }
 
@@ -396,31 +415,46 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
     }
     cudaMemcpy(s->work.items, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(s->work_quad.items, qflat.data(), sizeof(int) * qflat.size(), cudaMemcpyHostToDevice);
-    for (int v = 0; d == 2 && v < 2; ++v) {
-        // per-item geometry of the mixed kernel (8 warps per CTA, RW = 8 or 16 outputs per thread)
-        const int RW = v == 0 ? 8 : 16;
+    for (int v = 0; d == 2 && v < 4; ++v) {
+        // per-item geometry of the mixed kernel (8 warps per CTA, RW = 8 or 16 outputs per thread,
+        // with or without the per-b orientation choice)
+        const int RW = v < 2 ? 8 : 16;
+        const bool orientable = (v & 1) != 0;
         std::vector<ItemMeta> meta(flat.size());
         const int h = N / 2;
         for (size_t i = 0; i < flat.size(); ++i) {
             const int ib = flat[i], b1 = ib / E - N, b2 = ib % E - N;
-            const int nlo1 = std::max(-h, b1 - h), L1 = std::min(h - 1, b1 + h - 1) - nlo1 + 1;
-            const int nlo2 = std::max(-h, b2 - h), L2 = std::min(h - 1, b2 + h - 1) - nlo2 + 1;
-            const int slo1 = std::max(-h, b1 - h + 1), S1 = std::min(h - 1, b1 + h) - slo1 + 1;
-            const int slo2 = std::max(-h, b2 - h + 1), S2 = std::min(h - 1, b2 + h) - slo2 + 1;
-            const int Gg = (L2 + RW - 1) / RW, base = L1 * Gg;
-            int J, chunk, units;
-            choose_split_host(base, S1, 8, &J, &chunk, &units);
+            const int bb[2] = {b1, b2};
+            int nlo[2], L[2], slo[2], S[2];
+            for (int dd = 0; dd < 2; ++dd) {
+                nlo[dd] = std::max(-h, bb[dd] - h);
+                L[dd] = std::min(h - 1, bb[dd] + h - 1) - nlo[dd] + 1;
+                slo[dd] = std::max(-h, bb[dd] - h + 1);
+                S[dd] = std::min(h - 1, bb[dd] + h) - slo[dd] + 1;
+            }
             ItemMeta m{};
-            m.ib = ib;
-            m.ginv = (65536 + Gg - 1) / Gg;
-            m.b1 = (short)b1; m.b2 = (short)b2;
-            m.nlo1 = (short)nlo1; m.nlo2 = (short)nlo2; m.L2 = (short)L2;
-            m.slo1 = (short)slo1; m.S1 = (short)S1; m.slo2 = (short)slo2; m.S2 = (short)S2;
-            m.Gg = (short)Gg; m.A1 = (short)(L1 + S1 - 1); m.A2 = (short)(RW * Gg + S2);
-            m.a1lo = (short)(nlo1 - slo1 - S1 + 1); m.a2lo = (short)(nlo2 - slo2 - S2);
-            m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
-            m.J = (short)J; m.tpw = (short)(32 / J); m.chunk = (short)chunk; m.units = (short)units;
-            m.base = (short)base;
+            long long best = -1;
+            for (int o = 0; o < (orientable ? 2 : 1); ++o) {   // o = 0: split dim 1, window along dim 2; 1: swapped
+                const int du = o == 0 ? 0 : 1, dw = 1 - du;
+                const int Gg = (L[dw] + RW - 1) / RW, base = L[du] * Gg;
+                int J, chunk, units;
+                const long long cost = (long long)choose_split_host(base, S[du], 8, &J, &chunk, &units) * S[dw];
+                if (best >= 0 && cost >= best) continue;
+                best = cost;
+                m.ib = ib;
+                m.ginv = (65536 + Gg - 1) / Gg;
+                m.linv = (65536 + L[du] - 1) / L[du];
+                m.Lu = (short)L[du];
+                m.orient = (short)o;
+                m.b1 = (short)b1; m.b2 = (short)b2;
+                m.nlo_u = (short)nlo[du]; m.nlo_w = (short)nlo[dw]; m.Lw = (short)L[dw];
+                m.slo_u = (short)slo[du]; m.Su = (short)S[du]; m.slo_w = (short)slo[dw]; m.Sw = (short)S[dw];
+                m.Gg = (short)Gg; m.Au = (short)(L[du] + S[du] - 1); m.Aw = (short)(RW * Gg + S[dw]);
+                m.a_ulo = (short)(nlo[du] - slo[du] - S[du] + 1); m.a_wlo = (short)(nlo[dw] - slo[dw] - S[dw]);
+                m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
+                m.J = (short)J; m.tpw = (short)(32 / J); m.chunk = (short)chunk; m.units = (short)units;
+                m.base = (short)base;
+            }
             meta[i] = m;
         }
         if (cudaMalloc(&s->work.meta[v], sizeof(ItemMeta) * meta.size()) != cudaSuccess) {

@@ -63,6 +63,8 @@ def test_create_rejects_bad_escalation_threshold(lib):
     assert lib.bn_create_solver(2, 16, 13.3, 6.0, 0, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == -1
     assert b"mixed_rw" in lib.bn_last_error()
     assert lib.bn_kernel_config(None, None, 0) == -1
+    o = B.options(precision=B.MIXED, mixed_variant=5)
+    assert lib.bn_create_solver(2, 16, 13.3, 6.0, 0, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == -1
 
 
 def test_null_handles(lib):

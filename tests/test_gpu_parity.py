@@ -123,14 +123,30 @@ def test_mixed_kernel_variants(B, N, eps, rw):
 
 def test_autotuner_choice(B):
     with B.Solver(2, 20, T6, R6, B.MAXWELL, 1.0, precision=B.MIXED) as s:
-        rw, ctas, t8, t16 = s.kernel_config()
-    assert rw in (8, 16) and ctas >= 1
-    if t8 > 0 and t16 > 0:   # timed here (not cached by an earlier solver of this N)
-        assert rw == (8 if t8 <= t16 else 16)
+        rw, ctas, oriented, ms = s.kernel_config()
+    assert rw in (8, 16) and ctas >= 1 and oriented in (0, 1)
+    if all(t > 0 for t in ms):   # timed here (not cached by an earlier solver of this N)
+        assert 2 * (rw == 16) + oriented == int(np.argmin(ms))
     with B.Solver(2, 20, T6, R6, B.MAXWELL, 1.0, precision=B.MIXED) as s2:
-        assert s2.kernel_config()[0] == rw   # cached per (device, N)
+        assert s2.kernel_config()[:3] == (rw, ctas, oriented)   # cached per (device, N)
     with B.Solver(2, 20, T6, R6, B.MAXWELL, 1.0) as s3:
         assert s3.kernel_config()[0] == 0    # FP64 has no such choice
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_mixed_kernel_forced_variants(B, variant):
+    """Every variant of the mixed kernel (8 / 16 outputs per thread, with and without the per-b
+    orientation choice) against the oracle, 2-D hard spheres N = 24 and Maxwell N = 32."""
+    for kernel, N, eps, kind in ((1, 24, -1.0, "two"), (0, 32, 1.0, "gauss")):
+        f = _f0(2, N, kind)
+        ora = O.Operator(2, N, T6, R6, kernel, eps, M=2 * N)
+        Q_o, gain, _, _ = ora.eval_collision(f, parts=True)
+        with B.Solver(2, N, T6, R6, kernel, eps, precision=B.MIXED, mixed_variant=variant) as s:
+            s.set_state(f)
+            Q_g = s.eval_collision()
+            cfg = s.kernel_config()
+        assert cfg[0] == (8 if variant <= 2 else 16) and cfg[2] == (variant - 1) % 2
+        assert rel(Q_g, Q_o, gain) <= 2e-6
 
 
 @pytest.mark.parametrize("integrator", [0, 1])
