@@ -81,12 +81,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ double2 cfma_d(double2 acc, double2 a, double2 b) {
-    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-    return acc;
-}
-
 template <typename Real>
 __device__ __forceinline__ double2 to_d2(cplx<Real> c) { return make_double2((double)c.x, (double)c.y); }
 
@@ -124,8 +118,8 @@ struct Layout2D {
     }
     // one buffer: the staged beta rectangle, reused for the split sums after the sweep
     static __host__ __device__ size_t slot(int N, int nt) {
-        const size_t bs = STAGE ? (size_t)(2 * N) * stride(N) * sizeof(Real) : 0;
         const size_t cp = (size_t)nt * RW * sizeof(cplx<Real>);
+        const size_t bs = STAGE ? (size_t)(2 * N) * stride(N) * sizeof(Real) : cp;
         return ((bs > cp ? bs : cp) + 15) / 16 * 16;
     }
     static __host__ __device__ size_t bytes(int N, int nt) {
@@ -592,23 +586,11 @@ void launch_group_t(cudaStream_t st, const void* d_jobs, const int* d_cta, int n
 
 }  // namespace
 
-// Double-buffered staging for mixed precision N <= 32 (3 CTAs/SM) or single buffer (4 CTAs/SM);
-// BN_FUSED_DB=0 selects the single buffer.
-static bool fused_db() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("BN_FUSED_DB");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
-
-// Variants: mixed precision N <= 32: FP32, 8 outputs per thread, 256 threads, double-buffered
-// staging; mixed N = 64: single buffer (shared memory); FP64: 2 outputs per thread (DFMA-bound),
-// staged for N <= 32, read through L1 for N = 64.
+// Kernels: mixed precision N <= 32: k_mixed2d (bn_fused2d_mixed.cu); mixed N > 32: this file's
+// kernel in FP32 with 8 outputs per thread and a single staging buffer (shared memory); FP64:
+// 2 outputs per thread (DFMA-bound), staged for N <= 32, read through L1 for N > 32.
 void configure_fused2d() {
     configure_mixed2d();
-    configure_one<float, 8, 256, true, true>();
     configure_one<float, 8, 256, true, false>();
     configure_one<double, 2, 128, true, false>();
     configure_one<double, 2, 256, false, false>();
