@@ -135,8 +135,8 @@ def source_sha(path: str) -> str:
 def recorded_traffic():
     """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the
     kernel source is unchanged since it was captured; else None."""
-    src = os.path.join(ROOT, "paper_2110_13735_gb300", "csrc", "bn_fused2d.cu")
-    rec = os.path.join(ROOT, "profiles", "fused2d_traffic.json")
+    src = os.path.join(ROOT, "paper_2110_13735_gb300", "csrc", "bn_fused2d_mixed.cu")
+    rec = os.path.join(ROOT, "profiles", "mixed2d_traffic.json")
     if not os.path.exists(rec):
         return None
     try:
@@ -146,6 +146,14 @@ def recorded_traffic():
     except Exception:
         return None
     return None
+
+
+def workload_config(ws: int) -> dict:
+    """The `config` of both arms' JSON lines (the same workload)."""
+    return {"workload": "2-D Maxwell molecules N=32 R=6 T=(3+sqrt2)R/2: BKW eps=0 (t0=1) + Gaussian "
+                        "(mass 5, T 0.5) eps=+1, RK4 dt=0.005, mixed precision",
+            "d": 2, "N": N_MODES, "requests_per_gpu": 2, "parallelism": f"replicas x{ws}",
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)"}
 
 
 def make_pair(bn, I, precision, stream, mixed_rw=0):
@@ -310,10 +318,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "2-D Maxwell molecules N=32 R=6 T=(3+sqrt2)R/2: BKW eps=0 (t0=1) + Gaussian "
-                                   "(mass 5, T 0.5) eps=+1, RK4 dt=0.005, mixed precision",
-                       "d": 2, "N": N_MODES, "requests_per_gpu": 2, "parallelism": f"replicas x{ws}",
-                       "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
+            "config": workload_config(ws),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
                     "steps": e2e_steps},
             "roofline": roofline,
@@ -364,7 +369,7 @@ def serving_run(bn, I, reqs, escalate_at: float):
     return np.array(lat), results, wall, stats
 
 
-def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32), escalations=(0.0, 0.55)):
+def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32), escalations=(0.0, 0.5)):
     """The serving mix (N in `Ns`, eps in {-1, 0, +1}, Maxwell molecules or hard spheres, two-Gaussian
     data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2) through the continuous-batching server,
     once per escalation threshold, against a stratified sample of the same requests solved one at a
@@ -453,8 +458,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "2-D Maxwell molecules N=32 R=6: BKW eps=0 + Gaussian (mass 5, T 0.5) eps=+1, "
-                               "oracle sample", "d": 2, "N": N_MODES},
+        "config": workload_config(ws),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

@@ -1,8 +1,9 @@
 // bn_batch.cu -- many 2-D requests advanced together: every stage of one RK step of all
-// requests runs as a fixed set of shared launches (transforms, the fused operator per
-// precision/size variant, partial sums, stage updates), captured once per set of requests
-// as one CUDA graph.  Each request keeps its own CTA partition, so its result is identical
-// to the one it gets alone.
+// requests runs as a fixed set of shared launches, captured once per set of requests as one CUDA
+// graph.  Per evaluation: the second forward transform pass, the S(b) kernel and the fused
+// operator per precision/size group, the partial sums, the first inverse pass, and one row kernel
+// with the last inverse pass, the RK update and the first forward pass of the next stage.  Each request keeps its own CTA partition and every output keeps the arithmetic of
+// the single-request kernels, so its result is identical to the one it gets alone.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -112,6 +113,63 @@ __global__ void k_dft_batch(const ElemJob* __restrict__ jobs, int pass, int stag
                 }
             }
         }
+    }
+}
+
+// The RK update of one entry after its stage derivative K (as in k_dft_batch, pass 3).
+__device__ __forceinline__ void rk_entry(const ElemJob& J, int idx, double K, int rk, double w_acc, double c_next,
+                                         int first) {
+    J.Qv[idx] = K;
+    if (rk == 1) {
+        J.kacc[idx] = first ? w_acc * K : fma(w_acc, K, J.kacc[idx]);
+        J.y[idx] = fma(c_next * J.dt, K, J.f[idx]);
+    } else if (rk >= 2) {
+        const double v = rk == 2 ? fma(J.dt / 6.0, J.kacc[idx] + K, J.f[idx]) : 0.5 * (J.f[idx] + fma(J.dt, K, J.y[idx]));
+        J.cand[idx] = v;
+        if (!isfinite(v)) atomicOr(&J.flags[0], 1);
+    }
+}
+
+// Row j1 = blockIdx.x of job blockIdx.y: the last inverse pass (work_c along n_2 -> Q), the RK update
+// of the row and, for an RK stage (rk == 1), the first forward pass of the next evaluation on the
+// new stage argument y (along n_2 -> work_c).  Each output is one warp with the lanes over the
+// summation index and the same butterfly as k_dft_batch, so the values are bitwise those of the
+// separate launches.  N <= 64.
+__global__ void __launch_bounds__(256) k_row_inv_rk_fwd(const ElemJob* __restrict__ jobs, int rk, double w_acc,
+                                                       double c_next, int first) {
+    __shared__ double ysh[64];
+    const ElemJob J = jobs[blockIdx.y];
+    const int N = J.N, j1 = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (j1 >= N) return;   // uniform per block
+    const int base = j1 * N;
+    for (int c = warp; c < N; c += 8) {   // pass 3: output (j1, c)
+        const int k = c - N / 2;
+        double sr = 0.0, si = 0.0;
+        for (int jj = lane; jj < N; jj += 32) {
+            const double2 w = tw_at(J.tw, k, jj - N / 2, N, +1);
+            const double2 x = J.work_c[base + jj];
+            sr = fma(x.x, w.x, fma(-x.y, w.y, sr));
+            si = fma(x.x, w.y, fma(x.y, w.x, si));
+        }
+        const double2 sum = warp_sum2(sr, si);
+        if (lane == 0) {
+            rk_entry(J, base + c, sum.x * J.scale, rk, w_acc, c_next, first);
+            if (rk == 1) ysh[c] = J.y[base + c];
+        }
+    }
+    if (rk != 1) return;   // uniform
+    __syncthreads();
+    for (int c = warp; c < N; c += 8) {   // pass 0 of the next evaluation: output (j1, c)
+        const int k = c - N / 2;
+        double sr = 0.0, si = 0.0;
+        for (int jj = lane; jj < N; jj += 32) {
+            const double2 w = tw_at(J.tw, k, jj - N / 2, N, -1);
+            const double x = ysh[jj];
+            sr = fma(x, w.x, sr);
+            si = fma(x, w.y, si);
+        }
+        const double2 sum = warp_sum2(sr, si);
+        if (lane == 0) J.work_c[base + c] = sum;
     }
 }
 
@@ -241,30 +299,43 @@ void destroy_plan(BatchPlan* p) {
 }
 
 // One evaluation of every request's operator; with rk != 0 (no request projects Q) the RK update
-// that follows is fused into the last transform pass (arguments as for k_dft_batch).
+// that follows is fused into the last transform pass (arguments as for k_dft_batch): per row, the
+// last inverse pass, the RK update and, for an RK stage, the first forward pass of the next
+// evaluation run as one launch (fwd0_done: this evaluation's first pass was done that way).
 static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in, int rk = 0, double w_acc = 0.0,
-                                double c_next = 0.0, int first = 0) {
+                                double c_next = 0.0, int first = 0, bool fwd0_done = false) {
     const int nj = (int)p->solvers.size();
     const dim3 gw((p->maxNm * 32 + kThreads - 1) / kThreads, nj);
-    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
+    if (!fwd0_done) {
+        k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
+        p->launches++;
+    }
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
+    p->launches++;
     for (auto& g : p->groups)
         if ((g.variant == 0 || g.variant == 4) && g.maxCount > 0) {
             launch_mixed2d_sred_group(st, g.d_jobs, g.njobs, g.maxCount);
             p->launches++;
         }
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
+    p->launches += (long long)p->groups.size();
     k_sum_partials_batch<<<dim3((p->maxNm + kPartModes - 1) / kPartModes, nj), 256, 0, st>>>(p->d_elem, p->d_time);
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
-    k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in, rk, w_acc, c_next, first);
-    p->launches += 5 + (long long)p->groups.size();
-    for (bn_solver* s : p->solvers)
-        if (s->opt.conserve) {
-            cudaStream_t own = s->stream;   // the projection kernel joins the capture on the shared stream
-            s->stream = st;
-            launch_conserve(s, s->Qv);
-            s->stream = own;
-        }
+    p->launches += 2;
+    if (rk == 0) {   // requests project Q: the last pass, the projection, then the RK kernels
+        k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in);
+        p->launches++;
+        for (bn_solver* s : p->solvers)
+            if (s->opt.conserve) {
+                cudaStream_t own = s->stream;   // the projection kernel joins the capture on the shared stream
+                s->stream = st;
+                launch_conserve(s, s->Qv);
+                s->stream = own;
+            }
+        return;
+    }
+    k_row_inv_rk_fwd<<<dim3(p->maxN, nj), 256, 0, st>>>(p->d_elem, rk, w_acc, c_next, first);
+    p->launches++;
 }
 
 bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, cudaStream_t st, BatchPlan** out,
@@ -358,7 +429,7 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         for (int stage = 0; stage < 4; ++stage) {
             if (fuse_rk) {
                 record_batched_eval(p, st, stage == 0 ? 0 : 1, stage < 3 ? 1 : 2, stage < 3 ? wacc[stage] : 0.0,
-                                    stage < 3 ? cnext[stage] : 0.0, stage == 0);
+                                    stage < 3 ? cnext[stage] : 0.0, stage == 0, stage > 0);
                 continue;
             }
             record_batched_eval(p, st, stage == 0 ? 0 : 1);
@@ -373,7 +444,7 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         }
     } else if (fuse_rk) {
         record_batched_eval(p, st, 0, 1, 0.0, 1.0, 1);
-        record_batched_eval(p, st, 1, 3);
+        record_batched_eval(p, st, 1, 3, 0.0, 0.0, 0, true);
     } else {
         record_batched_eval(p, st, 0);
         k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, 0.0, 1.0, 1);
