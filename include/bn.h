@@ -232,9 +232,11 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
  * the initial state f0 (N^d FP64 values on the grid, row-major), the step dt
  * and the final time t_end (steps = round(t_end / dt) of the chosen
  * integrator, from t = 0).  bn_server_submit copies f0 and returns at once; a
- * worker thread owned by the server admits queued requests in arrival order as
- * long as the device-memory budget allows (the kernel-mode tables of one
- * operator are shared and counted once), advances all running requests
+ * worker thread owned by the server admits queued requests, the one with the
+ * least estimated work (steps x terms per evaluation) first and, past 60 s in
+ * the queue, the oldest first, as long as max_active and the device-memory
+ * budget allow (the kernel-mode tables of one operator are shared and counted
+ * once), advances all running requests
  * together in shared launches (a few RK steps per tick; 2-D requests in one
  * captured graph per set of running requests), and retires finished requests
  * with their final state copied to host memory.  A request's result does not

@@ -2,7 +2,8 @@
 //
 // Requests (homogeneous Boltzmann-Nordheim solves: operator, initial state, dt, t_end) are
 // queued by any thread.  One worker thread owns the GPU work: at every tick it admits
-// queued requests in arrival order while the device-memory budget allows (kernel-mode
+// queued requests, the one with the least estimated work first (a request queued for longer
+// than kMaxWait seconds goes first), while slots and the device-memory budget allow (kernel-mode
 // tables are shared by requests with the same operator and counted once), advances every
 // active request by a few RK steps in shared launches (bn_step_rk_batch: one captured graph
 // for the whole active set), and retires finished requests, copying their final state to
@@ -34,6 +35,7 @@ struct ServerReq {
     int state = 0;   // 0 queued, 1 running, 2 done, 3 failed
     double t_submit = 0, t_admit = 0, t_done = 0;
     long long steps_total = 0, steps_done = 0;
+    double work = 0;   // estimated work: steps x terms of one evaluation
     bn_solver* s = nullptr;
     size_t bytes = 0;
     std::string err;
@@ -131,13 +133,21 @@ void bn_server::retire(ServerReq* q, bool ok, const std::string& err) {
     cv.notify_all();
 }
 
+// Queued requests older than this are admitted before any shorter one (no starvation).
+constexpr double kMaxWait = 60.0;
+
 void bn_server::admit_locked(std::unique_lock<std::mutex>& lock) {
     while (!pending.empty() && (int)active.size() < max_active) {
-        ServerReq* q = pending.front();
+        // the least estimated work first (ties: arrival order), unless the oldest waited too long
+        auto pick = pending.begin();
+        if (now() - pending.front()->t_submit <= kMaxWait)
+            for (auto it = pending.begin(); it != pending.end(); ++it)
+                if ((*it)->work < (*pick)->work) pick = it;
+        ServerReq* q = *pick;
         const std::string key = table_key(q->r);
         const size_t need = solver_bytes(q->r) + (table_refs.count(key) ? 0 : table_bytes(q->r));
         if (bytes_in_use + need > budget && !active.empty()) break;   // wait for memory to free up
-        pending.pop_front();
+        pending.erase(pick);
         in_flight++;
         q->bytes = solver_bytes(q->r);
         bytes_in_use += need;
@@ -257,6 +267,13 @@ bn_status bn_server_submit(bn_server* S, const bn_request* r, const double* f0, 
     q->f0.assign(f0, f0 + count);
     q->steps_total = (long long)std::llround(r->t_end / r->dt);
     if (q->steps_total < 1) q->steps_total = 1;
+    {
+        // terms of one evaluation: the Q_{1,q} sum when eps != 0, else the quadratic sum; FP64 runs
+        // count 32 times (the FP64 pipe's rate against FP32)
+        const double n = r->N;
+        const double c = r->eps != 0.0 ? std::pow(2.0 * (n * n * n - n) / 3.0, r->d) : std::pow(0.75 * n * n, r->d);
+        q->work = (double)q->steps_total * c * (r->opt.precision == BN_MIXED ? 1.0 : 32.0);
+    }
     std::lock_guard<std::mutex> lock(S->mu);
     q->id = S->next_id++;
     q->t_submit = S->now();

@@ -5,6 +5,8 @@ result as alone (bitwise: every request keeps its own CTA partition and reductio
 server's results match the FP64 oracle."""
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 
@@ -102,6 +104,24 @@ def test_server_admission_by_memory(B):
         assert all(srv.poll(i)[0] == 2 for i in ids)
         st = srv.stats()
         assert st["max_active"] <= 2 and st["done"] == 5
+
+
+def test_server_admits_least_work_first(B):
+    """With one slot busy, of two queued requests the one with less estimated work (steps x terms
+    per evaluation) is admitted first, whatever the submission order."""
+    with B.Server(max_active=1) as srv:
+        blocker = srv.submit(2, 16, T6, R6, B.MAXWELL, 1.0, _f0(16, 0), 0.01, 1.0)   # 100 steps
+        deadline = time.monotonic() + 60
+        while srv.poll(blocker)[0] == 0 and time.monotonic() < deadline:
+            time.sleep(0.001)
+        assert srv.poll(blocker)[0] >= 1
+        big = srv.submit(2, 32, T6, R6, B.MAXWELL, 1.0, _f0(32, 1), 0.01, 0.05)
+        small = srv.submit(2, 16, T6, R6, B.MAXWELL, 0.0, _f0(16, 2), 0.01, 0.05)
+        srv.wait_idle(300)
+        t_blk, t_big, t_small = (srv.poll(i)[2] for i in (blocker, big, small))
+        assert all(srv.poll(i)[0] == 2 for i in (blocker, big, small))
+    assert t_small[1] <= t_big[1]      # admission times
+    assert t_small[1] >= t_blk[1]
 
 
 def test_server_failed_request(B):
