@@ -13,9 +13,10 @@
 //  * The beta rectangle (box_n - box_s) of the next b is copied into shared memory asynchronously
 //    and its P_b formed while the current b is swept: one CTA barrier per b.
 //  * The sweep is split into warp units.  A unit is 32/J (output row, group of 8 outputs along n_2)
-//    tasks times J chunks of the s_1 range (J in {1, 2, 4, 8}, chosen per b to balance the warps);
-//    the J partial sums of a task meet by warp shuffles, so no shared-memory reduction or extra
-//    barrier is needed, and the lanes of the chunks share the epilogue.
+//    tasks times J chunks of the s_1 range (J in {1, 2, 4, 8}, chosen per b from an issue-cost model
+//    of the busiest warp); the J partial sums of a task meet by a shuffle reduce-scatter, so no
+//    shared-memory reduction or extra barrier is needed, and each of the J lanes finishes 8/J of
+//    the task's outputs.
 //  * Each thread keeps 8 outputs in registers; along s_2 the weights beta(n-s, b) slide through a
 //    register window (one shared load of beta, one of P_b, 16 FFMA per step).
 //  * G^_{n-b} D_b(n) is added to an FP32 (sum, compensation) pair per output in shared memory
@@ -138,17 +139,27 @@ struct Geo {
 // columns whose a_w falls outside [-N, N) are zero-filled.
 __device__ __forceinline__ void stage_beta(float* Bs, const float* __restrict__ beta, const float* __restrict__ betaT,
                                            const ItemMeta& m, int N, int WS) {
+    constexpr int kCB = 3;   // column blocks of 32: rectangles up to 96 columns wide (N <= 32 needs 64)
     const int E = 2 * N, Au = m.Au, Aw = m.Aw, lane = threadIdx.x & 31;
     const int clo = -N - m.a_wlo, chi = N - m.a_wlo;   // valid columns [clo, chi)
     const float* __restrict__ src0 =
         (m.orient ? betaT : beta) + (size_t)m.ib * E * E + (m.a_ulo + N) * E + N + m.a_wlo;
+    // the column predicates and source offsets are the same in every row
+    bool in[kCB], ok[kCB];
+    int off[kCB];
+#pragma unroll
+    for (int q = 0; q < kCB; ++q) {
+        const int c = lane + 32 * q;
+        in[q] = c < Aw;
+        ok[q] = c >= clo && c < chi;
+        off[q] = ok[q] ? c : 0;
+    }
     for (int r = threadIdx.x >> 5; r < Au; r += kNW) {
         const float* __restrict__ src = src0 + r * E;
-        float* dst = Bs + r * WS;
-        for (int c = lane; c < Aw; c += 32) {
-            const bool ok = c >= clo && c < chi;
-            cp4(dst + c, ok ? src + c : src0, ok);
-        }
+        float* dst = Bs + r * WS + lane;
+#pragma unroll
+        for (int q = 0; q < kCB; ++q)
+            if (in[q]) cp4(dst + 32 * q, src + off[q], ok[q]);
     }
 }
 
@@ -217,6 +228,20 @@ __device__ __forceinline__ void row_sweep(const float* __restrict__ brow, int c0
             ar[r] = fmaf(wr, p.x, ar[r]);
             ai[r] = fmaf(wr, p.y, ai[r]);
         }
+    }
+}
+
+// One halving step of the shuffle reduce-scatter over the first L of the kRW sums: the lane keeps
+// entries [0, L/2) (hi false) or [L/2, L) (hi true), adds the partner's copy (lane ^ mk) of the same
+// entries and stores them in [0, L/2).
+template <int kRW, int L>
+__device__ __forceinline__ void reduce_half(float (&ar)[kRW], float (&ai)[kRW], bool hi, int mk) {
+#pragma unroll
+    for (int i = 0; i < L / 2; ++i) {
+        const float sr = hi ? ar[i] : ar[i + L / 2], si = hi ? ai[i] : ai[i + L / 2];
+        const float kr = hi ? ar[i + L / 2] : ar[i], ki = hi ? ai[i + L / 2] : ai[i];
+        ar[i] = kr + __shfl_xor_sync(0xffffffffu, sr, mk);
+        ai[i] = ki + __shfl_xor_sync(0xffffffffu, si, mk);
     }
 }
 
@@ -378,43 +403,40 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                     for (int s1 = s1b; s1 < s1e; ++s1, brow -= WS, prow += PS)
                         row_sweep<kRW>(brow, c0, prow, Sw, ar, ai);
                 }
-                // the J chunk sums of a task (lanes t + tpw j) meet by shuffles: a butterfly when
-                // J is a power of two (tpw J = 32), else in the order j = 0 .. J-1
-                if ((J & (J - 1)) == 0) {
-                    for (int mk = tpw; mk < 32; mk <<= 1) {
-#pragma unroll
-                        for (int r = 0; r < kRW; ++r) {
-                            ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], mk);
-                            ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], mk);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < kRW; ++r) {
-                        float xr = 0.f, xi = 0.f;
-                        for (int j = 0; j < J; ++j) {
-                            xr += __shfl_sync(0xffffffffu, ar[r], t + tpw * j);
-                            xi += __shfl_sync(0xffffffffu, ai[r], t + tpw * j);
-                        }
-                        ar[r] = xr;
-                        ai[r] = xi;
-                    }
+                // the J chunk sums of a task (lanes t + tpw j, J a power of two) meet by a shuffle
+                // reduce-scatter: each halving step keeps half of the outputs, so that afterwards lane
+                // j holds the complete sums of kRW / J outputs, starting at output `off`
+                int off = 0;
+                if (J >= 2) {
+                    const bool hi = (lane & tpw) != 0;
+                    reduce_half<kRW, kRW>(ar, ai, hi, tpw);
+                    off += hi ? kRW / 2 : 0;
+                }
+                if (J >= 4) {
+                    const bool hi = (lane & (2 * tpw)) != 0;
+                    reduce_half<kRW, kRW / 2>(ar, ai, hi, 2 * tpw);
+                    off += hi ? kRW / 4 : 0;
+                }
+                if (J >= 8) {
+                    const bool hi = (lane & (4 * tpw)) != 0;
+                    reduce_half<kRW, kRW / 4>(ar, ai, hi, 4 * tpw);
+                    off += hi ? kRW / 8 : 0;
                 }
                 if (valid) {
-                    const float* qrow = dqb + n_u * eu;
-                    const int on0 = (n_u + h) * su + h * sw;
-                    int rj = 0;   // r mod J
+                    const int cnt = kRW / J;
+                    const int nw1 = nw0 + off;
+                    const float* qrow = dqb + n_u * eu + nw1 * ew;
+                    const int on1 = (n_u + h) * su + h * sw + nw1 * sw;
 #pragma unroll
-                    for (int r = 0; r < kRW; ++r, rj = rj + 1 == J ? 0 : rj + 1) {
-                        const int n_w = nw0 + r;
-                        if (rj != jl || n_w >= nwend) continue;
+                    for (int r = 0; r < kRW; ++r) {
+                        if (r >= cnt || nw1 + r >= nwend) break;
                         float2 D = make_float2(eps_r * (ar[r] + S.x), eps_r * (ai[r] + S.y));
                         if (quad) {
-                            const float wq = __ldg(qrow + n_w * ew);
+                            const float wq = __ldg(qrow + r * ew);
                             D.x = fmaf(wq, gb.x, D.x);
                             D.y = fmaf(wq, gb.y, D.y);
                         }
-                        const int on = on0 + n_w * sw;
+                        const int on = on1 + r * sw;
                         const float2 x = cmulf(Gs[on - bshift], D);
                         kahan(Qs[on].x, Qc[on].x, x.x);
                         kahan(Qs[on].y, Qc[on].y, x.y);

@@ -159,15 +159,19 @@ struct WorkList {
 };
 
 // The warp split of one b for a CTA of `warps` warps: J in {1, 2, 4, 8} chunks of the S_u rows,
-// tpw = 32 / J tasks per warp unit; minimises rounds x chunk (sweep rows per lane).  Returns that
-// cost.  (Other J would balance the warps a little better by the row count, but their ordered
-// shuffle reduction and idle lanes cost more than they save.)
-inline int choose_split_host(int base, int Su, int warps, int* J, int* chunk, int* units) {
+// tpw = 32 / J tasks per warp unit.  Minimises the issue cost of the busiest warp: rounds x (chunk
+// rows x (Sw steps x kStepInstr + kRowInstr) + kUnitInstr), instruction counts per lane of one sweep
+// step (16 FFMA + 2 shared loads), of the per-row work (window load, loop tail) and of the per-unit
+// work (task decode, reduce-scatter, epilogue); the two overheads were calibrated by timing the
+// kernel at N = 32 (a split that ignores them picks J = 8 for most b, with units too short to
+// amortise them).  Returns that cost.
+constexpr int kStepInstr = 18, kRowInstr = 150, kUnitInstr = 400;
+inline int choose_split_host(int base, int Su, int Sw, int warps, int* J, int* chunk, int* units) {
     int bestJ = 1, best = 0x7fffffff;
     for (int j = 1; j <= 8; j <<= 1) {
         const int tpw = 32 / j;
         const int u = (base + tpw - 1) / tpw;
-        const int cost = ((u + warps - 1) / warps) * ((Su + j - 1) / j);
+        const int cost = ((u + warps - 1) / warps) * (((Su + j - 1) / j) * (Sw * kStepInstr + kRowInstr) + kUnitInstr);
         if (cost < best) {
             best = cost;
             bestJ = j;

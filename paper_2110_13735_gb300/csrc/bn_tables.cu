@@ -438,7 +438,7 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
                 const int du = o == 0 ? 0 : 1, dw = 1 - du;
                 const int Gg = (L[dw] + RW - 1) / RW, base = L[du] * Gg;
                 int J, chunk, units;
-                const long long cost = (long long)choose_split_host(base, S[du], 8, &J, &chunk, &units) * S[dw];
+                const long long cost = choose_split_host(base, S[du], S[dw], 8, &J, &chunk, &units);
                 if (best >= 0 && cost >= best) continue;
                 best = cost;
                 m.ib = ib;
