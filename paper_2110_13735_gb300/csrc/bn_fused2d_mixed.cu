@@ -186,48 +186,58 @@ __device__ __forceinline__ void build_P(float2* Pb, const float2* Gs, const Item
     }
 }
 
-// One s_1 row of the Toeplitz product: ar/ai[r] += sum_{s2} beta[c0 + r - s2] P[s2], the weights in a
-// register window whose slots rotate (slot of column x is x mod RW): per step one shared load of
-// beta, one of P and 2 RW FFMA.  Columns read: c0 - S2 + 1 .. c0 + RW - 1.
+// Packed FP32 pairs (sm_100 family): a 64-bit register holding two floats, and the paired FMA
+// fma.rn.f32x2, which rounds each half exactly as fmaf does and issues once for both.
+__device__ __forceinline__ uint64_t dup2(float x) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ void split2(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// One s_1 row of the Toeplitz product: acc[r] += sum_{s2} beta[c0 + r - s2] P[s2] with acc[r] the
+// (real, imaginary) pair of output r, the weights in a register window whose slots rotate (slot of
+// column x is x mod RW) and hold each weight twice, so that one paired FMA serves both halves of
+// P: per step one shared load of beta, one of P and RW paired FMA.  Columns read:
+// c0 - S2 + 1 .. c0 + RW - 1.
 template <int kRW>
-__device__ __forceinline__ void row_sweep(const float* __restrict__ brow, int c0, const float2* __restrict__ prow,
-                                          int S2, float (&ar)[kRW], float (&ai)[kRW]) {
-    float w[kRW];
+__device__ __forceinline__ void row_sweep(const float* __restrict__ brow, int c0, const uint64_t* __restrict__ prow,
+                                          int S2, uint64_t (&acc)[kRW]) {
+    uint64_t w[kRW];
 #pragma unroll
-    for (int r = 0; r < kRW; ++r) w[r] = brow[c0 + r];
+    for (int r = 0; r < kRW; ++r) w[r] = dup2(brow[c0 + r]);
     int sl = 0;
     for (; sl + kRW <= S2; sl += kRW) {
 #pragma unroll
         for (int kk = 0; kk < kRW; ++kk) {
             if (kk == 0) {
-                if (sl > 0) w[0] = brow[c0 - sl];
+                if (sl > 0) w[0] = dup2(brow[c0 - sl]);
             } else {
-                w[kRW - kk] = brow[c0 - sl - kk];
+                w[kRW - kk] = dup2(brow[c0 - sl - kk]);
             }
-            const float2 p = prow[sl + kk];
+            const uint64_t p = prow[sl + kk];
 #pragma unroll
-            for (int r = 0; r < kRW; ++r) {
-                const float wr = w[(r - kk + kRW) % kRW];
-                ar[r] = fmaf(wr, p.x, ar[r]);
-                ai[r] = fmaf(wr, p.y, ai[r]);
-            }
+            for (int r = 0; r < kRW; ++r) acc[r] = fma2(w[(r - kk + kRW) % kRW], p, acc[r]);
         }
     }
 #pragma unroll
     for (int kk = 0; kk < kRW; ++kk) {
         if (sl + kk >= S2) break;
         if (kk == 0) {
-            if (sl > 0) w[0] = brow[c0 - sl];
+            if (sl > 0) w[0] = dup2(brow[c0 - sl]);
         } else {
-            w[kRW - kk] = brow[c0 - sl - kk];
+            w[kRW - kk] = dup2(brow[c0 - sl - kk]);
         }
-        const float2 p = prow[sl + kk];
+        const uint64_t p = prow[sl + kk];
 #pragma unroll
-        for (int r = 0; r < kRW; ++r) {
-            const float wr = w[(r - kk + kRW) % kRW];
-            ar[r] = fmaf(wr, p.x, ar[r]);
-            ai[r] = fmaf(wr, p.y, ai[r]);
-        }
+        for (int r = 0; r < kRW; ++r) acc[r] = fma2(w[(r - kk + kRW) % kRW], p, acc[r]);
     }
 }
 
@@ -383,12 +393,9 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                         gg = tau - irow * Gg;
                     }
                 }
-                float ar[kRW], ai[kRW];
+                uint64_t acc[kRW];
 #pragma unroll
-                for (int r = 0; r < kRW; ++r) {
-                    ar[r] = 0.f;
-                    ai[r] = 0.f;
-                }
+                for (int r = 0; r < kRW; ++r) acc[r] = 0ull;   // (+0.0f, +0.0f)
                 const int n_u = nlo_u + irow;
                 const int nw0 = nlo_w + kRW * gg;
                 if (valid && quad) {
@@ -399,10 +406,13 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                 if (valid) {
                     const int c0 = kRW * gg + Sw;
                     const float* brow = Bs + (n_u - a_ulo - s1b) * WS;
-                    const float2* prow = Pb + (s1b - slo_u) * PS;
+                    const uint64_t* prow = reinterpret_cast<const uint64_t*>(Pb) + (s1b - slo_u) * PS;
                     for (int s1 = s1b; s1 < s1e; ++s1, brow -= WS, prow += PS)
-                        row_sweep<kRW>(brow, c0, prow, Sw, ar, ai);
+                        row_sweep<kRW>(brow, c0, prow, Sw, acc);
                 }
+                float ar[kRW], ai[kRW];
+#pragma unroll
+                for (int r = 0; r < kRW; ++r) split2(acc[r], ar[r], ai[r]);
                 // the J chunk sums of a task (lanes t + tpw j, J a power of two) meet by a shuffle
                 // reduce-scatter: each halving step keeps half of the outputs, so that afterwards lane
                 // j holds the complete sums of kRW / J outputs, starting at output `off`

@@ -369,6 +369,43 @@ double count_reducible_terms(int d, int N) {
     return std::pow((double)N * N, d) + std::pow((double)N * N - 1.0, d);
 }
 
+// Item order of the mixed kernel for a grid of nblk CTAs, which take the items k nblk + j (k = 0,
+// 1, ...) in turn: the items, by estimated cost (descending), are dealt in rounds of nblk, each
+// round's heaviest item to the CTA with the least load so far; the CTAs that receive an item of the
+// last (partial) round are then numbered first, so that every position below the item count is
+// used.  Estimated cost per item = the split cost of its sweep + kItemInstr (staging, P_b, setup).
+// The order changes only which CTA adds an item's terms into its partial sums, not the terms.
+constexpr long long kItemInstr = 500;
+static std::vector<ItemMeta> balance_items(const std::vector<ItemMeta>& meta, const std::vector<long long>& cost,
+                                           int nblk) {
+    const int n = (int)meta.size();
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<long long> load(nblk, 0);
+    std::vector<std::vector<int>> mine(nblk);
+    std::vector<int> ctas(nblk);
+    int last = 0;   // items of the last round
+    for (int k = 0; k < n; k += nblk) {
+        for (int j = 0; j < nblk; ++j) ctas[j] = j;
+        std::stable_sort(ctas.begin(), ctas.end(), [&](int x, int y) { return load[x] < load[y]; });
+        last = std::min(nblk, n - k);
+        for (int i = 0; i < last; ++i) {
+            const int item = order[k + i], c = ctas[i];
+            mine[c].push_back(item);
+            load[c] += cost[item];
+        }
+    }
+    const size_t rounds = n > 0 ? (size_t)((n + nblk - 1) / nblk) : 0;
+    std::vector<int> id(nblk);
+    int first = 0, rest = last;   // CTAs with a last-round item get ids 0 .. last-1
+    for (int j = 0; j < nblk; ++j) id[j] = mine[j].size() == rounds ? first++ : rest++;
+    std::vector<ItemMeta> out(n);
+    for (int j = 0; j < nblk; ++j)
+        for (size_t k = 0; k < mine[j].size(); ++k) out[k * nblk + id[j]] = meta[mine[j][k]];
+    return out;
+}
+
 bn_status build_work_list(bn_solver* s, std::string* err) {
     const int d = s->g.d, N = s->g.N, E = s->g.E;
     std::vector<std::pair<long long, int>> items;
@@ -415,12 +452,16 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
     }
     cudaMemcpy(s->work.items, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(s->work_quad.items, qflat.data(), sizeof(int) * qflat.size(), cudaMemcpyHostToDevice);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (sms <= 0) sms = 152;
     for (int v = 0; d == 2 && v < 4; ++v) {
         // per-item geometry of the mixed kernel (8 warps per CTA, RW = 8 or 16 outputs per thread,
         // with or without the per-b orientation choice)
         const int RW = v < 2 ? 8 : 16;
         const bool orientable = (v & 1) != 0;
         std::vector<ItemMeta> meta(flat.size());
+        std::vector<long long> cost(flat.size());
         const int h = N / 2;
         for (size_t i = 0; i < flat.size(); ++i) {
             const int ib = flat[i], b1 = ib / E - N, b2 = ib % E - N;
@@ -456,7 +497,11 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
                 m.base = (short)base;
             }
             meta[i] = m;
+            cost[i] = best + kItemInstr;
         }
+        configure_mixed2d();
+        const int nblk = std::max(1, std::min((int)flat.size(), mixed2d_ctas_per_sm(N, RW) * sms));
+        meta = balance_items(meta, cost, nblk);
         if (cudaMalloc(&s->work.meta[v], sizeof(ItemMeta) * meta.size()) != cudaSuccess) {
             cudaGetLastError();
             *err = "work list allocation failed";
