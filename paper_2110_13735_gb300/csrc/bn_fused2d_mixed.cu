@@ -366,7 +366,8 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
             const float2* __restrict__ Pb = P0 + k * pstep;
             const int orient = m.orient, b1 = m.b1, b2 = m.b2;
             const int nlo_u = m.nlo_u, nlo_w = m.nlo_w, slo_u = m.slo_u, Su = m.Su, Sw = m.Sw;
-            const int Gg = m.Gg, a_ulo = m.a_ulo, J = m.J, tpw = m.tpw, base = m.base;
+            const int Gg = m.Gg, a_ulo = m.a_ulo, base = m.base;
+            const int umain = m.units, uall = m.units + m.units2;
             const int nwend = nlo_w + m.Lw;
             const int su = orient ? 1 : N, sw = orient ? N : 1;   // flat strides of u and w (modes)
             const int eu = orient ? 1 : E, ew = orient ? E : 1;   // and in the extended box
@@ -377,12 +378,16 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                 gb = Gs[(b1 + h) * N + (b2 + h)];
                 dqb += (size_t)((b1 + h) * N + (b2 + h)) * E * E + (N - b1) * E + (N - b2);   // dq at a = n - b
             }
-            const int jl = lane / tpw, t = lane - jl * tpw;
-            const int s1b = slo_u + jl * m.chunk, s1e = min(slo_u + Su, s1b + m.chunk);
             const int bshift = b1 * N + b2;   // flat offset of n - b from n
-            for (int u = warp; u < m.units; u += kNW) {
-                const int tau = u * tpw + t;
-                const bool valid = jl < J && tau < base;
+            for (int u = warp; u < uall; u += kNW) {
+                // units of the full rounds, then those of the re-split last round
+                const bool tl = u >= umain;
+                const int J = tl ? m.J2 : m.J, chunk = tl ? m.chunk2 : m.chunk;
+                const int lgt = 5 - (31 - __clz(J)), tpw = 1 << lgt;   // tasks per unit, 32 / J
+                const int jl = lane >> lgt, t = lane & (tpw - 1);
+                const int s1b = slo_u + jl * chunk, s1e = min(slo_u + Su, s1b + chunk);
+                const int tau = tl ? m.tail0 + ((u - umain) << lgt) + t : (u << lgt) + t;
+                const bool valid = tau < base;
                 int irow = 0, gg = 0;
                 if (valid) {
                     if (orient) {   // row fastest
@@ -432,8 +437,21 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                     reduce_half<kRW, kRW / 4>(ar, ai, hi, 4 * tpw);
                     off += hi ? kRW / 8 : 0;
                 }
-                if (valid) {
-                    const int cnt = kRW / J;
+                if constexpr (kRW >= 16) {
+                    if (J >= 16) {
+                        const bool hi = (lane & (8 * tpw)) != 0;
+                        reduce_half<kRW, kRW / 8>(ar, ai, hi, 8 * tpw);
+                        off += hi ? kRW / 16 : 0;
+                    }
+                }
+                // more chunks than outputs (a re-split last round): each lane holds one output; the
+                // copies of chunk groups jl, jl + RW, ... meet by a butterfly and group jl < RW stores it
+                for (int mk = kRW * tpw; mk < 32; mk <<= 1) {
+                    ar[0] += __shfl_xor_sync(0xffffffffu, ar[0], mk);
+                    ai[0] += __shfl_xor_sync(0xffffffffu, ai[0], mk);
+                }
+                if (valid && jl < kRW) {
+                    const int cnt = J >= kRW ? 1 : kRW / J;
                     const int nw1 = nw0 + off;
                     const float* qrow = dqb + n_u * eu + nw1 * ew;
                     const int on1 = (n_u + h) * su + h * sw + nw1 * sw;

@@ -145,7 +145,9 @@ struct ItemMeta {
     int ib, ginv, linv;
     short orient, b1, b2, nlo_u, nlo_w, Lu, Lw, slo_u, Su, slo_w, Sw, Gg, Au, Aw, a_ulo, a_wlo, quad, J, tpw, chunk,
         units, base;
-    short pad[4];
+    // the last, partial round of units may use a finer split: units2 units of 32/J2 tasks x J2
+    // chunks (of chunk2 rows) covering the tasks [tail0, base); units then counts full rounds only
+    short J2, chunk2, units2, tail0;
 };
 static_assert(sizeof(ItemMeta) == 64, "ItemMeta is 64 bytes");
 
@@ -159,27 +161,50 @@ struct WorkList {
 };
 
 // The warp split of one b for a CTA of `warps` warps: J in {1, 2, 4, 8} chunks of the S_u rows,
-// tpw = 32 / J tasks per warp unit.  Minimises the issue cost of the busiest warp: rounds x (chunk
-// rows x (Sw steps x kStepInstr + kRowInstr) + kUnitInstr), instruction counts per lane of one sweep
-// step (16 FFMA + 2 shared loads), of the per-row work (window load, loop tail) and of the per-unit
-// work (task decode, reduce-scatter, epilogue); the two overheads were calibrated by timing the
-// kernel at N = 32 (a split that ignores them picks J = 8 for most b, with units too short to
-// amortise them).  Returns that cost.
-constexpr int kStepInstr = 18, kRowInstr = 150, kUnitInstr = 400;
-inline int choose_split_host(int base, int Su, int Sw, int warps, int* J, int* chunk, int* units) {
-    int bestJ = 1, best = 0x7fffffff;
+// tpw = 32 / J tasks per warp unit, units dealt to the warps round-robin.  When the unit count is
+// not a multiple of `warps`, the tasks of the last round may be re-split with J2 in {J .. 32}
+// chunks, so that its work spreads over more warps instead of leaving most of them idle at the
+// barrier that ends the b.  Minimises the issue cost of the busiest warp: per round, chunk rows x
+// (Sw steps x kStepInstr + kRowInstr) + kUnitInstr (+ kStageInstr per butterfly stage when the
+// chunks outnumber the RW outputs of a task), instruction counts per lane of one sweep step (8
+// paired FMA + 2 shared loads + the window duplication), of the per-row work (window load, loop
+// tail) and of the per-unit work (task decode, reduce-scatter, epilogue); the overheads were
+// calibrated by timing the kernel at N = 32.  Returns that cost.
+constexpr int kStepInstr = 18, kRowInstr = 150, kUnitInstr = 400, kStageInstr = 20;
+struct SplitChoice {
+    int J, chunk, units, J2, chunk2, units2, tail0;
+};
+inline int unit_cost_host(int J, int Su, int Sw, int RW) {
+    int c = ((Su + J - 1) / J) * (Sw * kStepInstr + kRowInstr) + kUnitInstr;
+    for (int j = RW; j < J; j <<= 1) c += kStageInstr;
+    return c;
+}
+inline int choose_split_host(int base, int Su, int Sw, int RW, int warps, SplitChoice* out) {
+    int best = 0x7fffffff;
     for (int j = 1; j <= 8; j <<= 1) {
         const int tpw = 32 / j;
         const int u = (base + tpw - 1) / tpw;
-        const int cost = ((u + warps - 1) / warps) * (((Su + j - 1) / j) * (Sw * kStepInstr + kRowInstr) + kUnitInstr);
+        const int tj = unit_cost_host(j, Su, Sw, RW);
+        const int full = u / warps;
+        SplitChoice c{j, (Su + j - 1) / j, u, j, (Su + j - 1) / j, 0, 0};
+        int cost = ((u + warps - 1) / warps) * tj;
+        if (u % warps != 0 && full > 0) {
+            // re-split the tasks of the last round
+            const int tail0 = full * warps * tpw, T = base - tail0;
+            for (int j2 = 2 * j; j2 <= 32; j2 <<= 1) {
+                const int u2 = (T + 32 / j2 - 1) / (32 / j2);
+                const int c2 = full * tj + ((u2 + warps - 1) / warps) * unit_cost_host(j2, Su, Sw, RW);
+                if (c2 < cost) {
+                    cost = c2;
+                    c = SplitChoice{j, (Su + j - 1) / j, full * warps, j2, (Su + j2 - 1) / j2, u2, tail0};
+                }
+            }
+        }
         if (cost < best) {
             best = cost;
-            bestJ = j;
+            *out = c;
         }
     }
-    *J = bestJ;
-    *chunk = (Su + bestJ - 1) / bestJ;
-    *units = (base + 32 / bestJ - 1) / (32 / bestJ);
     return best;
 }
 

@@ -478,8 +478,8 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
             for (int o = 0; o < (orientable ? 2 : 1); ++o) {   // o = 0: split dim 1, window along dim 2; 1: swapped
                 const int du = o == 0 ? 0 : 1, dw = 1 - du;
                 const int Gg = (L[dw] + RW - 1) / RW, base = L[du] * Gg;
-                int J, chunk, units;
-                const long long cost = choose_split_host(base, S[du], S[dw], 8, &J, &chunk, &units);
+                SplitChoice sc;
+                const long long cost = choose_split_host(base, S[du], S[dw], RW, 8, &sc);
                 if (best >= 0 && cost >= best) continue;
                 best = cost;
                 m.ib = ib;
@@ -493,8 +493,9 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
                 m.Gg = (short)Gg; m.Au = (short)(L[du] + S[du] - 1); m.Aw = (short)(RW * Gg + S[dw]);
                 m.a_ulo = (short)(nlo[du] - slo[du] - S[du] + 1); m.a_wlo = (short)(nlo[dw] - slo[dw] - S[dw]);
                 m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
-                m.J = (short)J; m.tpw = (short)(32 / J); m.chunk = (short)chunk; m.units = (short)units;
+                m.J = (short)sc.J; m.tpw = (short)(32 / sc.J); m.chunk = (short)sc.chunk; m.units = (short)sc.units;
                 m.base = (short)base;
+                m.J2 = (short)sc.J2; m.chunk2 = (short)sc.chunk2; m.units2 = (short)sc.units2; m.tail0 = (short)sc.tail0;
             }
             meta[i] = m;
             cost[i] = best + kItemInstr;
