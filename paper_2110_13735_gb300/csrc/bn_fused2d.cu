@@ -27,6 +27,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 
 #include "bn_internal.cuh"
 
@@ -72,6 +73,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+// threads per CTA of the mixed-precision kernel for N > 32 (one CTA per SM, limited by shared memory:
+// 32 warps hide the shared-load latency of the sweep better than 8)
+constexpr int kBigNT = 1024;
 
 
 
@@ -216,10 +221,61 @@ __device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b
 // weights held in a register window whose slots rotate (slot of offset x is x mod RW), so that
 // every step costs one load of beta, half a load of P (pairs, the row starts 16-byte aligned)
 // and 2 RW FMA, with no register moves.
+// FP32 form of the row sweep below: the (real, imaginary) sums of an output and the duplicated
+// weight are packed pairs, so that one paired FMA (fma.rn.f32x2, rounded per half exactly as fmaf)
+// serves both parts of P: per step one load of beta, half a load of P and RW paired FMA.
+template <int RW, typename LoadB>
+__device__ __forceinline__ void row_sweep_f32(LoadB ldb, int c0, const float2* __restrict__ prow, int S2,
+                                              float (&ar)[RW], float (&ai)[RW]) {
+    uint64_t acc[RW], w[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        acc[r] = pack2(ar[r], ai[r]);
+        w[r] = dup2(ldb(c0 + r));
+    }
+    int sl = 0;
+    for (; sl + RW <= S2; sl += RW) {
+#pragma unroll
+        for (int k = 0; k < RW; k += 2) {
+            const ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(prow + sl + k);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kk = k + h;
+                if (kk == 0) {
+                    if (sl > 0) w[0] = dup2(ldb(c0 - sl));
+                } else {
+                    w[RW - kk] = dup2(ldb(c0 - sl - kk));
+                }
+                const uint64_t p = h == 0 ? pp.x : pp.y;
+#pragma unroll
+                for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        if (sl + k >= S2) break;
+        if (k == 0) {
+            if (sl > 0) w[0] = dup2(ldb(c0 - sl));
+        } else {
+            w[RW - k] = dup2(ldb(c0 - sl - k));
+        }
+        const uint64_t p = *reinterpret_cast<const uint64_t*>(prow + sl + k);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - k + RW) % RW], p, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) split2(acc[r], ar[r], ai[r]);
+}
+
 template <typename Real, int RW, typename LoadB>
 __device__ __forceinline__ void row_sweep(LoadB ldb, int c0, const cplx<Real>* __restrict__ prow, int S2,
                                           Real (&ar)[RW], Real (&ai)[RW]) {
     static_assert(RW % 2 == 0, "RW must be even");
+    if constexpr (std::is_same<Real, float>::value) {
+        row_sweep_f32<RW>(ldb, c0, prow, S2, ar, ai);
+        return;
+    }
     Real w[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) w[r] = ldb(c0 + r);
@@ -591,13 +647,13 @@ void launch_group_t(cudaStream_t st, const void* d_jobs, const int* d_cta, int n
 // 2 outputs per thread (DFMA-bound), staged for N <= 32, read through L1 for N > 32.
 void configure_fused2d() {
     configure_mixed2d();
-    configure_one<float, 8, 256, true, false>();
+    configure_one<float, 8, kBigNT, true, false>();
     configure_one<double, 2, 128, true, false>();
     configure_one<double, 2, 256, false, false>();
 }
 
 size_t fused2d_smem(int N, int precision) {
-    if (precision == BN_MIXED) return N > 32 ? Layout2D<float, 8, true, false>::bytes(N, 256) : mixed2d_smem(N, 8);
+    if (precision == BN_MIXED) return N > 32 ? Layout2D<float, 8, true, false>::bytes(N, kBigNT) : mixed2d_smem(N, 8);
     return N > 32 ? Layout2D<double, 2, false, false>::bytes(N, 256) : Layout2D<double, 2, true, false>::bytes(N, 128);
 }
 
@@ -630,7 +686,7 @@ void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* p
             launch_mixed2d(A, std::max(1, std::min(A.count, s->n_partials)), s->mixed_rw, Qhat, st);
             break;
         }
-        case 1: into_t<float, 8, 256, true, false>(s, st, G, partials, Qhat, err); break;
+        case 1: into_t<float, 8, kBigNT, true, false>(s, st, G, partials, Qhat, err); break;
         case 2: into_t<double, 2, 128, true, false>(s, st, G, partials, Qhat, err); break;
         default: into_t<double, 2, 256, false, false>(s, st, G, partials, Qhat, err); break;
     }
@@ -740,7 +796,7 @@ size_t fused2d_variant_smem(int variant, int N) {
     switch (variant) {
         case 0: return mixed2d_smem(N, 8);
         case 4: return mixed2d_smem(N, 16);
-        case 1: return Layout2D<float, 8, true, false>::bytes(N, 256);
+        case 1: return Layout2D<float, 8, true, false>::bytes(N, kBigNT);
         case 2: return Layout2D<double, 2, true, false>::bytes(N, 128);
         default: return Layout2D<double, 2, false, false>::bytes(N, 256);
     }
@@ -752,7 +808,7 @@ void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, cons
     switch (variant) {
         case 0: launch_mixed2d_group(st, 8, d_jobs, d_cta, njobs, total, maxN); break;
         case 4: launch_mixed2d_group(st, 16, d_jobs, d_cta, njobs, total, maxN); break;
-        case 1: launch_group_t<float, 8, 256, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
+        case 1: launch_group_t<float, 8, kBigNT, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
         case 2: launch_group_t<double, 2, 128, true, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
         default: launch_group_t<double, 2, 256, false, false>(st, d_jobs, d_cta, njobs, total, maxN); break;
     }
@@ -763,7 +819,7 @@ void launch_fused2d(bn_solver* s) {
     const bool mixed = s->opt.precision == BN_MIXED;
     const bool big = s->g.N > 32;
     if (mixed) {
-        if (big) launch_t<float, 8, 256, true, false>(s, s->Ghat32, s->tabs->beta32);
+        if (big) launch_t<float, 8, kBigNT, true, false>(s, s->Ghat32, s->tabs->beta32);
         else launch_mixed(s);
     } else {
         if (big) launch_t<double, 2, 256, false, false>(s, s->Ghat, s->tabs->beta64);

@@ -186,22 +186,6 @@ __device__ __forceinline__ void build_P(float2* Pb, const float2* Gs, const Item
     }
 }
 
-// Packed FP32 pairs (sm_100 family): a 64-bit register holding two floats, and the paired FMA
-// fma.rn.f32x2, which rounds each half exactly as fmaf does and issues once for both.
-__device__ __forceinline__ uint64_t dup2(float x) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ void split2(uint64_t v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-
 // One s_1 row of the Toeplitz product: acc[r] += sum_{s2} beta[c0 + r - s2] P[s2] with acc[r] the
 // (real, imaginary) pair of output r, the weights in a register window whose slots rotate (slot of
 // column x is x mod RW) and hold each weight twice, so that one paired FMA serves both halves of

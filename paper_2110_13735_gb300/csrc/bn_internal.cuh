@@ -81,6 +81,27 @@ struct FusedArgs {
 // 256 / kPartModes thread groups adds the partials c = w, w + groups, ... with FP32 compensated
 // (Kahan) summation, and the group results meet in a fixed FP64 tree (deterministic).
 constexpr int kPartModes = 4;
+// Packed FP32 pairs (sm_100 family): a 64-bit register holding two floats, and the paired FMA
+// fma.rn.f32x2, which rounds each half exactly as fmaf does and issues once for both.
+__device__ __forceinline__ uint64_t dup2(float x) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ void split2(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
 __device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
