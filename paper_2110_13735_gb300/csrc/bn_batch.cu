@@ -1,7 +1,7 @@
 // bn_batch.cu -- many 2-D requests advanced together: every stage of one RK step of all
 // requests runs as a fixed set of shared launches, captured once per set of requests as one CUDA
-// graph.  Per evaluation: the second forward transform pass, the S(b) kernel and the fused
-// operator per precision/size group, the partial sums, the first inverse pass, and one row kernel
+// graph.  Per evaluation: the second forward transform pass, the fused operator per
+// precision/size group, the partial sums, the first inverse pass, and one row kernel
 // with the last inverse pass, the RK update and the first forward pass of the next stage.  Each request keeps its own CTA partition and every output keeps the arithmetic of
 // the single-request kernels, so its result is identical to the one it gets alone.
 #include <algorithm>
@@ -36,6 +36,8 @@ struct ElemJob {
     int nPart;
     int part32;
     double dt, scale;
+    const float2* Sb;   // mixed N <= 32 with eps != 0: S(b) from the operator kernel (else null)
+    float eps;
 };
 
 __device__ __forceinline__ double2 warp_sum2(double sr, double si) {
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __res
     const ElemJob J = jobs[blockIdx.y];
     if (J.part32) {
         if (blockIdx.x * kPartModes >= J.nm) return;   // uniform per block
-        sum_partials_f32_block(J.nm, J.nPart, reinterpret_cast<const float4*>(J.partials), J.Qhat, blockIdx.x);
+        sum_partials_f32_block(J.nm, J.nPart, reinterpret_cast<const float4*>(J.partials), J.Qhat, blockIdx.x, J.N,
+                               J.Ghat32, J.Sb, J.eps);
         return;
     }
     if (blockIdx.x * 8 >= J.nm) return;   // uniform per block
@@ -312,11 +315,6 @@ static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in, int
     }
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
     p->launches++;
-    for (auto& g : p->groups)
-        if ((g.variant == 0 || g.variant == 4) && g.maxCount > 0) {
-            launch_mixed2d_sred_group(st, g.d_jobs, g.njobs, g.maxCount);
-            p->launches++;
-        }
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
     p->launches += (long long)p->groups.size();
     k_sum_partials_batch<<<dim3((p->maxNm + kPartModes - 1) / kPartModes, nj), 256, 0, st>>>(p->d_elem, p->d_time);
@@ -366,6 +364,8 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         J.partials = s->partials;
         J.nPart = std::max(1, std::min(s->eps != 0.0 ? s->work.count : s->work_quad.count, s->n_partials));
         J.part32 = fused2d_partials_f32(s) ? 1 : 0;
+        J.Sb = J.part32 && s->eps != 0.0 && s->work.count > 0 ? reinterpret_cast<const float2*>(s->S2) : nullptr;
+        J.eps = (float)s->eps;
         J.dt = dts[i];
         J.scale = s->scale;
         elem.push_back(J);

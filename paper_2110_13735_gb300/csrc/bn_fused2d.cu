@@ -595,8 +595,8 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.betaT = s->tabs->beta32T;
 }
 
-// Mixed precision N <= 32 (variant 0): the S(b) kernel, k_mixed2d and the FP32-compensated
-// partial sum (bn_fused2d_mixed.cu).
+// Mixed precision N <= 32 (variant 0): k_mixed2d (which also forms S(b)) and the FP32-compensated
+// partial sum with the S(b) convolution (bn_fused2d_mixed.cu).
 void launch_mixed(bn_solver* s) {
     FusedArgs<float> A;
     fill_args_t<float>(s, A);

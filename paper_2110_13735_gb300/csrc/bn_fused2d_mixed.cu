@@ -8,8 +8,9 @@
 //   S(b)   = sum_{s in box_s(b)} W(b, s) P_b(s),        W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b).
 //
 // Organisation (one CTA walks a static share of the b values, heaviest first):
-//  * S(b) for every b comes from a separate small kernel (one warp per b), so the operator kernel
-//    has no global-memory dependency chain per b.
+//  * S(b) (the reducible part) is formed per b from the staged P_b by the warps once their sweep
+//    units are done, summed in warp order and written out; its convolution with G^ is added by
+//    the partial-sum kernel, so no output of this kernel waits on it.
 //  * The beta rectangle (box_n - box_s) of the next b is copied into shared memory asynchronously
 //    and its P_b formed while the current b is swept: one CTA barrier per b.
 //  * The sweep is split into warp units.  A unit is 32/J (output row, group of 8 outputs along n_2)
@@ -33,6 +34,7 @@ namespace {
 
 constexpr int kNT = 256;            // threads per CTA
 constexpr int kNW = kNT / 32;       // warps per CTA
+constexpr int kWRows = 32 / kNW;    // P_b rows per warp in the S(b) sums (N <= 32)
 constexpr uint32_t kWait = 1u << 22;  // polls of the bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -104,33 +106,8 @@ struct MixedLayout {
     static __host__ __device__ size_t bslot(int N) { return ((size_t)2 * N * ws(N) * 4 + 15) / 16 * 16; }
     static __host__ __device__ size_t pslot(int N) { return ((size_t)N * ps(N) * 8 + 15) / 16 * 16; }
     static __host__ __device__ size_t bytes(int N) {
-        return (size_t)N * N * sizeof(float2) * 3 + 2 * pslot(N) + 2 * bslot(N) + 3 * sizeof(ItemMeta) + 16;
-    }
-};
-
-// Boxes of one b (flat extended index ib): outputs n (n, n-b in I_N), inner s (s, b-s in I_N)
-// and the beta rectangle a = n - s, with one spare column on the left.
-struct Geo {
-    int b1, b2, nlo1, L1, nlo2, L2, slo1, S1, slo2, S2, Gg, A1, a1lo, A2, a2lo;
-    bool quad;
-    __device__ __forceinline__ Geo(int ib, int N) {
-        const int E = 2 * N, h = N / 2;
-        b1 = ib / E - N;
-        b2 = ib % E - N;
-        nlo1 = max(-h, b1 - h);
-        L1 = min(h - 1, b1 + h - 1) - nlo1 + 1;
-        nlo2 = max(-h, b2 - h);
-        L2 = min(h - 1, b2 + h - 1) - nlo2 + 1;
-        slo1 = max(-h, b1 - h + 1);
-        S1 = min(h - 1, b1 + h) - slo1 + 1;
-        slo2 = max(-h, b2 - h + 1);
-        S2 = min(h - 1, b2 + h) - slo2 + 1;
-        quad = b1 >= -h && b1 < h && b2 >= -h && b2 < h;
-        Gg = (L2 + 7) / 8;
-        A1 = L1 + S1 - 1;
-        a1lo = nlo1 - slo1 - S1 + 1;
-        A2 = 8 * Gg + S2;
-        a2lo = nlo2 - slo2 - S2;
+        return (size_t)N * N * sizeof(float2) * 3 + 2 * pslot(N) + 2 * bslot(N) + 3 * sizeof(ItemMeta) + 16 +
+               2 * 8 * sizeof(float2);
     }
 };
 
@@ -265,10 +242,12 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
     p += 2 * Lay::bslot(N);
     ItemMeta* ring = reinterpret_cast<ItemMeta*>(p);                       // 3 slots
     uint64_t* bar = reinterpret_cast<uint64_t*>(p + 3 * sizeof(ItemMeta));
+    float2* Sred = reinterpret_cast<float2*>(p + 3 * sizeof(ItemMeta) + 16);   // [2][kNW] warp sums of S(b)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cubic = A.eps != 0.0;
     const float eps_r = (float)A.eps;
-    const float2* __restrict__ Sb = reinterpret_cast<const float2*>(A.Sb);
+    float2* __restrict__ Sb = reinterpret_cast<float2*>(A.Sb);
+    const float* __restrict__ Wt = A.sw;
     const ItemMeta* __restrict__ meta = reinterpret_cast<const ItemMeta*>(A.meta);
     if (A.stamps && tid == 0) atomicMin(&A.stamps[0], now_ns());
 
@@ -334,9 +313,14 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
         cp_wait_all();
         __syncthreads();
 
-        int k = 0, slot = 0;
+        int k = 0, slot = 0, prev_ib = -1;
         for (int item = blk; item < A.count; item += nblk) {
             const ItemMeta& m = ring[slot];
+            if (tid == 0 && prev_ib >= 0) {   // S(b) of the previous b: its warp sums, in warp order
+                float2 t = Sred[(k ^ 1) * kNW];
+                for (int w = 1; w < kNW; ++w) t = make_float2(t.x + Sred[(k ^ 1) * kNW + w].x, t.y + Sred[(k ^ 1) * kNW + w].y);
+                Sb[prev_ib] = t;
+            }
             const int nslot = slot == 2 ? 0 : slot + 1, n2slot = nslot == 2 ? 0 : nslot + 1;
             // the buffers and ring slot of the previous b are free (barrier at its end): fill them
             fetch_meta(ring + n2slot, meta, item + 2 * nblk, A.count);
@@ -345,13 +329,21 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                 build_P(P0 + (k ^ 1) * pstep, Gs, ring[nslot], N, PS);
             }
             cp_commit();
-            const float2 S = Sb[m.ib];
             const float* __restrict__ Bs = B0 + k * bstep;
             const float2* __restrict__ Pb = P0 + k * pstep;
             const int orient = m.orient, b1 = m.b1, b2 = m.b2;
             const int nlo_u = m.nlo_u, nlo_w = m.nlo_w, slo_u = m.slo_u, Su = m.Su, Sw = m.Sw;
             const int Gg = m.Gg, a_ulo = m.a_ulo, base = m.base;
             const int umain = m.units, uall = m.units + m.units2;
+            // the weights W(b, s) of this warp's P_b rows for S(b), requested now and used after the
+            // sweep (N <= 32: at most 4 rows of at most 32 entries per warp)
+            float wv[kWRows];
+#pragma unroll
+            for (int j = 0; j < kWRows; ++j) {
+                const int r = warp + kNW * j, su_ = m.slo_u + r, sw_ = m.slo_w + lane;
+                const int s1 = orient ? sw_ : su_, s2 = orient ? su_ : sw_;
+                wv[j] = r < Su && lane < Sw ? __ldg(Wt + (size_t)m.ib * nm + (s1 + h) * N + (s2 + h)) : 0.f;
+            }
             const int nwend = nlo_w + m.Lw;
             const int su = orient ? 1 : N, sw = orient ? N : 1;   // flat strides of u and w (modes)
             const int eu = orient ? 1 : E, ew = orient ? E : 1;   // and in the extended box
@@ -442,7 +434,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
 #pragma unroll
                     for (int r = 0; r < kRW; ++r) {
                         if (r >= cnt || nw1 + r >= nwend) break;
-                        float2 D = make_float2(eps_r * (ar[r] + S.x), eps_r * (ai[r] + S.y));
+                        float2 D = make_float2(eps_r * ar[r], eps_r * ai[r]);
                         if (quad) {
                             const float wq = __ldg(qrow + r * ew);
                             D.x = fmaf(wq, gb.x, D.x);
@@ -455,10 +447,36 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
                     }
                 }
             }
+            {
+                // S(b) = sum over box_s of W(b, s) P_b(s) (the reducible part; its convolution with
+                // G^ is added by the partial-sum kernel): warp w takes the P_b rows w, w + 8, ...
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int j = 0; j < kWRows; ++j) {
+                    const int r = warp + kNW * j;
+                    if (r < Su && lane < Sw) {
+                        const float2 pv = Pb[r * PS + lane];
+                        sr = fmaf(wv[j], pv.x, sr);
+                        si = fmaf(wv[j], pv.y, si);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) Sred[k * kNW + warp] = make_float2(sr, si);
+            }
+            prev_ib = m.ib;
             cp_wait_all();
             __syncthreads();
             k ^= 1;
             slot = nslot;
+        }
+        if (tid == 0 && prev_ib >= 0) {
+            float2 t = Sred[(k ^ 1) * kNW];
+            for (int w = 1; w < kNW; ++w) t = make_float2(t.x + Sred[(k ^ 1) * kNW + w].x, t.y + Sred[(k ^ 1) * kNW + w].y);
+            Sb[prev_ib] = t;
         }
     }
     __syncthreads();
@@ -494,65 +512,13 @@ __global__ void __launch_bounds__(kNT, RW == 8 ? 3 : 2) k_mixed2d_batch(const Fu
     mixed_body<RW>(A, blockIdx.x - cta_begin[lo], cta_begin[lo + 1] - cta_begin[lo]);
 }
 
-// S(b) for the items [8 blockIdx.x, 8 blockIdx.x + 8) of one request: the CTA stages G^ (N <= 32) in
-// shared memory, then each warp takes one b; lanes run along s_2 and four rows s_1 are in flight at
-// once (independent loads of W); the lane sums meet by shuffles.
-__device__ __forceinline__ void sred_body(const FusedArgs<float>& A, int item0) {
-    __shared__ float2 Gsh[32 * 32];
-    if (item0 >= A.count || A.eps == 0.0) return;   // uniform per CTA
-    const int N = A.N, nm = N * N, h = N / 2, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) Gsh[i] = A.G[i];
-    __syncthreads();
-    const int item = item0 + (threadIdx.x >> 5);
-    if (item >= A.count) return;
-    const int ib = A.items[item];
-    const Geo g(ib, N);
-    const float* __restrict__ wrow = A.sw + (size_t)ib * nm + h * N + h + g.slo2;
-    float sr = 0.f, si = 0.f;
-    if (lane < g.S2) {
-        const int s2 = g.slo2 + lane;
-        const float2* gs = Gsh + h * N + h + s2;                   // G^_(s1, s2) at gs[s1 N]
-        const float2* gm = Gsh + (g.b1 + h) * N + h + g.b2 - s2;   // G^_(b - s) at gm[-s1 N]
-        int r = 0;
-        for (; r + 4 <= g.S1; r += 4) {
-            float w[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w[q] = __ldg(wrow + (g.slo1 + r + q) * N + lane);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int s1 = g.slo1 + r + q;
-                const float2 P = cmulf(gs[s1 * N], gm[-s1 * N]);
-                sr = fmaf(w[q], P.x, sr);
-                si = fmaf(w[q], P.y, si);
-            }
-        }
-        for (; r < g.S1; ++r) {
-            const int s1 = g.slo1 + r;
-            const float w = __ldg(wrow + s1 * N + lane);
-            const float2 P = cmulf(gs[s1 * N], gm[-s1 * N]);
-            sr = fmaf(w, P.x, sr);
-            si = fmaf(w, P.y, si);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
-    }
-    if (lane == 0) reinterpret_cast<float2*>(A.Sb)[ib] = make_float2(sr, si);
-}
-
-__global__ void __launch_bounds__(256) k_sred2d(FusedArgs<float> A) { sred_body(A, blockIdx.x * 8); }
-__global__ void __launch_bounds__(256) k_sred2d_batch(const FusedArgs<float>* __restrict__ jobs) {
-    sred_body(jobs[blockIdx.y], blockIdx.x * 8);
-}
-
 }  // namespace
 
 namespace {
 __global__ void __launch_bounds__(256) k_sum_partials_f32(int nm, int nPart, const float4* __restrict__ partials,
-                                                          double2* __restrict__ out) {
-    sum_partials_f32_block(nm, nPart, partials, out, blockIdx.x);
+                                                          double2* __restrict__ out, int N, const float2* __restrict__ G32,
+                                                          const float2* __restrict__ Sb, float eps) {
+    sum_partials_f32_block(nm, nPart, partials, out, blockIdx.x, N, G32, Sb, eps);
 }
 }  // namespace
 
@@ -574,10 +540,6 @@ int mixed2d_ctas_per_sm(int N, int rw) {
     return std::max(1, n);
 }
 
-void launch_mixed2d_sred(const FusedArgs<float>& A, cudaStream_t st) {
-    if (A.eps != 0.0 && A.count > 0) k_sred2d<<<(A.count + 7) / 8, 256, 0, st>>>(A);
-}
-
 void launch_mixed2d_kernel(const FusedArgs<float>& A, int grid, int rw, cudaStream_t st) {
     if (rw == 16) k_mixed2d<16><<<grid, kNT, MixedLayout<16>::bytes(A.N), st>>>(A);
     else k_mixed2d<8><<<grid, kNT, MixedLayout<8>::bytes(A.N), st>>>(A);
@@ -585,19 +547,12 @@ void launch_mixed2d_kernel(const FusedArgs<float>& A, int grid, int rw, cudaStre
 
 int launch_mixed2d(const FusedArgs<float>& A, int grid, int rw, double2* Qhat, cudaStream_t st) {
     const int nm = A.N * A.N;
-    int launches = 2;
-    if (A.eps != 0.0 && A.count > 0) {
-        launch_mixed2d_sred(A, st);
-        ++launches;
-    }
+    const bool red = A.eps != 0.0 && A.count > 0;   // the kernel writes S(b); its convolution follows
     launch_mixed2d_kernel(A, grid, rw, st);
     k_sum_partials_f32<<<(nm + kPartModes - 1) / kPartModes, 256, 0, st>>>(
-        nm, grid, reinterpret_cast<const float4*>(A.partials), Qhat);
-    return launches;
-}
-
-void launch_mixed2d_sred_group(cudaStream_t st, const void* d_jobs, int njobs, int maxCount) {
-    k_sred2d_batch<<<dim3((maxCount + 7) / 8, njobs), 256, 0, st>>>(static_cast<const FusedArgs<float>*>(d_jobs));
+        nm, grid, reinterpret_cast<const float4*>(A.partials), Qhat, A.N, reinterpret_cast<const float2*>(A.G),
+        red ? reinterpret_cast<const float2*>(A.Sb) : nullptr, (float)A.eps);
+    return 2;
 }
 
 void launch_mixed2d_group(cudaStream_t st, int rw, const void* d_jobs, const int* d_cta, int njobs, int total,

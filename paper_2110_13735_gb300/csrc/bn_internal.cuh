@@ -70,7 +70,7 @@ struct FusedArgs {
     int* err;                // [0] set to 1 if a bounded wait gave up
     unsigned long long* stamps;  // optional [2]: min start / max end %globaltimer (ns) over CTAs
     const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
-    void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the S(b) kernel
+    void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the operator kernel
     const void* meta;        // mixed N <= 32: ItemMeta per item (same order as items)
     const float* dq;         // mixed N <= 32: quadratic weights beta(a, b) - beta(b, b), [b in I_N][a]
     const float* betaT;      // mixed N <= 32: [b][a2][a1]
@@ -108,8 +108,12 @@ __device__ __forceinline__ void kahan_add_f(float& s, float& c, float x) {
     c = (t - s) - y;
     s = t;
 }
+// With Sb (mixed 2-D, eps != 0) the reducible part eps sum_b G^_{n-b} S(b) is added as well: S(b) for
+// every b with a non-empty box_s (b_d <= N - 2) was written by the operator kernel, G32 = G^ in FP32.
 __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const float4* __restrict__ partials,
-                                                       double2* __restrict__ out, int bx) {
+                                                       double2* __restrict__ out, int bx, int N = 0,
+                                                       const float2* __restrict__ G32 = nullptr,
+                                                       const float2* __restrict__ Sb = nullptr, float eps = 0.f) {
     constexpr int G = 256 / kPartModes;
     __shared__ double2 sh[256];
     const int m = threadIdx.x % kPartModes, w = threadIdx.x / kPartModes;
@@ -135,6 +139,17 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
             kahan_add_f(sx, cx, -v.z);
             kahan_add_f(sy, cy, v.y);
             kahan_add_f(sy, cy, -v.w);
+        }
+        if (Sb) {
+            // eps sum over k in I_N of G^_k S(n - k), k = w, w + G, ...
+            const int h = N / 2, E = 2 * N, n1 = i / N - h, n2 = i % N - h;
+            for (int kf = w; kf < nm; kf += G) {
+                const int b1 = n1 - (kf / N - h), b2 = n2 - (kf % N - h);
+                if (b1 > N - 2 || b2 > N - 2) continue;   // box_s(b) empty: S(b) = 0
+                const float2 g = G32[kf], sb = Sb[(b1 + N) * E + (b2 + N)];
+                kahan_add_f(sx, cx, eps * fmaf(g.x, sb.x, -g.y * sb.y));
+                kahan_add_f(sy, cy, eps * fmaf(g.x, sb.y, g.y * sb.x));
+            }
         }
     }
     sh[threadIdx.x] = make_double2((double)sx - (double)cx, (double)sy - (double)cy);
@@ -330,10 +345,8 @@ int triple_partials(const bn_solver* s);
 size_t mixed2d_smem(int N, int rw);
 void configure_mixed2d();
 int mixed2d_ctas_per_sm(int N, int rw);
-void launch_mixed2d_sred(const FusedArgs<float>& A, cudaStream_t st);
 void launch_mixed2d_kernel(const FusedArgs<float>& A, int grid, int rw, cudaStream_t st);
 int launch_mixed2d(const FusedArgs<float>& A, int grid, int rw, double2* Qhat, cudaStream_t st);   // returns launches
-void launch_mixed2d_sred_group(cudaStream_t st, const void* d_jobs, int njobs, int maxCount);
 void launch_mixed2d_group(cudaStream_t st, int rw, const void* d_jobs, const int* d_cta, int njobs, int total,
                           int maxN);
 // Chooses the outputs per thread of the mixed 2-D kernel for this solver (option, cache, or timing
