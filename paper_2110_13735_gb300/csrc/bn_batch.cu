@@ -384,7 +384,17 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         if (e != cudaSuccess) break;
         BatchPlan::Group g;
         g.variant = kv.first;
-        const bool mixed = kv.first <= 1;
+        const bool mixed = kv.first <= 1 || kv.first == 4;
+        // heaviest requests first: their CTAs take the SMs at the start of the launch and the CTAs of
+        // light requests (e.g. eps = 0, quadratic part only) fill the tail; a request's CTAs compute
+        // the same whatever their position in the grid
+        std::stable_sort(kv.second.begin(), kv.second.end(), [&](int x, int y) {
+            const bn_solver* a = solvers[x];
+            const bn_solver* b = solvers[y];
+            const double wa = a->eps != 0.0 ? a->work.terms : (double)a->work_quad.count;
+            const double wb = b->eps != 0.0 ? b->work.terms : (double)b->work_quad.count;
+            return wa > wb;
+        });
         const size_t asz = mixed ? sizeof(FusedArgs<float>) : sizeof(FusedArgs<double>);
         std::vector<unsigned char> args(asz * kv.second.size());
         std::vector<int> cta(1, 0);
