@@ -141,14 +141,25 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
             kahan_add_f(sy, cy, -v.w);
         }
         if (Sb) {
-            // eps sum over k in I_N of G^_k S(n - k), k = w, w + G, ...
+            // eps sum over k in I_N of G^_k S(n - k), k = w, w + G, ...: eight terms' loads in flight,
+            // then added in order; terms with an empty box_s(b) (b_d = N - 1: S(b) = 0) are skipped
             const int h = N / 2, E = 2 * N, n1 = i / N - h, n2 = i % N - h;
-            for (int kf = w; kf < nm; kf += G) {
-                const int b1 = n1 - (kf / N - h), b2 = n2 - (kf % N - h);
-                if (b1 > N - 2 || b2 > N - 2) continue;   // box_s(b) empty: S(b) = 0
-                const float2 g = G32[kf], sb = Sb[(b1 + N) * E + (b2 + N)];
-                kahan_add_f(sx, cx, eps * fmaf(g.x, sb.x, -g.y * sb.y));
-                kahan_add_f(sy, cy, eps * fmaf(g.x, sb.y, g.y * sb.x));
+            for (int kf = w; kf < nm; kf += 8 * G) {
+                float2 g[8], sb[8];
+                bool ok[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = kf + q * G, b1 = n1 - (k / N - h), b2 = n2 - (k % N - h);
+                    ok[q] = k < nm && b1 <= N - 2 && b2 <= N - 2;
+                    g[q] = ok[q] ? G32[k] : make_float2(0.f, 0.f);
+                    sb[q] = ok[q] ? Sb[(b1 + N) * E + (b2 + N)] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (ok[q]) {
+                        kahan_add_f(sx, cx, eps * fmaf(g[q].x, sb[q].x, -g[q].y * sb[q].y));
+                        kahan_add_f(sy, cy, eps * fmaf(g[q].x, sb[q].y, g[q].y * sb[q].x));
+                    }
             }
         }
     }
