@@ -251,3 +251,33 @@ def test_modes_parity_2d_n64_sampled(B, precision, tol):
     err = float(np.linalg.norm(blk - Qh_o) / np.linalg.norm(gain_o))
     print(f"2-D N=64 {precision} sampled-mode error {err:.3e}")
     assert err <= tol
+
+
+def test_bench_workload_step_vs_oracle(B):
+    """The benchmark's workload in the launch configuration it times: the 2-D N=32 pair (BKW eps=0 at
+    t0=1 and the bosonic Gaussian eps=+1, Maxwell molecules, R=6), mixed precision, advanced together by
+    one RK4 step (dt = 0.005) through the batched, graph-captured step, against the FP64 oracle's step.
+    Bound: each of the four stage evaluations is within the mixed operator tolerance (e_Q <= 2e-6 of
+    the gain term), so the step differs by at most dt * 2e-6 * ||gain(f)|| (stage arguments stay within
+    dt of f; a factor 2 of margin)."""
+    N, dt = 32, 0.005
+    f0s = [I.config1_bkw_f0(N, R6), I.config1_boson_f0(N, R6)]
+    epss = [0.0, 1.0]
+    solvers = [B.Solver(2, N, T6, R6, B.MAXWELL, e, precision=B.MIXED) for e in epss]
+    try:
+        for s, f in zip(solvers, f0s):
+            s.set_state(f)
+        assert B.step_rk_batch(solvers, [dt, dt], 1) == -1
+        for s, f, e in zip(solvers, f0s, epss):
+            got = s.get_state().reshape(N, N)
+            ora = O.Operator(2, N, T6, R6, 0, e, M=2 * N)
+            _, gain, _, _ = ora.eval_collision(f, parts=True)
+            ref = ora.step(f, dt, 1, 0).reshape(N, N)
+            err = float(np.linalg.norm(got - ref))
+            bound = 2.0 * dt * 2e-6 * float(np.linalg.norm(gain))
+            print(f"bench pair, eps={e}: ||f_gpu - f_oracle|| = {err:.3e} (bound {bound:.3e}), "
+                  f"relative to the step's change {err / float(np.linalg.norm(ref - f.reshape(N, N))):.3e}")
+            assert err <= bound
+    finally:
+        for s in solvers:
+            s.close()
