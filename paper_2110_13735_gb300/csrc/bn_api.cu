@@ -277,6 +277,14 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         return fail(st, err);
     }
     s->n_partials = bn::triple_partials(s);
+    st = bn::balance_work_lists(s, &err);
+    if (st != BN_OK) {
+        free_buffers(s);   // the work lists (the other buffers are not allocated yet)
+        bn::release_tables(s->tabs);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return fail(st, err);
+    }
     const size_t n = s->g.nModes;
     e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {

@@ -324,6 +324,7 @@ namespace bn {
 bn_status acquire_tables(bn_solver* s, std::string* err);
 void release_tables(KernelTables* t);
 bn_status build_work_list(bn_solver* s, std::string* err);
+bn_status balance_work_lists(bn_solver* s, std::string* err);   // after n_partials is set
 double count_triple_terms(int d, int N);
 double count_pair_terms(int d, int N);
 double count_reducible_terms(int d, int N);

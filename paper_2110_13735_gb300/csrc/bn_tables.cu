@@ -376,8 +376,8 @@ double count_reducible_terms(int d, int N) {
 // used.  Estimated cost per item = the split cost of its sweep + kItemInstr (staging, P_b, setup).
 // The order changes only which CTA adds an item's terms into its partial sums, not the terms.
 constexpr long long kItemInstr = 500;
-static std::vector<ItemMeta> balance_items(const std::vector<ItemMeta>& meta, const std::vector<long long>& cost,
-                                           int nblk) {
+template <typename T>
+static std::vector<T> balance_items(const std::vector<T>& meta, const std::vector<long long>& cost, int nblk) {
     const int n = (int)meta.size();
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -400,7 +400,7 @@ static std::vector<ItemMeta> balance_items(const std::vector<ItemMeta>& meta, co
     std::vector<int> id(nblk);
     int first = 0, rest = last;   // CTAs with a last-round item get ids 0 .. last-1
     for (int j = 0; j < nblk; ++j) id[j] = mine[j].size() == rounds ? first++ : rest++;
-    std::vector<ItemMeta> out(n);
+    std::vector<T> out(n);
     for (int j = 0; j < nblk; ++j)
         for (size_t k = 0; k < mine[j].size(); ++k) out[k * nblk + id[j]] = meta[mine[j][k]];
     return out;
@@ -513,6 +513,48 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
     s->work.count = (int)flat.size();
     s->work.terms = total;
     s->work_quad.count = (int)qflat.size();
+    return BN_OK;
+}
+
+// The item lists of the kernels that take items k nblk + blockIdx.x (k_fused2d: FP64, and mixed
+// N > 32; k_triple in 3-D), dealt to their nblk = min(count, n_partials) CTAs as balance_items does
+// for the mixed kernel, with the terms of an item (cubic list: |box_n| |box_s|; quadratic list:
+// |box_n|) plus kItemTerms for its fixed work as the cost.  The mixed 2-D kernel for N <= 32 deals
+// its own per-item metadata and keeps the lists as they are.
+constexpr long long kItemTerms = 4000;
+bn_status balance_work_lists(bn_solver* s, std::string* err) {
+    const int d = s->g.d, N = s->g.N, E = s->g.E;
+    if (d == 2 && s->opt.precision == BN_MIXED && N <= 32) return BN_OK;
+    WorkList* lists[2] = {&s->work, &s->work_quad};
+    for (int li = 0; li < 2; ++li) {
+        WorkList* wl = lists[li];
+        const int n = wl->count;
+        if (n <= 1 || !wl->items) continue;
+        const int nblk = std::max(1, std::min(n, s->n_partials));
+        std::vector<int> items(n);
+        if (cudaMemcpy(items.data(), wl->items, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            *err = "work list read-back failed";
+            return BN_ERR_CUDA;
+        }
+        std::vector<long long> cost(n);
+        for (int i = 0; i < n; ++i) {
+            int r = items[i];
+            long long w = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                const int b = r % E - N;
+                r /= E;
+                w *= li == 0 ? box_n(N, b) * box_s(N, b) : box_n(N, b);
+            }
+            cost[i] = w + kItemTerms;
+        }
+        const std::vector<int> laid = balance_items(items, cost, nblk);
+        if (cudaMemcpy(wl->items, laid.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            *err = "work list upload failed";
+            return BN_ERR_CUDA;
+        }
+    }
     return BN_OK;
 }
 
