@@ -27,6 +27,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -229,8 +230,7 @@ def run_ours(args):
 
     # ---- mixed precision (the headline)
     solvers, f0 = make_pair(bn, I, bn.MIXED, stream, args.mixed_rw)
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f".clocks_rank{rank}.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"bn_bench_clocks_rank{rank}_{os.getpid()}.csv")
     p, fh = clocks_sampler_start(clk_path)
     ms, launches, prof, window = timed(solvers, args.steps, args.warmup, profile=True)
     clocks = clocks_sampler_stop(p, fh, clk_path, local, window)
