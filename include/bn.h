@@ -206,6 +206,23 @@ bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escal
  * by opt.mixed_rw, or not applicable).  count >= 7. */
 bn_status bn_kernel_config(const bn_solver* s, double* out, size_t count);
 
+/* Host-side plan of the mixed 2-D operator kernel (N <= 32), computed on the CPU
+ * exactly as a solver computes it, no GPU needed.  The work items are the b of the
+ * Lemma's factorised sum with non-empty boxes (Sec. 3.3 step 2(c)); for RW = rw
+ * outputs per thread (8 or 16), the per-b orientation choice on (oriented = 1) or
+ * off, and a grid of nblk CTAs, one row of 14 ints per item is written to out, in
+ * the order the kernel's CTAs take them (row k nblk + j is CTA j's k-th item):
+ *   [ib, orient, J, chunk, units, J2, chunk2, units2, tail0, base, Lu, Lw, Su, Sw]
+ * ib = (b1 + N) 2N + (b2 + N); the sweep splits dimension u (orient 0: u = 1,
+ * w = 2; 1: swapped) into units of 32/J tasks x J chunks of `chunk` s_u rows
+ * (`units` units), the last partial round re-split into units2 units of 32/J2 tasks
+ * x J2 chunks of chunk2 rows covering the tasks [tail0, base); base = Lu x ceil(Lw
+ * / rw) tasks; Lu, Lw, Su, Sw are the output and inner box sizes along u and w.
+ * *n_items receives the item count; with out = NULL only the count is returned.
+ * BN_ERR_ARG if N is odd or outside [2, 32], rw is not 8 or 16, nblk < 1,
+ * n_items is NULL, or count < 14 x items. */
+bn_status bn_plan_mixed2d(int N, int rw, int oriented, int nblk, int* out, size_t count, int* n_items);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* bn_last_error(void);
 

@@ -73,6 +73,8 @@ def load(path: str | None = None):
     lib.bn_work_counts.argtypes = [vp, dp, sz]
     lib.bn_precision_state.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
     lib.bn_kernel_config.argtypes = [vp, dp, sz]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.bn_plan_mixed2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, sz, ip]
     lib.bn_kernel_launches.argtypes = [vp]
     lib.bn_kernel_launches.restype = ctypes.c_longlong
     lib.bn_last_error.restype = ctypes.c_char_p
@@ -107,6 +109,22 @@ def _check(status: int):
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+PLAN_COLUMNS = ("ib", "orient", "J", "chunk", "units", "J2", "chunk2", "units2", "tail0", "base",
+                "Lu", "Lw", "Su", "Sw")
+
+
+def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) -> np.ndarray:
+    """The mixed 2-D kernel's host-side plan (include/bn.h: bn_plan_mixed2d): one row per work item
+    in the order the CTAs take them, columns PLAN_COLUMNS.  Needs no GPU."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.bn_plan_mixed2d(int(N), int(rw), int(bool(oriented)), int(nblk), None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, len(PLAN_COLUMNS)), dtype=np.int32)
+    _check(lib.bn_plan_mixed2d(int(N), int(rw), int(bool(oriented)), int(nblk),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), out.size, ctypes.byref(n)))
+    return out
 
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,

@@ -1,6 +1,7 @@
 // bn_api.cu -- the C ABI of libbn (include/bn.h): solver lifecycle, evaluation of
 // Q_eps(f) (Mouton & Rey, Sec. 3.3 step 2, classical method of Sec. 3.2) and
 // Runge-Kutta time stepping with one captured CUDA graph per step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -641,3 +642,15 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
 }
 
 }  // extern "C"
+
+extern "C" bn_status bn_plan_mixed2d(int N, int rw, int oriented, int nblk, int* out, size_t count, int* n_items) {
+    if (N < 2 || N > 32 || (N & 1) || (rw != 8 && rw != 16) || nblk < 1 || !n_items)
+        return fail(BN_ERR_ARG, "bn_plan_mixed2d: N even in [2, 32], rw 8 or 16, nblk >= 1, n_items non-null");
+    const std::vector<int> rows = bn::plan_mixed2d_rows(N, rw, oriented != 0, nblk);
+    *n_items = (int)(rows.size() / bn::kPlanCols);
+    if (out) {
+        if (count < rows.size()) return fail(BN_ERR_ARG, "bn_plan_mixed2d: out too small");
+        std::copy(rows.begin(), rows.end(), out);
+    }
+    return BN_OK;
+}

@@ -325,6 +325,8 @@ bn_status acquire_tables(bn_solver* s, std::string* err);
 void release_tables(KernelTables* t);
 bn_status build_work_list(bn_solver* s, std::string* err);
 bn_status balance_work_lists(bn_solver* s, std::string* err);   // after n_partials is set
+constexpr int kPlanCols = 14;   // columns of a bn_plan_mixed2d row
+std::vector<int> plan_mixed2d_rows(int N, int rw, bool oriented, int nblk);
 double count_triple_terms(int d, int N);
 double count_pair_terms(int d, int N);
 double count_reducible_terms(int d, int N);

@@ -406,6 +406,95 @@ static std::vector<T> balance_items(const std::vector<T>& meta, const std::vecto
     return out;
 }
 
+// Per-item geometry and warp split of the mixed 2-D kernel (8 warps per CTA, RW outputs per
+// thread, with or without the per-b orientation choice) for the items `flat` (extended indices of
+// b), in the same order, with each item's estimated cost for the CTA layout.  Host only.
+static void plan_mixed_items(int N, int RW, bool orientable, const std::vector<int>& flat, std::vector<ItemMeta>* meta_out,
+                             std::vector<long long>* cost_out) {
+    const int E = 2 * N, h = N / 2;
+    std::vector<ItemMeta>& meta = *meta_out;
+    std::vector<long long>& cost = *cost_out;
+    meta.assign(flat.size(), ItemMeta{});
+    cost.assign(flat.size(), 0);
+    for (size_t i = 0; i < flat.size(); ++i) {
+        const int ib = flat[i], b1 = ib / E - N, b2 = ib % E - N;
+        const int bb[2] = {b1, b2};
+        int nlo[2], L[2], slo[2], S[2];
+        for (int dd = 0; dd < 2; ++dd) {
+            nlo[dd] = std::max(-h, bb[dd] - h);
+            L[dd] = std::min(h - 1, bb[dd] + h - 1) - nlo[dd] + 1;
+            slo[dd] = std::max(-h, bb[dd] - h + 1);
+            S[dd] = std::min(h - 1, bb[dd] + h) - slo[dd] + 1;
+        }
+        ItemMeta m{};
+        long long best = -1;
+        for (int o = 0; o < (orientable ? 2 : 1); ++o) {   // o = 0: split dim 1, window along dim 2; 1: swapped
+            const int du = o == 0 ? 0 : 1, dw = 1 - du;
+            const int Gg = (L[dw] + RW - 1) / RW, base = L[du] * Gg;
+            SplitChoice sc;
+            const long long c = choose_split_host(base, S[du], S[dw], RW, 8, &sc);
+            if (best >= 0 && c >= best) continue;
+            best = c;
+            m.ib = ib;
+            m.ginv = (65536 + Gg - 1) / Gg;
+            m.linv = (65536 + L[du] - 1) / L[du];
+            m.Lu = (short)L[du];
+            m.orient = (short)o;
+            m.b1 = (short)b1; m.b2 = (short)b2;
+            m.nlo_u = (short)nlo[du]; m.nlo_w = (short)nlo[dw]; m.Lw = (short)L[dw];
+            m.slo_u = (short)slo[du]; m.Su = (short)S[du]; m.slo_w = (short)slo[dw]; m.Sw = (short)S[dw];
+            m.Gg = (short)Gg; m.Au = (short)(L[du] + S[du] - 1); m.Aw = (short)(RW * Gg + S[dw]);
+            m.a_ulo = (short)(nlo[du] - slo[du] - S[du] + 1); m.a_wlo = (short)(nlo[dw] - slo[dw] - S[dw]);
+            m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
+            m.J = (short)sc.J; m.tpw = (short)(32 / sc.J); m.chunk = (short)sc.chunk; m.units = (short)sc.units;
+            m.base = (short)base;
+            m.J2 = (short)sc.J2; m.chunk2 = (short)sc.chunk2; m.units2 = (short)sc.units2; m.tail0 = (short)sc.tail0;
+        }
+        meta[i] = m;
+        cost[i] = best + kItemInstr;
+    }
+}
+
+// The work items of the cubic part (b with non-empty boxes), heaviest first (host only).
+static std::vector<int> cubic_items(int d, int N) {
+    const int E = 2 * N, nb = d == 2 ? E * E : E * E * E;
+    std::vector<std::pair<long long, int>> items;
+    for (int ib = 0; ib < nb; ++ib) {
+        int b[3];
+        int r = ib;
+        for (int i = d - 1; i >= 0; --i) { b[i] = r % E - N; r /= E; }
+        long long w = 1;
+        for (int i = 0; i < d; ++i) {
+            const long long ln = box_n(N, b[i]), ls = box_s(N, b[i]);
+            if (ln <= 0 || ls <= 0) { w = 0; break; }
+            w *= ln * ls;
+        }
+        if (w > 0) items.push_back({w, ib});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
+    std::vector<int> flat(items.size());
+    for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].second;
+    return flat;
+}
+
+// The plan the mixed 2-D kernel runs for N, rw, orientation choice and nblk CTAs, as rows of
+// kPlanCols ints in the order the CTAs take the items (bn_plan_mixed2d).  Host only.
+std::vector<int> plan_mixed2d_rows(int N, int rw, bool oriented, int nblk) {
+    std::vector<ItemMeta> meta;
+    std::vector<long long> cost;
+    plan_mixed_items(N, rw, oriented, cubic_items(2, N), &meta, &cost);
+    meta = balance_items(meta, cost, std::max(1, std::min((int)meta.size(), nblk)));
+    std::vector<int> rows;
+    rows.reserve(meta.size() * kPlanCols);
+    for (const ItemMeta& m : meta) {
+        const int r[kPlanCols] = {m.ib, m.orient, m.J, m.chunk, m.units, m.J2, m.chunk2, m.units2, m.tail0, m.base,
+                                  m.Lu, m.Lw, m.Su, m.Sw};
+        rows.insert(rows.end(), r, r + kPlanCols);
+    }
+    return rows;
+}
+
 bn_status build_work_list(bn_solver* s, std::string* err) {
     const int d = s->g.d, N = s->g.N, E = s->g.E;
     std::vector<std::pair<long long, int>> items;
@@ -460,46 +549,9 @@ bn_status build_work_list(bn_solver* s, std::string* err) {
         // with or without the per-b orientation choice)
         const int RW = v < 2 ? 8 : 16;
         const bool orientable = (v & 1) != 0;
-        std::vector<ItemMeta> meta(flat.size());
-        std::vector<long long> cost(flat.size());
-        const int h = N / 2;
-        for (size_t i = 0; i < flat.size(); ++i) {
-            const int ib = flat[i], b1 = ib / E - N, b2 = ib % E - N;
-            const int bb[2] = {b1, b2};
-            int nlo[2], L[2], slo[2], S[2];
-            for (int dd = 0; dd < 2; ++dd) {
-                nlo[dd] = std::max(-h, bb[dd] - h);
-                L[dd] = std::min(h - 1, bb[dd] + h - 1) - nlo[dd] + 1;
-                slo[dd] = std::max(-h, bb[dd] - h + 1);
-                S[dd] = std::min(h - 1, bb[dd] + h) - slo[dd] + 1;
-            }
-            ItemMeta m{};
-            long long best = -1;
-            for (int o = 0; o < (orientable ? 2 : 1); ++o) {   // o = 0: split dim 1, window along dim 2; 1: swapped
-                const int du = o == 0 ? 0 : 1, dw = 1 - du;
-                const int Gg = (L[dw] + RW - 1) / RW, base = L[du] * Gg;
-                SplitChoice sc;
-                const long long cost = choose_split_host(base, S[du], S[dw], RW, 8, &sc);
-                if (best >= 0 && cost >= best) continue;
-                best = cost;
-                m.ib = ib;
-                m.ginv = (65536 + Gg - 1) / Gg;
-                m.linv = (65536 + L[du] - 1) / L[du];
-                m.Lu = (short)L[du];
-                m.orient = (short)o;
-                m.b1 = (short)b1; m.b2 = (short)b2;
-                m.nlo_u = (short)nlo[du]; m.nlo_w = (short)nlo[dw]; m.Lw = (short)L[dw];
-                m.slo_u = (short)slo[du]; m.Su = (short)S[du]; m.slo_w = (short)slo[dw]; m.Sw = (short)S[dw];
-                m.Gg = (short)Gg; m.Au = (short)(L[du] + S[du] - 1); m.Aw = (short)(RW * Gg + S[dw]);
-                m.a_ulo = (short)(nlo[du] - slo[du] - S[du] + 1); m.a_wlo = (short)(nlo[dw] - slo[dw] - S[dw]);
-                m.quad = (short)(b1 >= -h && b1 < h && b2 >= -h && b2 < h);
-                m.J = (short)sc.J; m.tpw = (short)(32 / sc.J); m.chunk = (short)sc.chunk; m.units = (short)sc.units;
-                m.base = (short)base;
-                m.J2 = (short)sc.J2; m.chunk2 = (short)sc.chunk2; m.units2 = (short)sc.units2; m.tail0 = (short)sc.tail0;
-            }
-            meta[i] = m;
-            cost[i] = best + kItemInstr;
-        }
+        std::vector<ItemMeta> meta;
+        std::vector<long long> cost;
+        plan_mixed_items(N, RW, orientable, flat, &meta, &cost);
         configure_mixed2d();
         const int nblk = std::max(1, std::min((int)flat.size(), mixed2d_ctas_per_sm(N, RW) * sms));
         meta = balance_items(meta, cost, nblk);
