@@ -7,7 +7,8 @@
 //   C_b(n) = sum_{s in box_s(b)} beta(n-s, b) P_b(s),   P_b(s) = G^_s G^_{b-s},
 //   S(b)   = sum_{s in box_s(b)} W(b, s) P_b(s),        W(b, s) = beta(s, b-s) - beta(b, s) - beta(s, b).
 //
-// Organisation (one CTA walks a static share of the b values, heaviest first):
+// Organisation (one CTA walks its share of the b values, dealt on the host by estimated cost,
+// heaviest first):
 //  * S(b) (the reducible part) is formed per b from the staged P_b by the warps once their sweep
 //    units are done, summed in warp order and written out; its convolution with G^ is added by
 //    the partial-sum kernel, so no output of this kernel waits on it.
@@ -15,14 +16,16 @@
 //    and its P_b formed while the current b is swept: one CTA barrier per b.
 //  * The sweep is split into warp units.  A unit is 32/J (output row, group of 8 outputs along n_2)
 //    tasks times J chunks of the s_1 range (J in {1, 2, 4, 8}, chosen per b from an issue-cost model
-//    of the busiest warp); the J partial sums of a task meet by a shuffle reduce-scatter, so no
-//    shared-memory reduction or extra barrier is needed, and each of the J lanes finishes 8/J of
-//    the task's outputs.
-//  * Each thread keeps 8 outputs in registers; along s_2 the weights beta(n-s, b) slide through a
-//    register window (one shared load of beta, one of P_b, 16 FFMA per step).
+//    of the busiest warp; a last partial round of units may be re-split into up to 32 chunks so
+//    that it spreads over all warps); the J partial sums of a task meet by a shuffle
+//    reduce-scatter (then a butterfly past 8 chunks), so no shared-memory reduction or extra
+//    barrier is needed, and each of the J lanes finishes 8/J of the task's outputs.
+//  * Each thread keeps 8 outputs in registers as (real, imaginary) pairs; along s_2 the weights
+//    beta(n-s, b) slide through a register window (one shared load of beta, its duplication into
+//    a pair, one 64-bit load of P_b and 8 paired FMAs, fma.rn.f32x2, per step).
 //  * G^_{n-b} D_b(n) is added to an FP32 (sum, compensation) pair per output in shared memory
 //    (Kahan); each CTA writes both words, and the partials of all CTAs are summed in FP32 with
-//    compensation in a fixed order, the 32 group sums in FP64 (deterministic).
+//    compensation in a fixed order, the group sums in FP64 (deterministic).
 #include <algorithm>
 #include <cstdint>
 
