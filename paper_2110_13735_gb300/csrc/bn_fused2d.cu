@@ -689,8 +689,9 @@ void launch_group_t(cudaStream_t st, const void* d_jobs, const int* d_cta, int n
 }  // namespace
 
 // Kernels: mixed precision N <= 32: k_mixed2d (bn_fused2d_mixed.cu); mixed N > 32: this file's
-// kernel in FP32 with 8 outputs per thread and a single staging buffer (shared memory); FP64:
-// 2 outputs per thread (DFMA-bound), staged for N <= 32, read through L1 for N > 32.
+// kernel in FP32 with 8 outputs per thread, kBigNT threads per CTA, the paired-FMA sweep and a
+// single staging buffer (shared memory); FP64: 2 outputs per thread (DFMA-bound), staged for
+// N <= 32, read through L1 for N > 32.
 void configure_fused2d() {
     configure_mixed2d();
     configure_one<float, 8, kBigNT, true, false>();
