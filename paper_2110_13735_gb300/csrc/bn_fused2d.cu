@@ -748,8 +748,9 @@ int fused2d_partials(const bn_solver* s) {
 // fewer warp units and a longer register window, more padding on small boxes), each with the
 // register window always along n_2 or with the orientation chosen per b by the host's mapping
 // model.  The variant is chosen per (device, N, forced RW) by timing the candidates on the
-// solver's stream: each runs twice untimed and three times timed (CUDA events) on the solver's own
-// tables and buffers; the fastest wins and is cached for the process.  opt.mixed_rw forces the
+// solver's stream: each runs twice untimed, then the candidates take turns for three rounds of one
+// timed launch each (CUDA events) on the solver's own tables and buffers; the candidate with the
+// fastest launch wins and is cached for the process.  opt.mixed_rw forces the
 // outputs per thread (the orientation is still timed); opt.mixed_variant forces a variant.
 namespace {
 std::mutex g_tune_mu;
@@ -778,38 +779,51 @@ bn_status tune_mixed2d(bn_solver* s, std::string* err) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        float best = 1e30f;
         const int v0 = forced == 16 ? 2 : 0, v1 = forced == 8 ? 2 : 4;
+        FusedArgs<float> A[4];
+        int grid[4];
         for (int v = v0; v < v1; ++v) {
             const int rw = v < 2 ? 8 : 16;
-            FusedArgs<float> A;
             s->mixed_rw = rw;
             s->mixed_v = v;
-            fill_args_t<float>(s, A);
-            A.items = s->work.items;   // the full cubic work list (timing does not depend on eps or values)
-            A.count = s->work.count;
-            A.eps = 1.0;
-            const int grid = std::min(parts(rw), s->n_partials);
-            for (int i = 0; i < 2; ++i) launch_mixed2d_kernel(A, grid, rw, s->stream);
-            cudaEventRecord(e0, s->stream);
-            for (int i = 0; i < 3; ++i) launch_mixed2d_kernel(A, grid, rw, s->stream);
-            cudaEventRecord(e1, s->stream);
-            cudaError_t e = cudaEventSynchronize(e1);
-            float ms = 0;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                cudaGetLastError();
-                *err = std::string("autotuner: ") + cudaGetErrorString(e);
-                return BN_ERR_CUDA;
+            fill_args_t<float>(s, A[v]);
+            A[v].items = s->work.items;   // the full cubic work list (timing does not depend on eps or values)
+            A[v].count = s->work.count;
+            A[v].eps = 1.0;
+            grid[v] = std::min(parts(rw), s->n_partials);
+        }
+        // all candidates warm up first, then take turns: kRounds rounds of one timed launch each, the
+        // fastest launch of a candidate counting (so a slow first launch or a transient on the GPU
+        // does not decide)
+        constexpr int kRounds = 3;
+        for (int v = v0; v < v1; ++v)
+            for (int i = 0; i < 2; ++i) launch_mixed2d_kernel(A[v], grid[v], v < 2 ? 8 : 16, s->stream);
+        float tmin[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+        for (int round = 0; round < kRounds; ++round)
+            for (int v = v0; v < v1; ++v) {
+                cudaEventRecord(e0, s->stream);
+                launch_mixed2d_kernel(A[v], grid[v], v < 2 ? 8 : 16, s->stream);
+                cudaEventRecord(e1, s->stream);
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    cudaGetLastError();
+                    *err = std::string("autotuner: ") + cudaGetErrorString(e);
+                    return BN_ERR_CUDA;
+                }
+                tmin[v] = std::min(tmin[v], ms);
             }
-            s->tune_ms[v] = ms / 3.0f;
-            if (ms < best) {
-                best = ms;
+        float best = 1e30f;
+        for (int v = v0; v < v1; ++v) {
+            s->tune_ms[v] = tmin[v];
+            if (tmin[v] < best) {
+                best = tmin[v];
                 choice = v;
             }
-            s->launches += 5;
+            s->launches += 2 + kRounds;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
