@@ -191,8 +191,13 @@ class Solver:
         """f_dev: a contiguous float64 CUDA tensor with N^d entries."""
         _check(_lib.bn_set_state_device(self._h, ctypes.c_void_p(f_dev.data_ptr()), f_dev.numel()))
 
-    def get_state(self) -> np.ndarray:
-        out = np.empty(self.n_modes)
+    def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The state on the host; into ``out`` (contiguous float64, N^d entries, e.g. pinned memory)
+        when given, else into a new array."""
+        if out is None:
+            out = np.empty(self.n_modes)
+        elif out.dtype != np.float64 or out.size != self.n_modes or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of N^d entries")
         _check(_lib.bn_get_state(self._h, _dptr(out), out.size))
         return out.reshape(self.shape)
 
