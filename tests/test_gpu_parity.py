@@ -281,3 +281,26 @@ def test_bench_workload_step_vs_oracle(B):
     finally:
         for s in solvers:
             s.close()
+
+
+@pytest.mark.parametrize("cfg", ["fermions_n16", "bkw_n32"])
+def test_full_run_against_oracle(B, cfg):
+    """Whole runs of the small configurations against the oracle's run of the same RK4 steps:
+    the 2-D Fermi-Dirac pair of Gaussians (N=16, eps=-1, max f0 = 0.8, dt = 0.01 to t = 2: 200 steps)
+    and the classical BKW datum (N=32, eps=0, t0 = 1 to t = 5 with dt = 0.005: 800 steps). FP64 within
+    1e-12 of the oracle's state; mixed precision within 1e-6 (the serving target on final states)."""
+    if cfg == "fermions_n16":
+        N, eps, dt, nsteps, f0 = 16, -1.0, 0.01, 200, I.config0_f0(16, R6)
+    else:
+        N, eps, dt, nsteps, f0 = 32, 0.0, 0.005, 800, I.config1_bkw_f0(32, R6)
+    ref = O.Operator(2, N, T6, R6, 0, eps, M=2 * N).step(f0, dt, nsteps, 0).reshape(N, N)
+    for precision, tol in ((B.FP64, 1e-12), (B.MIXED, 1e-6)):
+        with B.Solver(2, N, T6, R6, B.MAXWELL, eps, precision=precision) as s:
+            s.set_state(f0)
+            s.step_rk(dt, nsteps)
+            got = s.get_state().reshape(N, N)
+            t_end = s.moments()[-1]
+        err = rel(got, ref, ref)
+        print(f"{cfg} {'fp64' if precision == B.FP64 else 'mixed'}: e_f = {err:.3e} after {nsteps} steps")
+        assert t_end == pytest.approx(nsteps * dt, rel=1e-12)
+        assert err <= tol
