@@ -217,17 +217,13 @@ __device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b
     b = p[1];
 }
 
-// One s_1 row of the Toeplitz product: ar/ai[r] += sum_{s2} beta(c0 + r - s2) P(s2), with the
-// weights held in a register window whose slots rotate (slot of offset x is x mod RW), so that
-// every step costs one load of beta, half a load of P (pairs, the row starts 16-byte aligned)
-// and 2 RW FMA, with no register moves.
-// FP32 form of the row sweep below: the (real, imaginary) sums of an output and the duplicated
-// weight are packed pairs, so that one paired FMA (fma.rn.f32x2, rounded per half exactly as fmaf)
-// serves both parts of P: per step one load of beta, half a load of P and RW paired FMA.
-// FP32 sweep of one s_1 row from the staged rectangle (the mixed N > 32 kernel): the same paired-FMA
-// window as row_sweep_f32, with the rectangle row as a plain pointer and one 64-bit load of P per
-// step, which lets the compiler address every load from one base (15 % faster than the generic
-// form at N = 64, bitwise the same sums).
+// FP32 sweep of one s_1 row from the staged rectangle (the mixed N > 32 kernel): ar/ai[r] +=
+// sum_{s2} beta(c0 + r - s2) P(s2) with the (real, imaginary) sums of an output and the duplicated
+// weight held as packed pairs, so that one paired FMA (fma.rn.f32x2, rounded per half exactly as
+// fmaf) serves both parts of P; the weights rotate through a register window (slot of offset x is
+// x mod RW).  Per step: one load of beta, its duplication, one 64-bit load of P and RW paired FMA.
+// The rectangle row is a plain pointer, so every load is addressed from one base (a form with a
+// load functor and paired P loads issued ~7 register moves per step: 15 % slower at N = 64).
 template <int RW>
 __device__ __forceinline__ void row_sweep_p(const float* __restrict__ brow, int c0, const uint64_t* __restrict__ prow,
                                             int S2, float (&ar)[RW], float (&ai)[RW]) {
@@ -267,58 +263,14 @@ __device__ __forceinline__ void row_sweep_p(const float* __restrict__ brow, int 
     for (int r = 0; r < RW; ++r) split2(acc[r], ar[r], ai[r]);
 }
 
-template <int RW, typename LoadB>
-__device__ __forceinline__ void row_sweep_f32(LoadB ldb, int c0, const float2* __restrict__ prow, int S2,
-                                              float (&ar)[RW], float (&ai)[RW]) {
-    uint64_t acc[RW], w[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-        acc[r] = pack2(ar[r], ai[r]);
-        w[r] = dup2(ldb(c0 + r));
-    }
-    int sl = 0;
-    for (; sl + RW <= S2; sl += RW) {
-#pragma unroll
-        for (int k = 0; k < RW; k += 2) {
-            const ulonglong2 pp = *reinterpret_cast<const ulonglong2*>(prow + sl + k);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int kk = k + h;
-                if (kk == 0) {
-                    if (sl > 0) w[0] = dup2(ldb(c0 - sl));
-                } else {
-                    w[RW - kk] = dup2(ldb(c0 - sl - kk));
-                }
-                const uint64_t p = h == 0 ? pp.x : pp.y;
-#pragma unroll
-                for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < RW; ++k) {
-        if (sl + k >= S2) break;
-        if (k == 0) {
-            if (sl > 0) w[0] = dup2(ldb(c0 - sl));
-        } else {
-            w[RW - k] = dup2(ldb(c0 - sl - k));
-        }
-        const uint64_t p = *reinterpret_cast<const uint64_t*>(prow + sl + k);
-#pragma unroll
-        for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - k + RW) % RW], p, acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < RW; ++r) split2(acc[r], ar[r], ai[r]);
-}
-
+// One s_1 row of the Toeplitz product in the generic form (FP64, and the unstaged path): ar/ai[r]
+// += sum_{s2} beta(c0 + r - s2) P(s2), with the weights held in a register window whose slots
+// rotate (slot of offset x is x mod RW), so that every step costs one load of beta, half a load
+// of P (pairs, the row starts 16-byte aligned) and 2 RW FMA, with no register moves.
 template <typename Real, int RW, typename LoadB>
 __device__ __forceinline__ void row_sweep(LoadB ldb, int c0, const cplx<Real>* __restrict__ prow, int S2,
                                           Real (&ar)[RW], Real (&ai)[RW]) {
     static_assert(RW % 2 == 0, "RW must be even");
-    if constexpr (std::is_same<Real, float>::value) {
-        row_sweep_f32<RW>(ldb, c0, prow, S2, ar, ai);
-        return;
-    }
     Real w[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) w[r] = ldb(c0 + r);
