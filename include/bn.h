@@ -57,7 +57,7 @@ typedef enum {
     BN_ERR_NONFINITE = -5,   /* the state became NaN/Inf during step_rk (state rolled back) */
     BN_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
     BN_ERR_STATE = -7,       /* call out of order (e.g. no state set) */
-    BN_ERR_UNSUPPORTED = -8  /* combination not implemented (e.g. 2-D hard spheres) */
+    BN_ERR_UNSUPPORTED = -8  /* combination not implemented (e.g. 3-D Maxwell molecules) */
 } bn_status;
 
 typedef enum { BN_MAXWELL = 0, BN_HARD_SPHERE = 1 } bn_kernel;
@@ -143,8 +143,10 @@ bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count);
  * clears what must start at zero.  Calls whose GPU work overlaps in time (other
  * threads, other streams) race on it: serialise them.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), which is
- * also when the driver loads the array onto that device; make that first call
- * before any stream capture.  The solver's read-only kernel-mode
+ * also when the driver loads the array onto that device.  Every call reads an
+ * error flag back and synchronises cuda_stream, so no call can be made while a stream is
+ * being captured.  The current device must be the solver's device (BN_ERR_ARG
+ * otherwise).  The solver's read-only kernel-mode
  * tables, work lists and twiddles are used; the solver itself is not modified.
  * 2-D solvers only (BN_ERR_UNSUPPORTED otherwise).  Runs on cuda_stream (NULL =
  * legacy default stream) and returns when Q_dev holds the result.

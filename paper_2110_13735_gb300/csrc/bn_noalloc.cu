@@ -30,20 +30,18 @@ void* g_na_ptr[64] = {};   // device address of the array, per device ordinal (s
 
 inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Device address of the scratch array on the current device; the first call on a device
-// looks it up (host code may not take the address of a __device__ variable directly).
-bn_status scratch_ptr(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
-        cudaGetLastError();
-        bn::set_last_error("no usable CUDA device");
+// Device address of the scratch array on device `dev`, which must be the current device; the
+// first call on a device looks it up (host code may not take the address of a __device__
+// variable directly: its host-side name is only a stand-in).
+bn_status scratch_ptr(int dev, void** out) {
+    if (dev < 0 || dev >= 64) {
+        bn::set_last_error("device ordinal out of range for the no-allocation scratch");
         return BN_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_na_mu);
     if (!g_na_ptr[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             bn::set_last_error(std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e));
@@ -63,6 +61,17 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
                                     void* cuda_stream) {
     if (!s || !f_dev || !Q_dev) {
         bn::set_last_error("null argument");
+        return BN_ERR_ARG;
+    }
+    // the solver's tables and work lists live on s->device: the call must run there
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        bn::set_last_error("no usable CUDA device");
+        return BN_ERR_CUDA;
+    }
+    if (cur != s->device) {
+        bn::set_last_error("the current device is not the solver's device: make the solver's device current first");
         return BN_ERR_ARG;
     }
     if (s->g.d != 2) {
@@ -92,7 +101,7 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
         return BN_ERR_ARG;
     }
     void* base = nullptr;
-    bn_status st = scratch_ptr(&base);
+    bn_status st = scratch_ptr(s->device, &base);
     if (st != BN_OK) return st;
     unsigned char* b = static_cast<unsigned char*>(base);
     int* err = reinterpret_cast<int*>(b + o_err);

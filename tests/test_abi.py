@@ -69,6 +69,8 @@ def test_create_rejects_bad_escalation_threshold(lib):
 
 def test_null_handles(lib):
     assert lib.bn_set_state(None, None, 0) == -1
+    # the no-allocation evaluation checks its arguments before any CUDA call
+    assert lib.bn_eval_collision_noalloc(None, None, None, 0, None) == -1
     assert lib.bn_step_rk(None, 0.1, 1) == -1
     assert lib.bn_kernel_launches(None) == 0
     lib.bn_destroy_solver(None)
