@@ -225,6 +225,18 @@ bn_status bn_kernel_config(const bn_solver* s, double* out, size_t count);
  * n_items is NULL, or count < 14 x items. */
 bn_status bn_plan_mixed2d(int N, int rw, int oriented, int nblk, int* out, size_t count, int* n_items);
 
+/*
+ * Measured CUDA-core FMA rate of the current device, the roofline denominator of the operator
+ * kernels (not part of the paper).  kind 0 = FP32 FMA (fmaf), 1 = paired FP32 FMA
+ * (fma.rn.f32x2, two multiply-adds per instruction), 2 = FP64 FMA.  Runs 4 CTAs of 256 threads
+ * per SM, each thread 8 independent chains of dependent multiply-adds, on cuda_stream (NULL =
+ * legacy default stream); the fastest of three timed launches (CUDA events) after an untimed
+ * one.  out[0] = TFLOP/s (2 flops per multiply-add), out[1] = ms of that launch, out[2] = its
+ * flops; count >= 3.  Allocates and frees a small device buffer; synchronises cuda_stream.
+ * The rate is that of the SM clock during the run: sample the clock alongside.
+ */
+bn_status bn_measure_fma_peak(int kind, void* cuda_stream, double* out, size_t count);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* bn_last_error(void);
 

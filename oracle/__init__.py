@@ -41,7 +41,7 @@ class _Params(ctypes.Structure):
         ("d", ctypes.c_int), ("N", ctypes.c_int), ("T", ctypes.c_double), ("R", ctypes.c_double),
         ("kernel", ctypes.c_int), ("eps", ctypes.c_double), ("M", ctypes.c_int),
         ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("c_phi", ctypes.c_double), ("quad3d", ctypes.c_int),
-        ("Q", ctypes.c_int),
+        ("Q", ctypes.c_int), ("wrap", ctypes.c_int),
     ]
 
 
@@ -59,6 +59,9 @@ def _load():
         _lib.ora_dft_inverse_real.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
         _lib.ora_collision_modes.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
         _lib.ora_collision_modes_onthefly.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.ora_collision_modes_at.argtypes = [P, dp, dp, dp, ip, ctypes.c_int, dp, dp, dp, dp]
+        _lib.ora_conserve.argtypes = [P, dp]
         _lib.ora_eval_collision_onthefly.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
         _lib.ora_scale.argtypes = [P]
         _lib.ora_scale.restype = ctypes.c_double
@@ -93,7 +96,10 @@ class Operator:
     radius in velocity units (the paper's S = R, Sec. 4.1), ``kernel`` 0 for
     Maxwell molecules (2-D) and 1 for hard spheres (3-D, and 2-D by reading r5 of
     the C source with ``Q`` Gauss-Legendre points per radius), ``eps`` = +1
-    bosons, -1 fermions, 0 classical (alpha = -eps in the paper's notation).
+    bosons, -1 fermions, 0 classical (alpha = -eps in the paper's notation),
+    ``wrap`` 0 for the Lemma's LINEAR truncation, 1 for the CIRCULAR variant
+    (reading r6 of the C source).  Angular points: M = 2N (2-D), M1 = M2 = N/2 (3-D)
+    unless given.
     """
     d: int
     N: int
@@ -107,6 +113,7 @@ class Operator:
     c_phi: float = 0.0
     quad3d: int = 0
     Q: int = 0
+    wrap: int = 0
 
     def __post_init__(self):
         if self.Q == 0:
@@ -114,21 +121,22 @@ class Operator:
         if self.M == 0:
             self.M = 2 * self.N
         if self.M1 == 0:
-            self.M1 = self.N
+            self.M1 = self.N // 2
         if self.M2 == 0:
-            self.M2 = self.N
+            self.M2 = self.N // 2
         if self.c_phi == 0.0:
             self.c_phi = 1.0 / (2 * math.pi) if self.d == 2 else 1.0 / (4 * math.pi)
         self._beta = None
         self._alpha = None
 
     # full kernel-mode tables above this many entries are not formed; beta is then
-    # evaluated on demand from the alpha tables (the sum of eq. betadD)
-    TABLE_LIMIT = 1 << 29
+    # evaluated on demand from the alpha tables (the sum of eq. betadD); in 3-D the
+    # on-demand sum is also the faster one beyond N = 8
+    TABLE_LIMIT = {2: 1 << 29, 3: 1 << 25}
 
     @property
     def use_table(self) -> bool:
-        return (2 * self.N) ** (2 * self.d) <= self.TABLE_LIMIT
+        return (2 * self.N) ** (2 * self.d) <= self.TABLE_LIMIT[self.d]
 
     def _alpha_cached(self):
         if self._alpha is None:
@@ -138,7 +146,7 @@ class Operator:
 
     def _p(self):
         return _Params(self.d, self.N, self.T, self.R, self.kernel, self.eps, self.M, self.M1,
-                       self.M2, self.c_phi, self.quad3d, self.Q)
+                       self.M2, self.c_phi, self.quad3d, self.Q, self.wrap)
 
     @property
     def n_modes(self) -> int:
@@ -208,6 +216,34 @@ class Operator:
                                                  int(n_cnt), *[_ptr(o) for o in outs])
         shape = (n_cnt,) * self.d
         return tuple(o.view(np.complex128).reshape(shape) for o in outs)
+
+    def collision_modes_at(self, Ghat: np.ndarray, nlist):
+        """The Lemma's sums at the listed output modes (an (count, d) integer array of modes in
+        I_N), beta on demand from the alpha tables.  Returns (Qhat, gain, loss, cubic), each a
+        complex array of length count."""
+        G = np.ascontiguousarray(np.asarray(Ghat, dtype=np.complex128).reshape(-1))
+        assert G.size == self.n_modes
+        nl = np.ascontiguousarray(np.asarray(nlist, dtype=np.int32).reshape(-1, self.d))
+        assert np.all(nl >= -self.N // 2) and np.all(nl < self.N // 2)
+        count = nl.shape[0]
+        outs = [np.zeros(2 * count) for _ in range(4)]
+        al, ap = self._alpha_cached()
+        p = self._p()
+        r = _load().ora_collision_modes_at(ctypes.byref(p), _ptr(al), _ptr(ap), _ptr(G.view(np.float64)),
+                                           nl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(count),
+                                           *[_ptr(o) for o in outs])
+        if r != 0:
+            raise MemoryError("oracle alpha-table copy failed")
+        return tuple(o.view(np.complex128) for o in outs)
+
+    def conserve(self, Q: np.ndarray) -> np.ndarray:
+        """The conservation projection Q - C^T (C C^T)^{-1} C Q onto zero mass, momentum and
+        energy (C: the collision invariants 1, v, |v|^2 on the grid)."""
+        out = np.ascontiguousarray(np.asarray(Q, dtype=np.float64).reshape(-1)).copy()
+        assert out.size == self.n_modes
+        p = self._p()
+        _load().ora_conserve(ctypes.byref(p), _ptr(out))
+        return out.reshape((self.N,) * self.d)
 
     def dft(self, f: np.ndarray) -> np.ndarray:
         f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))

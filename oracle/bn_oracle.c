@@ -43,6 +43,12 @@
  *        Gauss-Legendre rule with Q points on [-R,R] in each radius; summing
  *        over the rho nodes first leaves a separable sum over (theta_p, rho'_j)
  *        with P = M Q terms.  Default Q = N + 8.
+ *   (r6) CIRCULAR truncation (wrap = 1): the Appendix evaluates Q_{1,q} with
+ *        discrete transforms, whose index arithmetic is modulo N.  In this
+ *        variant every index sum (n = k+l(+m), and the kernel-mode arguments
+ *        k+m, l+m) is reduced into I_N modulo N before it is used, and beta is
+ *        taken at the reduced representatives.  LINEAR (wrap = 0) is the
+ *        Lemma's definition and the default.
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC bn_oracle.c -o libbn_oracle.so -lm
  */
@@ -71,6 +77,8 @@ typedef struct {
     double c_phi;   /* C_Phi */
     int quad3d;     /* 0: Gauss-Legendre in cos(theta); 1: printed rectangle rule */
     int Q;          /* 2-D hard spheres: Gauss-Legendre points per radius (reading r5) */
+    int wrap;       /* 0: LINEAR truncation (the Lemma: k,l,m,n in I_N, sums exact);
+                       1: CIRCULAR (reading r6): every index sum reduced into I_N mod N */
 } ora_params;
 
 static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
@@ -312,56 +320,138 @@ int ora_dft_inverse_real(int d, int N, const double* Qhat, double* Q) {
  * (cubic is returned as 0).
  */
 /* Kernel modes: either a full table (beta != NULL) or the sum of eq. betadD
- * evaluated on demand from the alpha tables (al, ap: P x (2N)^d each). */
+ * evaluated on demand.  For the on-demand sum the alpha tables are copied
+ * node-last ([a][p]) so that one beta is a dot product of two contiguous rows;
+ * the sum over p is carried in four interleaved partial sums (p mod 4) added at
+ * the end, which changes only the rounding order of the sum over the nodes. */
 typedef struct { const double* beta; const double* al; const double* ap; int P; int nE; } ora_kernel_modes;
 
 static double beta_get(const ora_kernel_modes* km, int ia, int ib) {
     if (km->beta) return km->beta[(size_t)ia * km->nE + ib];
-    double s = 0.0;
-    for (int q = 0; q < km->P; ++q) s += km->al[(size_t)q * km->nE + ia] * km->ap[(size_t)q * km->nE + ib];
-    return s;
+    const double* x = km->al + (size_t)ia * km->P;
+    const double* y = km->ap + (size_t)ib * km->P;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int q = 0;
+    for (; q + 3 < km->P; q += 4) {
+        s0 += x[q] * y[q];
+        s1 += x[q + 1] * y[q + 1];
+        s2 += x[q + 2] * y[q + 2];
+        s3 += x[q + 3] * y[q + 3];
+    }
+    for (; q < km->P; ++q) s0 += x[q] * y[q];
+    return (s0 + s1) + (s2 + s3);
 }
 
-static int collision_modes_impl(const ora_params* p, const ora_kernel_modes* km, const double* Ghat,
-                                int n_lo, int n_cnt,
-                                double* Qhat, double* gain, double* loss, double* cubic) {
-    const int d = p->d, N = p->N, nN = ipow(N, d);
-    const int nOut = ipow(n_cnt, d);
+/* Node-last copies of the alpha tables for beta_get (caller frees). */
+static int transpose_alpha(const ora_params* p, const double* al, const double* ap, double** alT, double** apT) {
+    const int nE = ipow(2 * p->N, p->d), P = ora_num_terms(p);
+    *alT = (double*)malloc(sizeof(double) * (size_t)P * nE);
+    *apT = (double*)malloc(sizeof(double) * (size_t)P * nE);
+    if (!*alT || !*apT) { free(*alT); free(*apT); return -1; }
+    #pragma omp parallel for schedule(static)
+    for (int ia = 0; ia < nE; ++ia)
+        for (int q = 0; q < P; ++q) {
+            (*alT)[(size_t)ia * P + q] = al[(size_t)q * nE + ia];
+            (*apT)[(size_t)ia * P + q] = ap[(size_t)q * nE + ia];
+        }
+    return 0;
+}
+
+/* x reduced into I_N = [-N/2, N/2-1] modulo N (reading r6). */
+static int wrap_IN(int x, int N) {
+    int r = (x + N / 2) % N;
+    if (r < 0) r += N;
+    return r - N / 2;
+}
+
+static int is_zero(cplx z) { return creal(z) == 0.0 && cimag(z) == 0.0; }
+
+/*
+ * The Lemma's sums for one output mode n (LINEAR: n may lie outside I_N, giving
+ * the unprojected modes; CIRCULAR: n in I_N).  A term with a factor G^ that is
+ * exactly zero is skipped (it adds nothing).
+ *   gain  = sum_{k+l=n} beta(k,l) G_k G_l,   loss = sum_{k+l=n} beta(l,l) G_k G_l,
+ *   cubic = sum_{k+l+m=n} [beta(k+m,l+m) + beta(l,m) - beta(l+m,l) - beta(l,l+m)] G_k G_l G_m.
+ */
+static void one_output(const ora_params* p, const ora_kernel_modes* km, const cplx* G, const int* n,
+                       cplx* out_g, cplx* out_l, cplx* out_c) {
+    const int d = p->d, N = p->N, nN = ipow(N, d), wrap = p->wrap;
     const double alpha = -p->eps;
-    const cplx* G = (const cplx*)Ghat;
+    int k[3], l[3], m[3], kpm[3], lpm[3];
 #define BETA(a, b) beta_get(km, flat_ext(a, d, N), flat_ext(b, d, N))
-    #pragma omp parallel for schedule(dynamic, 1)
-    for (int io = 0; io < nOut; ++io) {
-        int n[3], k[3], l[3], m[3], kpm[3], lpm[3];
-        unflat(io, d, n_cnt, -n_lo, n);
-        cplx sg = 0.0, sl = 0.0, sc = 0.0;
-        for (int ik = 0; ik < nN; ++ik) {
-            unflat(ik, d, N, N / 2, k);
-            /* quadratic: l = n - k */
-            for (int i = 0; i < d; ++i) l[i] = n[i] - k[i];
-            if (in_IN(l, d, N)) {
-                cplx gg = G[ik] * G[flat_IN(l, d, N)];
+    cplx sg = 0.0, sl = 0.0, sc = 0.0;
+    for (int ik = 0; ik < nN; ++ik) {
+        if (is_zero(G[ik])) continue;
+        unflat(ik, d, N, N / 2, k);
+        /* quadratic: l = n - k */
+        for (int i = 0; i < d; ++i) l[i] = wrap ? wrap_IN(n[i] - k[i], N) : n[i] - k[i];
+        if (in_IN(l, d, N)) {
+            const cplx gl = G[flat_IN(l, d, N)];
+            if (!is_zero(gl)) {
+                cplx gg = G[ik] * gl;
                 sg += BETA(k, l) * gg;
                 sl += BETA(l, l) * gg;
             }
-            if (alpha == 0.0) continue;   /* the cubic bracket is multiplied by alpha */
-            /* cubic: m = n - k - l */
-            for (int il = 0; il < nN; ++il) {
-                unflat(il, d, N, N / 2, l);
-                for (int i = 0; i < d; ++i) m[i] = n[i] - k[i] - l[i];
-                if (!in_IN(m, d, N)) continue;
-                for (int i = 0; i < d; ++i) { kpm[i] = k[i] + m[i]; lpm[i] = l[i] + m[i]; }
-                double w = BETA(kpm, lpm) + BETA(l, m) - BETA(lpm, l) - BETA(l, lpm);
-                sc += w * G[ik] * G[il] * G[flat_IN(m, d, N)];
-            }
         }
-        cplx q = sg - sl - alpha * sc;
-        if (Qhat)  { Qhat[2 * io] = creal(q);   Qhat[2 * io + 1] = cimag(q); }
-        if (gain)  { gain[2 * io] = creal(sg);  gain[2 * io + 1] = cimag(sg); }
-        if (loss)  { loss[2 * io] = creal(sl);  loss[2 * io + 1] = cimag(sl); }
-        if (cubic) { cubic[2 * io] = creal(sc); cubic[2 * io + 1] = cimag(sc); }
+        if (alpha == 0.0) continue;   /* the cubic bracket is multiplied by alpha */
+        /* cubic: m = n - k - l */
+        for (int il = 0; il < nN; ++il) {
+            if (is_zero(G[il])) continue;
+            unflat(il, d, N, N / 2, l);
+            for (int i = 0; i < d; ++i) m[i] = wrap ? wrap_IN(n[i] - k[i] - l[i], N) : n[i] - k[i] - l[i];
+            if (!in_IN(m, d, N)) continue;
+            const cplx gm = G[flat_IN(m, d, N)];
+            if (is_zero(gm)) continue;
+            for (int i = 0; i < d; ++i) {
+                kpm[i] = wrap ? wrap_IN(k[i] + m[i], N) : k[i] + m[i];
+                lpm[i] = wrap ? wrap_IN(l[i] + m[i], N) : l[i] + m[i];
+            }
+            double w = BETA(kpm, lpm) + BETA(l, m) - BETA(lpm, l) - BETA(l, lpm);
+            sc += w * G[ik] * G[il] * gm;
+        }
     }
 #undef BETA
+    *out_g = sg; *out_l = sl; *out_c = sc;
+}
+
+static void store_output(int io, double alpha, cplx sg, cplx sl, cplx sc,
+                         double* Qhat, double* gain, double* loss, double* cubic) {
+    cplx q = sg - sl - alpha * sc;
+    if (Qhat)  { Qhat[2 * io] = creal(q);   Qhat[2 * io + 1] = cimag(q); }
+    if (gain)  { gain[2 * io] = creal(sg);  gain[2 * io + 1] = cimag(sg); }
+    if (loss)  { loss[2 * io] = creal(sl);  loss[2 * io + 1] = cimag(sl); }
+    if (cubic) { cubic[2 * io] = creal(sc); cubic[2 * io + 1] = cimag(sc); }
+}
+
+/*
+ * Lemma of Sec. 2.3, for the output modes n in the box [n_lo, n_lo + n_cnt)^d
+ * (n_lo = -N/2, n_cnt = N gives I_N; in LINEAR mode a larger box gives the
+ * unprojected modes of Q^R(G) for a band-limited G).  beta is the table of
+ * ora_beta_table.
+ *
+ * out (interleaved complex, n_cnt^d entries each):
+ *   gain  = Q^_{1c}(G,G)_n = sum_{k+l=n}       beta(k,l)   G_k G_l
+ *   loss  = Q^_{2c}(G,G)_n = sum_{k+l=n}       beta(l,l)   G_k G_l
+ *   cubic = [Q1q+Q2q-Q3q-Q4q]_n = sum_{k+l+m=n} [beta(k+m,l+m) + beta(l,m)
+ *                                - beta(l+m,l) - beta(l,l+m)] G_k G_l G_m
+ *   Qhat  = gain - loss - alpha*cubic,   alpha = -eps.
+ * Any of the outputs may be NULL; for eps = 0 the cubic sum is not formed
+ * (cubic is returned as 0).
+ */
+static int collision_modes_impl(const ora_params* p, const ora_kernel_modes* km, const double* Ghat,
+                                int n_lo, int n_cnt,
+                                double* Qhat, double* gain, double* loss, double* cubic) {
+    const int d = p->d;
+    const int nOut = ipow(n_cnt, d);
+    const cplx* G = (const cplx*)Ghat;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int io = 0; io < nOut; ++io) {
+        int n[3];
+        unflat(io, d, n_cnt, -n_lo, n);
+        cplx sg, sl, sc;
+        one_output(p, km, G, n, &sg, &sl, &sc);
+        store_output(io, -p->eps, sg, sl, sc, Qhat, gain, loss, cubic);
+    }
     return 0;
 }
 
@@ -377,8 +467,32 @@ int ora_collision_modes(const ora_params* p, const double* beta, const double* G
 int ora_collision_modes_onthefly(const ora_params* p, const double* al, const double* ap, const double* Ghat,
                                  int n_lo, int n_cnt,
                                  double* Qhat, double* gain, double* loss, double* cubic) {
-    ora_kernel_modes km = {NULL, al, ap, ora_num_terms(p), ipow(2 * p->N, p->d)};
-    return collision_modes_impl(p, &km, Ghat, n_lo, n_cnt, Qhat, gain, loss, cubic);
+    double *alT, *apT;
+    if (transpose_alpha(p, al, ap, &alT, &apT) != 0) return -1;
+    ora_kernel_modes km = {NULL, alT, apT, ora_num_terms(p), ipow(2 * p->N, p->d)};
+    int r = collision_modes_impl(p, &km, Ghat, n_lo, n_cnt, Qhat, gain, loss, cubic);
+    free(alT); free(apT);
+    return r;
+}
+
+/* The Lemma's sums at a list of output modes n (count vectors of d ints, each
+ * component in I_N), beta on demand from the alpha tables; outputs as in
+ * ora_collision_modes, one entry per listed mode. */
+int ora_collision_modes_at(const ora_params* p, const double* al, const double* ap, const double* Ghat,
+                           const int* nlist, int count,
+                           double* Qhat, double* gain, double* loss, double* cubic) {
+    double *alT, *apT;
+    if (transpose_alpha(p, al, ap, &alT, &apT) != 0) return -1;
+    ora_kernel_modes km = {NULL, alT, apT, ora_num_terms(p), ipow(2 * p->N, p->d)};
+    const cplx* G = (const cplx*)Ghat;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int io = 0; io < count; ++io) {
+        cplx sg, sl, sc;
+        one_output(p, &km, G, nlist + (size_t)io * p->d, &sg, &sl, &sc);
+        store_output(io, -p->eps, sg, sl, sc, Qhat, gain, loss, cubic);
+    }
+    free(alT); free(apT);
+    return 0;
 }
 
 /* (T/pi)^{d+gamma}: the classical-method prefactor of Sec. 3.2 (c = 1). */
@@ -422,8 +536,12 @@ int ora_eval_collision(const ora_params* p, const double* beta, const double* f,
 
 int ora_eval_collision_onthefly(const ora_params* p, const double* al, const double* ap, const double* f,
                                 double* Q, double* gain_v, double* loss_v, double* cubic_v) {
-    ora_kernel_modes km = {NULL, al, ap, ora_num_terms(p), ipow(2 * p->N, p->d)};
-    return eval_impl(p, &km, f, Q, gain_v, loss_v, cubic_v);
+    double *alT, *apT;
+    if (transpose_alpha(p, al, ap, &alT, &apT) != 0) return -1;
+    ora_kernel_modes km = {NULL, alT, apT, ora_num_terms(p), ipow(2 * p->N, p->d)};
+    int r = eval_impl(p, &km, f, Q, gain_v, loss_v, cubic_v);
+    free(alT); free(apT);
+    return r;
 }
 
 /* Classical RK4 (integrator 0) or SSP-RK2 / Heun (integrator 1) on df/dt = Q(f). */
@@ -500,6 +618,55 @@ int ora_moments(const ora_params* p, const double* f, double* out) {
     out[0] = rho;
     for (int i = 0; i < d; ++i) out[1 + i] = mom[i];
     out[1 + d] = e; out[2 + d] = ec; out[3 + d] = H; out[4 + d] = fmax;
+    return 0;
+}
+
+/*
+ * Conservation projection (not in the paper; the constrained L^2 projection of
+ * Gamba & Tharkabhushanam, 2009): Q* = Q - C^T (C C^T)^{-1} C Q, with the d+2
+ * rows of C the collision invariants 1, v_1..v_d, |v|^2 sampled on the grid
+ * v_j = 2Tj/N (the common factor dv cancels).  The (d+2) x (d+2) system
+ * (C C^T) lambda = C Q is solved by Gaussian elimination with partial pivoting.
+ */
+int ora_conserve(const ora_params* p, double* Q) {
+    const int d = p->d, N = p->N, nN = ipow(N, d), nc = d + 2;
+    const double h = 2.0 * p->T / N;
+    double A[5][6];
+    memset(A, 0, sizeof(A));
+    int j[3];
+    for (int ij = 0; ij < nN; ++ij) {
+        unflat(ij, d, N, N / 2, j);
+        double psi[5], v2 = 0.0;
+        psi[0] = 1.0;
+        for (int i = 0; i < d; ++i) { psi[1 + i] = h * j[i]; v2 += psi[1 + i] * psi[1 + i]; }
+        psi[1 + d] = v2;
+        for (int a = 0; a < nc; ++a) {
+            for (int b = 0; b < nc; ++b) A[a][b] += psi[a] * psi[b];   /* C C^T */
+            A[a][nc] += psi[a] * Q[ij];                                 /* C Q */
+        }
+    }
+    for (int c = 0; c < nc; ++c) {              /* forward elimination */
+        int piv = c;
+        for (int r = c + 1; r < nc; ++r) if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        for (int k = 0; k <= nc; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        for (int r = c + 1; r < nc; ++r) {
+            double m = A[r][c] / A[c][c];
+            for (int k = c; k <= nc; ++k) A[r][k] -= m * A[c][k];
+        }
+    }
+    double lam[5];
+    for (int c = nc - 1; c >= 0; --c) {        /* back substitution */
+        double t = A[c][nc];
+        for (int k = c + 1; k < nc; ++k) t -= A[c][k] * lam[k];
+        lam[c] = t / A[c][c];
+    }
+    for (int ij = 0; ij < nN; ++ij) {          /* Q - C^T lambda */
+        unflat(ij, d, N, N / 2, j);
+        double v2 = 0.0, corr = lam[0];
+        for (int i = 0; i < d; ++i) { double v = h * j[i]; corr += lam[1 + i] * v; v2 += v * v; }
+        corr += lam[1 + d] * v2;
+        Q[ij] -= corr;
+    }
     return 0;
 }
 

@@ -75,6 +75,7 @@ def load(path: str | None = None):
     lib.bn_kernel_config.argtypes = [vp, dp, sz]
     ip = ctypes.POINTER(ctypes.c_int)
     lib.bn_plan_mixed2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, sz, ip]
+    lib.bn_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp, sz]
     lib.bn_kernel_launches.argtypes = [vp]
     lib.bn_kernel_launches.restype = ctypes.c_longlong
     lib.bn_last_error.restype = ctypes.c_char_p
@@ -264,6 +265,16 @@ class Solver:
         out = np.zeros(4)
         _check(_lib.bn_profile_read(self._h, _dptr(out), 4))
         return float(out[0]), int(out[1]), float(out[2]), int(out[3])
+
+
+def measure_fma_peak(kind: int, stream=None):
+    """Measured FMA rate of the current device (include/bn.h: bn_measure_fma_peak): kind 0 FP32,
+    1 paired FP32, 2 FP64.  Returns (TFLOP/s, ms of the timed launch)."""
+    lib = load()
+    raw = int(getattr(stream, "cuda_stream", stream)) if stream is not None else 0
+    out = np.zeros(3)
+    _check(lib.bn_measure_fma_peak(int(kind), ctypes.c_void_p(raw) if raw else None, _dptr(out), 3))
+    return float(out[0]), float(out[1])
 
 
 def step_rk_batch(solvers, dts, nsteps: int):
