@@ -87,6 +87,16 @@ typedef struct {
                          the per-b orientation choice is tuned in either case) */
     int mixed_variant; /* mixed 2-D N <= 32: 0 = as mixed_rw says; 1..4 forces the kernel
                          variant (8, 8 oriented, 16, 16 oriented outputs per thread) */
+    int wrap;         /* 0 = LINEAR truncation (the Lemma: k, l, m, n in I_N, sums exact; the
+                         default); 1 = CIRCULAR: every index sum reduced into I_N modulo N and
+                         beta taken at the reduced representatives, the index arithmetic of the
+                         Appendix's discrete-transform evaluation */
+    int beta_resident; /* 3-D and CIRCULAR: 1 = produce the kernel-mode slices beta(., b) once and
+                         keep them on the device when they fit the slice budget (else they are
+                         recomputed from the quadrature factors at every evaluation, the default) */
+    long long beta_budget_mb; /* 3-D and CIRCULAR: device memory (MiB) for the slices of one round
+                         (0 = 40% of the free memory, at most 40 GiB); slices that do not fit are
+                         produced and consumed in several rounds per evaluation */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */

@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("M1", ctypes.c_int), ("M2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
-                ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int)]
+                ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int), ("wrap", ctypes.c_int),
+                ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong)]
 
 
 class Request(ctypes.Structure):
@@ -129,11 +130,12 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
 
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
-            escalate_at=0.0, mixed_rw=0, mixed_variant=0) -> Options:
+            escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
+    o.wrap, o.beta_resident, o.beta_budget_mb = wrap, beta_resident, beta_budget_mb
     return o
 
 

@@ -49,12 +49,13 @@ void free_buffers(bn_solver* s) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
+    bn::free_nd(s);
 }
 
 // One evaluation Q = Q_eps(f_in) in velocity units, entirely on the solver's stream.
 void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
     bn::launch_dft_forward(s, f_in, s->Ghat);   // also writes the FP32 copy in mixed precision
-    if (s->g.d == 2) {
+    if (!s->nd) {
         // the whole 2-D operator in one pass over b (quadratic + reducible + Q_{1,q})
         const int slot = s->prof_slot;
         if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
@@ -67,17 +68,14 @@ void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
         if (s->opt.conserve) bn::launch_conserve(s, Q_out);
         return;
     }
-    bn::launch_pair_sums(s);
-    if (s->eps != 0.0) {
-        const int slot = s->prof_slot;
-        if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
-        bn::launch_triple_sum(s);
-        if (s->prof && slot < 8) {
-            cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
-            s->prof_slot = slot + 1;
-        }
+    // 3-D and CIRCULAR: kernel-mode slices recomputed per evaluation (bn_opnd.cu)
+    const int slot = s->prof_slot;
+    if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
+    bn::launch_nd(s, nullptr);
+    if (s->prof && slot < 8) {
+        cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
+        s->prof_slot = slot + 1;
     }
-    bn::launch_combine(s);
     bn::launch_dft_inverse_real(s, s->Qhat, Q_out, s->scale);
     if (s->opt.conserve) bn::launch_conserve(s, Q_out);
 }
@@ -140,6 +138,21 @@ void check_escalation(bn_solver* s) {
     if (s->opt.precision == BN_MIXED && s->opt.escalate_at > 0 && std::fabs(s->eps) * s->last_max_f >= s->opt.escalate_at) {
         s->opt.precision = BN_FP64;
         s->t_escalated = s->t;
+        if (s->nd) {
+            // the slice buffers and kernel shapes depend on the precision
+            cudaStreamSynchronize(s->stream);
+            bn::free_nd(s);
+            std::string err;
+            if (bn::plan_nd(s, &err) != BN_OK || bn::prepare_nd(s) != BN_OK) {
+                bn::free_nd(s);
+                s->opt.precision = BN_MIXED;
+                s->t_escalated = -1;
+                err = "escalation to FP64 failed: " + err;
+                bn::plan_nd(s, &err);
+                bn::prepare_nd(s);
+            }
+            s->n_partials = bn::nd_ctas(s);
+        }
         if (s->step_graph) {
             cudaGraphExecDestroy(s->step_graph);
             s->step_graph = nullptr;
@@ -197,8 +210,8 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     *out = nullptr;
     if (d != 2 && d != 3) return fail(BN_ERR_ARG, "d must be 2 or 3");
     if (N < 4 || N % 2 != 0) return fail(BN_ERR_ARG, "N must be even and >= 4");
-    if ((d == 2 && N > 64) || (d == 3 && N > 16))
-        return fail(BN_ERR_UNSUPPORTED, d == 2 ? "2-D N > 64 is not supported" : "3-D N > 16 is not supported yet");
+    if ((d == 2 && N > 64) || (d == 3 && N > 48))
+        return fail(BN_ERR_UNSUPPORTED, d == 2 ? "2-D N > 64 is not supported" : "3-D N > 48 is not supported");
     if (!(T > 0) || !(R > 0) || !std::isfinite(T) || !std::isfinite(R)) return fail(BN_ERR_ARG, "T and R must be > 0");
     if (!std::isfinite(eps)) return fail(BN_ERR_ARG, "eps must be finite");
     if (kernel != BN_MAXWELL && kernel != BN_HARD_SPHERE) return fail(BN_ERR_ARG, "unknown kernel");
@@ -240,6 +253,14 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(BN_ERR_ARG, "mixed_variant must be in 0..4");
     }
+    if (s->opt.wrap != 0 && s->opt.wrap != 1) {
+        delete s;
+        return fail(BN_ERR_ARG, "wrap must be 0 (LINEAR) or 1 (CIRCULAR)");
+    }
+    if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1)) {
+        delete s;
+        return fail(BN_ERR_ARG, "beta_budget_mb must be >= 0 and beta_resident 0 or 1");
+    }
     if (s->opt.M <= 0) s->opt.M = 2 * N;
     if (s->opt.c_phi <= 0) s->opt.c_phi = d == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI);
     if (d == 2) {
@@ -270,17 +291,19 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(st, err);
     }
-    st = bn::build_work_list(s, &err);
-    if (st != BN_OK) {
-        bn::release_tables(s->tabs);
-        if (s->own_stream) cudaStreamDestroy(s->stream);
-        delete s;
-        return fail(st, err);
+    const bool nd = bn::use_nd(s);
+    if (nd) {
+        st = bn::plan_nd(s, &err);
+        s->n_partials = bn::nd_ctas(s);
+    } else {
+        st = bn::build_work_list(s, &err);
+        if (st == BN_OK) {
+            s->n_partials = bn::triple_partials(s);
+            st = bn::balance_work_lists(s, &err);
+        }
     }
-    s->n_partials = bn::triple_partials(s);
-    st = bn::balance_work_lists(s, &err);
     if (st != BN_OK) {
-        free_buffers(s);   // the work lists (the other buffers are not allocated yet)
+        free_buffers(s);   // the work lists / operator plan (the other buffers are not allocated yet)
         bn::release_tables(s->tabs);
         if (s->own_stream) cudaStreamDestroy(s->stream);
         delete s;
@@ -304,7 +327,7 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     alloc((void**)&s->quad, n * sizeof(double2));
     alloc((void**)&s->red, n * sizeof(double2));
     alloc((void**)&s->q1q, n * sizeof(double2));
-    alloc((void**)&s->partials, (size_t)s->n_partials * n * sizeof(double2));
+    if (!nd) alloc((void**)&s->partials, (size_t)s->n_partials * n * sizeof(double2));
     alloc((void**)&s->Qhat, n * sizeof(double2));
     alloc((void**)&s->moments, 16 * sizeof(double));
     alloc((void**)&s->flags, 8 * sizeof(int));
@@ -319,8 +342,9 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     }
     cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream);
     cudaMemsetAsync(s->Qhat, 0, n * sizeof(double2), s->stream);
-    st = bn::tune_mixed2d(s, &err);
+    st = nd ? bn::prepare_nd(s) : bn::tune_mixed2d(s, &err);
     if (st != BN_OK) {
+        if (nd) err = "kernel-mode slice production failed";
         free_buffers(s);
         bn::release_tables(s->tabs);
         if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -484,9 +508,17 @@ bn_status bn_moments(bn_solver* s, double* out, size_t count) {
 bn_status bn_work_counts(const bn_solver* s, double* out, size_t count) {
     if (!valid_solver(s) || !out) return fail(BN_ERR_ARG, "null argument");
     if (count < 4) return fail(BN_ERR_ARG, "count must be >= 4");
-    out[0] = bn::count_pair_terms(s->g.d, s->g.N);
-    out[1] = s->eps != 0.0 ? bn::count_reducible_terms(s->g.d, s->g.N) : 0.0;
-    out[2] = s->eps != 0.0 ? bn::count_triple_terms(s->g.d, s->g.N) : 0.0;
+    if (s->opt.wrap) {
+        // CIRCULAR: every pair (x, y) and triple of I_N contributes
+        const double nm = (double)s->g.nModes;
+        out[0] = nm * nm;
+        out[1] = s->eps != 0.0 ? 2.0 * nm * nm : 0.0;
+        out[2] = s->eps != 0.0 ? nm * nm * nm : 0.0;
+    } else {
+        out[0] = bn::count_pair_terms(s->g.d, s->g.N);
+        out[1] = s->eps != 0.0 ? bn::count_reducible_terms(s->g.d, s->g.N) : 0.0;
+        out[2] = s->eps != 0.0 ? bn::count_triple_terms(s->g.d, s->g.N) : 0.0;
+    }
     out[3] = s->g.nModes;
     return BN_OK;
 }
@@ -561,7 +593,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
         if (!(dts[i] > 0) || !std::isfinite(dts[i])) return fail(BN_ERR_ARG, "dt must be > 0");
         for (int j = 0; j < i; ++j)
             if (solvers[j] == solvers[i]) return fail(BN_ERR_ARG, "a solver appears twice in the batch");
-        if (solvers[i]->g.d != 2 || solvers[i]->opt.integrator != solvers[0]->opt.integrator) shared = false;
+        if (solvers[i]->nd || solvers[i]->opt.integrator != solvers[0]->opt.integrator) shared = false;
     }
     if (nsteps == 0) return BN_OK;
     cudaStream_t st0 = solvers[0]->stream;

@@ -53,6 +53,12 @@ struct KernelTables {
     double* sw64 = nullptr;       // 2-D: [b (ext)][s in I_N] = beta(s,b-s) - beta(b,s) - beta(s,b) (0 off box_s(b))
     float* sw32 = nullptr;
     float* dq32 = nullptr;        // 2-D: [b in I_N][a (ext)] = beta(a, b) - beta(b, b), formed in FP64, rounded once
+    float* alpha32 = nullptr;     // FP32 copies of alpha64 / alphap64 ([P][nExt])
+    float* alphap32 = nullptr;
+    double* alphaI64 = nullptr;   // alpha, alpha' restricted to a in I_N ([P][N^d]), FP64 and FP32
+    double* alphapI64 = nullptr;
+    float* alphaI32 = nullptr;
+    float* alphapI32 = nullptr;
     size_t bytes = 0;
 };
 
@@ -176,6 +182,7 @@ __device__ __forceinline__ void sum_partials_f32_block(int nm, int nPart, const 
 }
 
 struct BatchPlan;
+struct NdPlan;
 
 // ---------------------------------------------------------------- triple-sum work list
 // Geometry of one b of the 2-D mixed kernel, derived once on the host (64 bytes).  The sweep runs
@@ -268,6 +275,7 @@ struct bn_solver {
     int device = 0;
     double scale = 1.0;          // (T/pi)^{d+gamma}
     bn::KernelTables* tabs = nullptr;
+    bn::NdPlan* nd = nullptr;    // 3-D and CIRCULAR operator path (bn_opnd.cu)
     bn::WorkList work;           // b with non-empty triple-sum boxes (eps != 0)
     bn::WorkList work_quad;      // b in I_N (quadratic part only, eps == 0)
     int n_partials = 0;          // CTAs of the triple-sum kernel (rows of the partial buffer)
@@ -347,10 +355,19 @@ void launch_conserve_on(const bn_solver* s, double* Q, cudaStream_t st);
 void dft2_forward_into(const bn_solver* s, cudaStream_t st, const double* f, double2* work, double2* out, float2* out32);
 void dft2_inverse_real_into(const bn_solver* s, cudaStream_t st, const double2* in, double2* work, double* out);
 
-// sums (bn_sums.cu)
-void launch_pair_sums(bn_solver* s);        // S2, quad, red from Ghat
-void launch_triple_sum(bn_solver* s);       // q1q from Ghat
-void launch_combine(bn_solver* s);          // Qhat = quad + eps (q1q + red)
+// 3-D and CIRCULAR operator (bn_opnd.cu)
+bool use_nd(const bn_solver* s);
+bn_status plan_nd(bn_solver* s, std::string* err);
+bn_status build_nd_tables(bn_solver* s, KernelTables* t, std::string* err);
+bn_status prepare_nd(bn_solver* s);
+void launch_nd(bn_solver* s, unsigned long long* stamps);
+void free_nd(bn_solver* s);
+double nd_triple_terms(const bn_solver* s);
+int nd_rounds(const bn_solver* s);
+int nd_ctas(const bn_solver* s);
+size_t nd_slice_bytes(const bn_solver* s);
+
+// CTAs of the 2-D fused operator launch (bn_sums.cu)
 int triple_partials(const bn_solver* s);
 
 // batched stepping of 2-D solvers (bn_batch.cu)

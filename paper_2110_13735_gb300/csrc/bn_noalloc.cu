@@ -74,8 +74,8 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
         bn::set_last_error("the current device is not the solver's device: make the solver's device current first");
         return BN_ERR_ARG;
     }
-    if (s->g.d != 2) {
-        bn::set_last_error("the no-allocation evaluation covers 2-D solvers only");
+    if (s->g.d != 2 || s->nd) {
+        bn::set_last_error("the no-allocation evaluation covers 2-D solvers with the LINEAR truncation only");
         return BN_ERR_UNSUPPORTED;
     }
     const size_t nm = (size_t)s->g.nModes;

@@ -1,0 +1,1354 @@
+// bn_opnd.cu -- the collision operator in 3-D (any N up to 48) and in the CIRCULAR truncation
+// (2-D and 3-D), with the kernel modes beta recomputed from the quadrature factors at every
+// evaluation (Mouton & Rey, Sec. 2.5, eq. betadD: beta(a,b) = sum_p alpha_p(a) alpha'_p(b)).
+//
+// The 2-D LINEAR operator has its own fused kernels (bn_fused2d*.cu) over a stored beta table.
+// In 3-D that table would hold (2N)^6 entries (6.9e10 at N = 32), so this path never forms it.
+// A 2-D problem is handled here as a 3-D one whose first axis is trivial (I = {0}).
+//
+// Factorisation (as in 2-D; b = l + m, s = l, every index sum reduced modulo N in CIRCULAR mode):
+//   Q^_n   = quad(n) + eps [Q1q(n) + red(n)]                         (Sec. 3.3 step 2(c), alpha = -eps)
+//   quad(n) = sum_{x+y=n} [beta(x,y) - beta(y,y)] G^_x G^_y          (Q_{1c} - Q_{2c})
+//   S(t)    = sum_{x+y=t} [beta(x,y) - beta(t,x) - beta(x,t)] G^_x G^_y,   red(n) = sum_k G^_k S(n-k)
+//                                                                     (Q_{2q} - Q_{3q} - Q_{4q})
+//   Q1q(n)  = sum_b G^_{n-b} C_b(n),  C_b(n) = sum_{s} beta(n-s, b) P_b(s),  P_b(s) = G^_s G^_{b-s}
+//                                                                     (Q_{1q}; Remark rem:computComplexity)
+// with the Lemma's index sets: n, x, y, s, b-s, n-b in I_N.  For each b the inner sum of Q1q is a
+// d-dimensional Toeplitz product of the kernel-mode slice beta(., b) with P_b.
+//
+// Kernels, per evaluation:
+//  * k_pair_nd: quad and S.  One CTA per row (t_0, t_1) of t = x + y; the weights of a tile of
+//    (x_2, y_2) pairs are summed over the quadrature nodes from the alpha tables (a small dense
+//    contraction per tile), multiplied by G^_x G^_y and reduced along the anti-diagonals in a fixed
+//    order.
+//  * k_beta_slices: the slices beta(a, b) for a in the box A(b) of the differences n - s.  The b
+//    whose boxes coincide in the first two axes (and nearly in the third) form groups of up to 64;
+//    a group's slices are one contraction over the nodes (rows: a in the union box, columns: the
+//    group's b), register-tiled 4 x 8 per thread, written to a slice buffer in global memory.
+//    The slices of a "round" (as many groups as fit the buffer) are produced, then consumed.
+//  * k_triple_nd: the Toeplitz products.  A work item is (b, T0 consecutive output planes n_0);
+//    the CTA walks the planes a_0 of the slice, staging each plane with one bulk (TMA) copy and the
+//    P_b planes it meets in shared memory, and each thread sweeps RW consecutive outputs along
+//    axis 2 with a register window of weights (paired FP32 FMA in mixed precision).  The s_1 range
+//    may be split over J lanes (reduced by shuffles) when an item has few output rows.  C_b(n)
+//    times G^_{n-b} is added to the CTA's own partial sums in global memory (FP32 Kahan pairs or
+//    FP64); items are dealt to CTAs on the host, so every sum has a fixed order.
+//  * k_sum_partials_nd, then k_red_combine_nd: Q1q from the partials, red(n), and Q^.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+namespace {
+
+constexpr int kMaxGroup = 64;     // b per producer group
+constexpr int kPA = 128;          // producer: a per CTA tile
+constexpr int kPK = 16;           // producer: nodes per staged chunk
+constexpr uint32_t kWaitNd = 1u << 22;   // polls of a bounded mbarrier wait
+
+// ------------------------------------------------------------------ geometry (host and device)
+// Axis x has n_x modes I_x = [lo_x, lo_x + n_x - 1] (n_x = 1: the trivial first axis of a 2-D
+// problem).  All per-b boxes follow from the index sets of the Lemma (LINEAR) or are the whole
+// I_x (CIRCULAR).
+struct NdGeo {
+    int d, N, wrap;
+    int n[3], lo[3];
+    int blo[3], nb[3];   // range of b per axis
+    int nbTotal;
+};
+
+__host__ __device__ inline int red_mod(int x, int lo, int n) {
+    int r = (x - lo) % n;
+    if (r < 0) r += n;
+    return r + lo;
+}
+
+struct Box3 { int nlo[3], L[3], slo[3], S[3], alo[3], A[3]; };
+
+__host__ __device__ inline void box_of(const NdGeo& g, const int* b, Box3& B) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const int lo = g.lo[x], hi = g.lo[x] + g.n[x] - 1;
+        if (g.wrap) {
+            B.nlo[x] = lo; B.L[x] = g.n[x];
+            B.slo[x] = lo; B.S[x] = g.n[x];
+        } else {
+            const int nlo = max(lo, b[x] + lo), nhi = min(hi, b[x] + hi);
+            const int slo = max(lo, b[x] - hi), shi = min(hi, b[x] - lo);
+            B.nlo[x] = nlo; B.L[x] = nhi - nlo + 1;
+            B.slo[x] = slo; B.S[x] = shi - slo + 1;
+        }
+        B.alo[x] = B.nlo[x] - (B.slo[x] + B.S[x] - 1);
+        B.A[x] = B.L[x] + B.S[x] - 1;
+    }
+}
+
+__host__ __device__ inline void b_of_flat(const NdGeo& g, int f, int* b) {
+    b[2] = f % g.nb[2] + g.blo[2];
+    f /= g.nb[2];
+    b[1] = f % g.nb[1] + g.blo[1];
+    b[0] = f / g.nb[1] + g.blo[0];
+}
+
+// row stride of a slice (elements): the axis-2 length rounded up so that rows start 16-byte aligned
+__host__ __device__ inline int slice_rs(int A2, int elem) { const int q = 16 / elem; return (A2 + q - 1) / q * q; }
+
+// flat index of a mode (or I_N-table entry) and of an extended-box alpha entry
+__host__ __device__ inline int mode_index(const NdGeo& g, int a0, int a1, int a2) {
+    return ((a0 - g.lo[0]) * g.n[1] + (a1 - g.lo[1])) * g.n[2] + (a2 - g.lo[2]);
+}
+__host__ __device__ inline int ext_index(const NdGeo& g, int a0, int a1, int a2) {
+    const int E = 2 * g.N;
+    const int e0 = g.d == 3 ? a0 + g.N : 0;
+    return (e0 * E + (a1 + g.N)) * E + (a2 + g.N);
+}
+// kernel-mode argument a (a difference n - s) as the alpha tables see it: reduced into I_N in
+// CIRCULAR mode
+__host__ __device__ inline int alpha_index(const NdGeo& g, int a0, int a1, int a2) {
+    if (g.wrap) {
+        a0 = red_mod(a0, g.lo[0], g.n[0]);
+        a1 = red_mod(a1, g.lo[1], g.n[1]);
+        a2 = red_mod(a2, g.lo[2], g.n[2]);
+    }
+    return ext_index(g, a0, a1, a2);
+}
+
+// ------------------------------------------------------------------ plan records
+struct NdGroup {
+    int ulo[3], uA[3];    // union box of the members' slice boxes (row-major order of a)
+    int first, nb;        // members: group_b[first .. first + nb)
+};
+
+struct NdItem {
+    uint32_t w0;          // b flat | (t0 index << 20) | (T0 << 26)
+    uint32_t off16;       // slice offset in 16-byte units from the slice buffer
+};
+
+template <typename Real> struct CT;
+template <> struct CT<float> { using C = float2; using P4 = float4; };
+template <> struct CT<double> { using C = double2; using P4 = double2; };
+
+// ------------------------------------------------------------------ producer: beta slices
+// CTA (group, tile): rows a = tile*kPA .. (the union box in row-major order), columns the group's
+// b; beta(a, b_j) = sum_p alpha_p(a) alpha'_p(b_j), thread (tx, ty) owns a = tx + 32 q (q < 4) and
+// j = 8 ty + r (r < 8); nodes staged kPK at a time.  Only a inside A(b_j) is stored.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_beta_slices(NdGeo g, int P, const Real* __restrict__ alpha,
+                                                     const Real* __restrict__ alphap, const NdGroup* __restrict__ groups,
+                                                     const int* __restrict__ group_b, const uint32_t* __restrict__ off16,
+                                                     const int2* __restrict__ work, Real* __restrict__ slices) {
+    __shared__ __align__(16) Real As[kPK][kPA];
+    __shared__ __align__(16) Real Bs[kPK][kMaxGroup];
+    const int2 wk = work[blockIdx.x];
+    const NdGroup G = groups[wk.x];
+    const int tile0 = wk.y * kPA;
+    const int uTot = G.uA[0] * G.uA[1] * G.uA[2];
+    const size_t nE = (size_t)(g.d == 3 ? 8 : 4) * g.N * g.N * (g.d == 3 ? g.N : 1);
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    // staging assignments: As element (k, c) for c = tid & 127, k = (tid >> 7) + 2 i; Bs (k, j) for
+    // j = tid & 63, k = (tid >> 6) + 4 i
+    const int ca = tid & (kPA - 1);
+    int ia_ext = -1;
+    {
+        const int u = tile0 + ca;
+        if (u < uTot) {
+            const int a2 = u % G.uA[2] + G.ulo[2], r = u / G.uA[2];
+            const int a1 = r % G.uA[1] + G.ulo[1], a0 = r / G.uA[1] + G.ulo[0];
+            ia_ext = alpha_index(g, a0, a1, a2);
+        }
+    }
+    const int cb = tid & (kMaxGroup - 1);
+    int ib_ext = -1;
+    if (cb < G.nb) {
+        int b[3];
+        b_of_flat(g, group_b[G.first + cb], b);
+        ib_ext = ext_index(g, b[0], b[1], b[2]);
+    }
+    Real acc[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[q][r] = 0;
+    for (int p0 = 0; p0 < P; p0 += kPK) {
+#pragma unroll
+        for (int i = 0; i < kPK / 2; ++i) {
+            const int k = (tid >> 7) + 2 * i, p = p0 + k;
+            As[k][ca] = (ia_ext >= 0 && p < P) ? alpha[(size_t)p * nE + ia_ext] : Real(0);
+        }
+#pragma unroll
+        for (int i = 0; i < kPK / 4; ++i) {
+            const int k = (tid >> 6) + 4 * i, p = p0 + k;
+            Bs[k][cb] = (ib_ext >= 0 && p < P) ? alphap[(size_t)p * nE + ib_ext] : Real(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kPK; ++k) {
+            Real av[4], bv[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[q] = As[k][tx + 32 * q];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) bv[r] = Bs[k][8 * ty + r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[q][r] = fma(av[q], bv[r], acc[q][r]);
+        }
+        __syncthreads();
+    }
+    // store the entries inside each member's own box
+    const int elem = (int)sizeof(Real);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int j = 8 * ty + r;
+        if (j >= G.nb) continue;
+        int b[3];
+        b_of_flat(g, group_b[G.first + j], b);
+        Box3 B;
+        box_of(g, b, B);
+        const int RS = slice_rs(B.A[2], elem);
+        Real* __restrict__ dst = slices + (size_t)off16[j + G.first] * (16 / elem);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = tile0 + tx + 32 * q;
+            if (u >= uTot) continue;
+            const int a2 = u % G.uA[2] + G.ulo[2], rr = u / G.uA[2];
+            const int a1 = rr % G.uA[1] + G.ulo[1], a0 = rr / G.uA[1] + G.ulo[0];
+            const int i0 = a0 - B.alo[0], i1 = a1 - B.alo[1], i2 = a2 - B.alo[2];
+            if (i0 < 0 || i0 >= B.A[0] || i1 < 0 || i1 >= B.A[1] || i2 < 0 || i2 >= B.A[2]) continue;
+            dst[((size_t)i0 * B.A[1] + i1) * RS + i2] = acc[q][r];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ consumer: Toeplitz sweeps
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void nd_bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// bulk (TMA engine) copy of `bytes` (multiple of 16, both ends 16-byte aligned) completing on bar
+__device__ __forceinline__ void nd_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool nd_bar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitNd; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// One row of the Toeplitz product in FP32: acc[r] += sum_{sl < S2} w[c0 + r - sl] P[sl], acc as
+// packed (re, im) pairs, the weights of the row in a rotating register window (slot of column x
+// is x mod RW), duplicated into pairs so that one paired FMA serves both halves of P.
+template <int RW>
+__device__ __forceinline__ void sweep_row_f32(const float* __restrict__ brow, int c0, const uint64_t* __restrict__ prow,
+                                              int S2, uint64_t (&acc)[RW]) {
+    uint64_t w[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) w[r] = dup2(brow[c0 + r]);
+    int sl = 0;
+    for (; sl + RW <= S2; sl += RW) {
+#pragma unroll
+        for (int kk = 0; kk < RW; ++kk) {
+            if (kk == 0) {
+                if (sl > 0) w[0] = dup2(brow[c0 - sl]);
+            } else {
+                w[RW - kk] = dup2(brow[c0 - sl - kk]);
+            }
+            const uint64_t p = prow[sl + kk];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < RW; ++kk) {
+        if (sl + kk >= S2) break;
+        if (kk == 0) {
+            if (sl > 0) w[0] = dup2(brow[c0 - sl]);
+        } else {
+            w[RW - kk] = dup2(brow[c0 - sl - kk]);
+        }
+        const uint64_t p = prow[sl + kk];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
+    }
+}
+
+// The same in FP64 (acc[r] = (re, im)).
+template <int RW>
+__device__ __forceinline__ void sweep_row_f64(const double* __restrict__ brow, int c0, const double2* __restrict__ prow,
+                                              int S2, double2 (&acc)[RW]) {
+    double w[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) w[r] = brow[c0 + r];
+    int sl = 0;
+    for (; sl + RW <= S2; sl += RW) {
+#pragma unroll
+        for (int kk = 0; kk < RW; ++kk) {
+            if (kk == 0) {
+                if (sl > 0) w[0] = brow[c0 - sl];
+            } else {
+                w[RW - kk] = brow[c0 - sl - kk];
+            }
+            const double2 p = prow[sl + kk];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const double ww = w[(r - kk + RW) % RW];
+                acc[r].x = fma(ww, p.x, acc[r].x);
+                acc[r].y = fma(ww, p.y, acc[r].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < RW; ++kk) {
+        if (sl + kk >= S2) break;
+        if (kk == 0) {
+            if (sl > 0) w[0] = brow[c0 - sl];
+        } else {
+            w[RW - kk] = brow[c0 - sl - kk];
+        }
+        const double2 p = prow[sl + kk];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const double ww = w[(r - kk + RW) % RW];
+            acc[r].x = fma(ww, p.x, acc[r].x);
+            acc[r].y = fma(ww, p.y, acc[r].y);
+        }
+    }
+}
+
+struct TripleNdArgs {
+    NdGeo g;
+    const void* G;            // modes (float2 or double2), N^d
+    const NdItem* items;      // per CTA: items[cta_off[c] .. cta_off[c+1])
+    const int* cta_off;
+    const void* slices;       // slice buffer (float or double)
+    void* partials;           // [gridDim.x][N^d]: float4 (sum, compensation) or double2
+    int* err;                 // [0] set when a bounded wait gives up
+    int PB;                   // elements per staged slice plane (max over items, + RW slack)
+    int PS;                   // P plane row stride (complex entries)
+    int PP;                   // complex entries per P plane
+    int T0max;
+    unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
+};
+
+__device__ __forceinline__ unsigned long long nd_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename Real>
+__device__ __forceinline__ typename CT<Real>::C load_mode(const TripleNdArgs& A, int m) {
+    return reinterpret_cast<const typename CT<Real>::C*>(A.G)[m];
+}
+
+// Shared memory: two slice-plane buffers, T0max + 1 P planes (a ring), one mbarrier per plane buffer.
+template <typename Real, int RW>
+__global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
+    using C = typename CT<Real>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* bufB = reinterpret_cast<Real*>(smem_raw);                       // [2][PB]
+    C* bufP = reinterpret_cast<C*>(bufB + 2 * (size_t)A.PB);             // [T0max + 1][PP]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bufP + (size_t)(A.T0max + 1) * A.PP);   // [2]
+    const NdGeo& g = A.g;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (A.stamps && tid == 0) atomicMin(A.stamps, nd_now());
+    if (tid == 0) {
+        nd_bar_init(&bar[0]);
+        nd_bar_init(&bar[1]);
+    }
+    __syncthreads();
+    uint32_t phases = 0u;   // bit i: parity of the next completion of bar[i]
+    const int it0 = A.cta_off[blockIdx.x], it1 = A.cta_off[blockIdx.x + 1];
+    const Real* slices = reinterpret_cast<const Real*>(A.slices);
+    for (int it = it0; it < it1; ++it) {
+        const NdItem item = A.items[it];
+        const int bflat = (int)(item.w0 & 0xFFFFFu);
+        const int t0i = (int)((item.w0 >> 20) & 63u), T0 = (int)(item.w0 >> 26);
+        int b[3];
+        b_of_flat(g, bflat, b);
+        Box3 B;
+        box_of(g, b, B);
+        const int RS = slice_rs(B.A[2], (int)sizeof(Real));
+        const Real* __restrict__ slice = slices + (size_t)item.off16 * (16 / sizeof(Real));
+        const int planeElems = B.A[1] * RS;
+        const int t0 = B.nlo[0] + t0i;
+        const int G2 = (B.L[2] + RW - 1) / RW;
+        const int tasks = T0 * B.L[1] * G2;
+        int J = 1;
+        while (J < 8 && tasks * 2 * J <= nthr && 2 * J <= B.S[1]) J *= 2;
+        const int task = tid / J, jj = tid % J;
+        const bool active = task < tasks;
+        const int g2 = task % G2, n1 = B.nlo[1] + (task / G2) % B.L[1], i0 = task / (G2 * B.L[1]);
+        const int n0 = t0 + i0;
+        const int ch = (B.S[1] + J - 1) / J;
+        const int s1a = B.slo[1] + jj * ch, s1b = min(B.slo[1] + B.S[1], s1a + ch);
+        const int n2 = B.nlo[2] + g2 * RW;
+        const int c0 = n2 - B.slo[2] - B.alo[2];
+        // planes a0 of the slice met by the outputs t0 .. t0 + T0 - 1
+        const int aHi = t0 + T0 - 1 - B.slo[0];
+        const int aLo = t0 - (B.slo[0] + B.S[0] - 1);
+        const int ringN = A.T0max + 1;
+        // accumulators
+        uint64_t acc32[RW];
+        double2 acc64[RW];
+        float ks[2 * RW], kc[2 * RW];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            acc32[r] = 0ull;
+            acc64[r] = make_double2(0.0, 0.0);
+            ks[2 * r] = ks[2 * r + 1] = 0.f;
+            kc[2 * r] = kc[2 * r + 1] = 0.f;
+        }
+        // P plane s0 into ring slot (s0 - slo0) mod ringN
+        auto build_P = [&](int s0) {
+            C* dst = bufP + (size_t)(((s0 - B.slo[0]) % ringN + ringN) % ringN) * A.PP;
+            const int tot = B.S[1] * B.S[2];
+            for (int q = tid; q < tot; q += nthr) {
+                const int r1 = q / B.S[2], r2 = q - r1 * B.S[2];
+                const int s1 = B.slo[1] + r1, s2 = B.slo[2] + r2;
+                int m0 = b[0] - s0, m1 = b[1] - s1, m2 = b[2] - s2;
+                if (g.wrap) {
+                    m0 = red_mod(m0, g.lo[0], g.n[0]);
+                    m1 = red_mod(m1, g.lo[1], g.n[1]);
+                    m2 = red_mod(m2, g.lo[2], g.n[2]);
+                }
+                dst[r1 * A.PS + r2] = cmul2(load_mode<Real>(A, mode_index(g, s0, s1, s2)),
+                                            load_mode<Real>(A, mode_index(g, m0, m1, m2)));
+            }
+        };
+        // previous item's readers are done with every buffer
+        __syncthreads();
+        if (tid == 0) {
+            nd_bulk_load(bufB, slice + (size_t)(aHi - B.alo[0]) * planeElems,
+                         (uint32_t)(planeElems * sizeof(Real)), &bar[0]);
+        }
+        // P planes needed at the first step: s0 = n0 - aHi for n0 in [t0, t0 + T0)
+        for (int s0 = max(B.slo[0], t0 - aHi); s0 <= min(B.slo[0] + B.S[0] - 1, t0 + T0 - 1 - aHi); ++s0) build_P(s0);
+        int slot = 0;
+        for (int a0 = aHi; a0 >= aLo; --a0) {
+            if (!nd_bar_wait(&bar[slot], (phases >> slot) & 1u)) {
+                if (tid == 0) atomicExch(A.err, 1);
+            }
+            phases ^= 1u << slot;
+            __syncthreads();   // the plane has landed and the P planes of this step are built
+            if (a0 > aLo) {
+                if (tid == 0)
+                    nd_bulk_load(bufB + (size_t)(slot ^ 1) * A.PB, slice + (size_t)(a0 - 1 - B.alo[0]) * planeElems,
+                                 (uint32_t)(planeElems * sizeof(Real)), &bar[slot ^ 1]);
+                const int sNew = t0 + T0 - 1 - (a0 - 1);   // the one P plane first needed at a0 - 1
+                if (sNew >= B.slo[0] && sNew < B.slo[0] + B.S[0]) build_P(sNew);
+            }
+            const int s0 = n0 - a0;
+            if (active && s0 >= B.slo[0] && s0 < B.slo[0] + B.S[0]) {
+                const Real* __restrict__ plane = bufB + (size_t)slot * A.PB;
+                const C* __restrict__ pplane = bufP + (size_t)(((s0 - B.slo[0]) % ringN + ringN) % ringN) * A.PP;
+                for (int s1 = s1a; s1 < s1b; ++s1) {
+                    const Real* brow = plane + (size_t)(n1 - s1 - B.alo[1]) * RS;
+                    const C* prow = pplane + (size_t)(s1 - B.slo[1]) * A.PS;
+                    if constexpr (sizeof(Real) == 4)
+                        sweep_row_f32<RW>(reinterpret_cast<const float*>(brow), c0,
+                                          reinterpret_cast<const uint64_t*>(prow), B.S[2], acc32);
+                    else
+                        sweep_row_f64<RW>(reinterpret_cast<const double*>(brow), c0,
+                                          reinterpret_cast<const double2*>(prow), B.S[2], acc64);
+                }
+                if constexpr (sizeof(Real) == 4) {
+                    // compensated accumulation of the plane's sums
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        float lo, hi;
+                        split2(acc32[r], lo, hi);
+                        kahan_add_f(ks[2 * r], kc[2 * r], lo);
+                        kahan_add_f(ks[2 * r + 1], kc[2 * r + 1], hi);
+                        acc32[r] = 0ull;
+                    }
+                }
+            }
+            __syncthreads();   // this plane buffer and the oldest P plane are free again
+            slot ^= 1;
+        }
+        // meet the J chunks of a task (lanes task*J .. task*J + J - 1 of one warp)
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            if constexpr (sizeof(Real) == 4) {
+                float x = ks[2 * r] - kc[2 * r], y = ks[2 * r + 1] - kc[2 * r + 1];
+                for (int o = 1; o < J; o <<= 1) {
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                    y += __shfl_xor_sync(0xffffffffu, y, o);
+                }
+                ks[2 * r] = x;
+                ks[2 * r + 1] = y;
+            } else {
+                double x = acc64[r].x, y = acc64[r].y;
+                for (int o = 1; o < J; o <<= 1) {
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                    y += __shfl_xor_sync(0xffffffffu, y, o);
+                }
+                acc64[r] = make_double2(x, y);
+            }
+        }
+        if (active && jj == 0) {
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int nn2 = n2 + r;
+                if (nn2 >= B.nlo[2] + B.L[2]) break;
+                int k0 = n0 - b[0], k1 = n1 - b[1], k2 = nn2 - b[2];
+                if (g.wrap) {
+                    k0 = red_mod(k0, g.lo[0], g.n[0]);
+                    k1 = red_mod(k1, g.lo[1], g.n[1]);
+                    k2 = red_mod(k2, g.lo[2], g.n[2]);
+                }
+                const C gk = load_mode<Real>(A, mode_index(g, k0, k1, k2));
+                const int on = mode_index(g, n0, n1, nn2);
+                const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
+                if constexpr (sizeof(Real) == 4) {
+                    const float2 c = make_float2(ks[2 * r], ks[2 * r + 1]);
+                    const float2 t = cmul2(gk, c);
+                    float4* pp = reinterpret_cast<float4*>(A.partials) + (size_t)blockIdx.x * nm + on;
+                    float4 v = *pp;
+                    kahan_add_f(v.x, v.z, t.x);
+                    kahan_add_f(v.y, v.w, t.y);
+                    *pp = v;
+                } else {
+                    const double2 t = cmul2(gk, acc64[r]);
+                    double2* pp = reinterpret_cast<double2*>(A.partials) + (size_t)blockIdx.x * nm + on;
+                    double2 v = *pp;
+                    v.x += t.x;
+                    v.y += t.y;
+                    *pp = v;
+                }
+            }
+        }
+    }
+    // drain: no bulk copy may still be in flight when the CTA exits (every issued copy was
+    // waited for above, since each issued plane is consumed by the next step)
+    __syncthreads();
+    if (A.stamps && tid == 0) atomicMax(A.stamps + 1, nd_now());
+}
+
+// ------------------------------------------------------------------ quadratic and reducible sums
+// CTA per t-row (t_0, t_1); TX x TX tiles of (x_2, y_2) per thread, pairs (x_0, x_1) processed
+// PPC at a time (one group of threads each).  wq = beta(x,y) - beta(y,y) = sum_p (alpha_p(x) -
+// alpha_p(y)) alpha'_p(y); wr = beta(x,y) - beta(t,x) - beta(x,t) = sum_p alpha_p(x) (alpha'_p(y) -
+// alpha'_p(t)) - alpha_p(t) alpha'_p(x).  Products with G^_x G^_y are reduced along the
+// anti-diagonals t_2 = x_2 + y_2 in a fixed order and accumulated in FP64.
+struct PairNdArgs {
+    NdGeo g;
+    int P;
+    const void* alphaI;    // [P][N^d] alpha on I_N
+    const void* alphapI;
+    const void* alphaE;    // [P][(2N)^d] extended-box tables (LINEAR t-rows)
+    const void* alphapE;
+    const void* G;         // modes (Real complex)
+    double2* quad;         // N^d
+    double2* S;            // t box: LINEAR (2n_x - 1) per axis, CIRCULAR I_N
+    int cubic;
+    int nt[3], tlo[3];     // t range per axis
+};
+
+template <typename Real, int TX>
+__global__ void __launch_bounds__(256) k_pair_nd(PairNdArgs A) {
+    using C = typename CT<Real>::C;
+    constexpr int KP = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const NdGeo& g = A.g;
+    const int n2 = g.n[2];
+    const int TN = (n2 + TX - 1) / TX;          // thread tiles per axis
+    const int tpp = TN * TN;                    // threads per pair
+    const int PPC = max(1, (int)blockDim.x / tpp);
+    const int nT2 = A.nt[2];
+    const int W = 2 * n2 - 1;                   // t-row entries (unwrapped x2 + y2)
+    // shared: rows [PPC][4][KP][n2], trow [2][KP][W], partial [PPC*tpp][2*TX-1] (2 complex each),
+    // accumulators quad/S [nT2] double2
+    Real* rows = reinterpret_cast<Real*>(smem_raw);
+    Real* trow = rows + (size_t)PPC * 4 * KP * n2;
+    C* part = reinterpret_cast<C*>(trow + 2 * KP * W);
+    double2* accQ = reinterpret_cast<double2*>(part + (size_t)PPC * tpp * (2 * TX - 1) * 2);
+    double2* accS = accQ + nT2;
+    const int t0 = A.tlo[0] + (int)blockIdx.x / A.nt[1], t1 = A.tlo[1] + (int)blockIdx.x % A.nt[1];
+    for (int i = threadIdx.x; i < nT2; i += blockDim.x) {
+        accQ[i] = make_double2(0.0, 0.0);
+        accS[i] = make_double2(0.0, 0.0);
+    }
+    // pairs (x0, x1): LINEAR x in box_s(t) per axis; CIRCULAR all of I
+    int xlo[2], xn[2];
+    for (int x = 0; x < 2; ++x) {
+        const int lo = g.lo[x], hi = g.lo[x] + g.n[x] - 1, t = x == 0 ? t0 : t1;
+        if (g.wrap) { xlo[x] = lo; xn[x] = g.n[x]; }
+        else { xlo[x] = max(lo, t - hi); xn[x] = min(hi, t - lo) - xlo[x] + 1; }
+    }
+    const int npairs = xn[0] * xn[1];
+    const int slotp = threadIdx.x / tpp, lt = threadIdx.x % tpp;
+    const int tx = lt % TN, ty = lt / TN;
+    const Real* aI = reinterpret_cast<const Real*>(A.alphaI);
+    const Real* apI = reinterpret_cast<const Real*>(A.alphapI);
+    const Real* aE = reinterpret_cast<const Real*>(A.alphaE);
+    const Real* apE = reinterpret_cast<const Real*>(A.alphapE);
+    const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t nE = (size_t)(g.d == 3 ? 8 : 4) * g.N * g.N * (g.d == 3 ? g.N : 1);
+    for (int pb = 0; pb < npairs; pb += PPC) {
+        // this thread's pair
+        const int pi = pb + slotp;
+        const bool pvalid = slotp < PPC && pi < npairs;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        if (pvalid) {
+            x0 = xlo[0] + pi / xn[1];
+            x1 = xlo[1] + pi % xn[1];
+            y0 = t0 - x0;
+            y1 = t1 - x1;
+            if (g.wrap) { y0 = red_mod(y0, g.lo[0], g.n[0]); y1 = red_mod(y1, g.lo[1], g.n[1]); }
+        }
+        Real wq[TX][TX], wr[TX][TX];
+#pragma unroll
+        for (int i = 0; i < TX; ++i)
+#pragma unroll
+            for (int j = 0; j < TX; ++j) { wq[i][j] = 0; wr[i][j] = 0; }
+        for (int p0 = 0; p0 < A.P; p0 += KP) {
+            __syncthreads();
+            // stage the x and y rows of the PPC pairs and the t row
+            for (int e = threadIdx.x; e < PPC * 4 * KP * n2; e += blockDim.x) {
+                const int c = e % n2, k = (e / n2) % KP, which = (e / (n2 * KP)) % 4, sp = e / (n2 * KP * 4);
+                const int pj = pb + sp, p = p0 + k;
+                Real v = 0;
+                if (pj < npairs && p < A.P) {
+                    const int xx0 = xlo[0] + pj / xn[1], xx1 = xlo[1] + pj % xn[1];
+                    int yy0 = t0 - xx0, yy1 = t1 - xx1;
+                    if (g.wrap) { yy0 = red_mod(yy0, g.lo[0], g.n[0]); yy1 = red_mod(yy1, g.lo[1], g.n[1]); }
+                    const bool isx = which < 2;
+                    const int m = isx ? mode_index(g, xx0, xx1, g.lo[2] + c) : mode_index(g, yy0, yy1, g.lo[2] + c);
+                    v = ((which & 1) ? apI : aI)[(size_t)p * nm + m];
+                }
+                rows[e] = v;
+            }
+            for (int e = threadIdx.x; e < 2 * KP * W; e += blockDim.x) {
+                const int c = e % W, k = (e / W) % KP, which = e / (W * KP);
+                const int p = p0 + k;
+                Real v = 0;
+                if (p < A.P && A.cubic) {
+                    int tt2 = 2 * g.lo[2] + c;   // unwrapped x2 + y2
+                    if (g.wrap) {
+                        tt2 = red_mod(tt2, g.lo[2], g.n[2]);
+                        v = (which ? apI : aI)[(size_t)p * nm + mode_index(g, t0, t1, tt2)];
+                    } else {
+                        v = (which ? apE : aE)[(size_t)p * nE + ext_index(g, t0, t1, tt2)];
+                    }
+                }
+                trow[e] = v;
+            }
+            __syncthreads();
+            if (pvalid) {
+                const Real* rb = rows + (size_t)slotp * 4 * KP * n2;
+#pragma unroll 2
+                for (int k = 0; k < KP; ++k) {
+                    Real ax[TX], apx[TX], ay[TX], apy[TX], at[2 * TX - 1], apt[2 * TX - 1];
+#pragma unroll
+                    for (int i = 0; i < TX; ++i) {
+                        const int cx = min(tx * TX + i, n2 - 1), cy = min(ty * TX + i, n2 - 1);
+                        ax[i] = rb[(0 * KP + k) * n2 + cx];
+                        apx[i] = rb[(1 * KP + k) * n2 + cx];
+                        ay[i] = rb[(2 * KP + k) * n2 + cy];
+                        apy[i] = rb[(3 * KP + k) * n2 + cy];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2 * TX - 1; ++i) {
+                        const int ct = min((tx + ty) * TX + i, W - 1);
+                        at[i] = trow[(0 * KP + k) * W + ct];
+                        apt[i] = trow[(1 * KP + k) * W + ct];
+                    }
+#pragma unroll
+                    for (int i = 0; i < TX; ++i)
+#pragma unroll
+                        for (int j = 0; j < TX; ++j) {
+                            wq[i][j] = fma(ax[i] - ay[j], apy[j], wq[i][j]);
+                            wr[i][j] = fma(ax[i], apy[j] - apt[i + j], fma(-at[i + j], apx[i], wr[i][j]));
+                        }
+                }
+            }
+        }
+        // products with G^_x G^_y, anti-diagonal partials of this thread
+        C* mypart = part + ((size_t)(slotp * tpp + lt)) * (2 * TX - 1) * 2;
+        if (slotp < PPC) {
+            C dq[2 * TX - 1], dr[2 * TX - 1];
+#pragma unroll
+            for (int i = 0; i < 2 * TX - 1; ++i) { dq[i].x = dq[i].y = 0; dr[i].x = dr[i].y = 0; }
+            if (pvalid) {
+                const C* Gm = reinterpret_cast<const C*>(A.G);
+#pragma unroll
+                for (int i = 0; i < TX; ++i) {
+                    const int x2 = g.lo[2] + tx * TX + i;
+                    if (x2 >= g.lo[2] + n2) break;
+                    const C gx = Gm[mode_index(g, x0, x1, x2)];
+#pragma unroll
+                    for (int j = 0; j < TX; ++j) {
+                        const int y2 = g.lo[2] + ty * TX + j;
+                        if (y2 >= g.lo[2] + n2) break;
+                        const C gxy = cmul2(gx, Gm[mode_index(g, y0, y1, y2)]);
+                        dq[i + j].x = fma(wq[i][j], gxy.x, dq[i + j].x);
+                        dq[i + j].y = fma(wq[i][j], gxy.y, dq[i + j].y);
+                        dr[i + j].x = fma(wr[i][j], gxy.x, dr[i + j].x);
+                        dr[i + j].y = fma(wr[i][j], gxy.y, dr[i + j].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2 * TX - 1; ++i) {
+                mypart[2 * i] = dq[i];
+                mypart[2 * i + 1] = dr[i];
+            }
+        }
+        __syncthreads();
+        // fixed-order reduction over the unwrapped index u = x2 + y2 - 2 lo2 (0 .. 2 n2 - 2): LINEAR
+        // t2 = 2 lo2 + u; CIRCULAR t2 = <2 lo2 + u>, i.e. u = (ti - lo2) mod n2 and that + n2
+        for (int ti = threadIdx.x; ti < nT2; ti += blockDim.x) {
+            double qx = 0, qy = 0, rx = 0, ry = 0;
+            const int ubase = g.wrap ? ((ti - g.lo[2]) % n2 + n2) % n2 : ti;
+            for (int sp = 0; sp < PPC; ++sp) {
+                if (pb + sp >= npairs) break;
+                for (int fold = 0; fold < (g.wrap ? 2 : 1); ++fold) {
+                    const int u = ubase + fold * n2;
+                    if (u > 2 * n2 - 2) continue;
+                    for (int txx = 0; txx < TN; ++txx)
+                        for (int dl = 0; dl < 2 * TX - 1; ++dl) {
+                            const int rem = u - dl - txx * TX;
+                            if (rem < 0 || rem % TX) continue;
+                            const int tyy = rem / TX;
+                            if (tyy >= TN) continue;
+                            const C* pp = part + ((size_t)(sp * tpp + tyy * TN + txx)) * (2 * TX - 1) * 2;
+                            qx += (double)pp[2 * dl].x;
+                            qy += (double)pp[2 * dl].y;
+                            rx += (double)pp[2 * dl + 1].x;
+                            ry += (double)pp[2 * dl + 1].y;
+                        }
+                }
+            }
+            accQ[ti].x += qx; accQ[ti].y += qy;
+            accS[ti].x += rx; accS[ti].y += ry;
+        }
+    }
+    __syncthreads();
+    // write the row: quad for t in I_N, S over the t box
+    const bool qrow = g.wrap || (t0 >= g.lo[0] && t0 < g.lo[0] + g.n[0] && t1 >= g.lo[1] && t1 < g.lo[1] + g.n[1]);
+    for (int ti = threadIdx.x; ti < nT2; ti += blockDim.x) {
+        const int t2 = A.tlo[2] + ti;
+        if (qrow && t2 >= g.lo[2] && t2 < g.lo[2] + n2) A.quad[mode_index(g, t0, t1, t2)] = accQ[ti];
+        if (A.cubic) A.S[((size_t)blockIdx.x) * nT2 + ti] = accS[ti];
+    }
+}
+
+// ------------------------------------------------------------------ partial sums and combination
+template <typename Real>
+__global__ void k_sum_partials_nd(int nm, int nPart, const void* __restrict__ partials, double2* __restrict__ q1q) {
+    if constexpr (sizeof(Real) == 4) {
+        sum_partials_f32_block(nm, nPart, reinterpret_cast<const float4*>(partials), q1q, blockIdx.x);
+    } else {
+        const double2* pp = reinterpret_cast<const double2*>(partials);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+            double x = 0, y = 0;
+            for (int c = 0; c < nPart; ++c) {
+                const double2 v = pp[(size_t)c * nm + i];
+                x += v.x;
+                y += v.y;
+            }
+            q1q[i] = make_double2(x, y);
+        }
+    }
+}
+
+// Q^(n) = quad(n) + eps (q1q(n) + red(n)), red(n) = sum_{k in I_N} G^_k S(n - k): CTA per output
+// row (n0, n1); warp w takes the k rows (k0, k1) with index = w mod warps, lane the outputs n2.
+__global__ void __launch_bounds__(256) k_red_combine_nd(NdGeo g, double eps, int cubic, const double2* __restrict__ G,
+                                                        const double2* __restrict__ quad, const double2* __restrict__ q1q,
+                                                        const double2* __restrict__ S, int nt0, int nt1, int nt2, int tlo0,
+                                                        int tlo1, int tlo2, double2* __restrict__ Qhat) {
+    __shared__ double2 red[8][64];
+    const int n0 = g.lo[0] + (int)blockIdx.x / g.n[1], n1 = g.lo[1] + (int)blockIdx.x % g.n[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n2c = g.n[2];
+    double2 acc[2] = {make_double2(0, 0), make_double2(0, 0)};
+    if (cubic) {
+        const int nrows = g.n[0] * g.n[1];
+        for (int kr = warp; kr < nrows; kr += nw) {
+            const int k0 = g.lo[0] + kr / g.n[1], k1 = g.lo[1] + kr % g.n[1];
+            int u0 = n0 - k0, u1 = n1 - k1;
+            if (g.wrap) { u0 = red_mod(u0, g.lo[0], g.n[0]); u1 = red_mod(u1, g.lo[1], g.n[1]); }
+            const int r0 = u0 - tlo0, r1 = u1 - tlo1;
+            if (!g.wrap && (r0 < 0 || r1 < 0 || r0 >= nt0 || r1 >= nt1)) continue;
+            const double2* Srow = S + ((size_t)r0 * nt1 + r1) * nt2;
+            const double2* Grow = G + (size_t)mode_index(g, k0, k1, g.lo[2]);
+            for (int k2i = 0; k2i < n2c; ++k2i) {
+                const double2 gk = Grow[k2i];
+                const int k2 = g.lo[2] + k2i;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int n2i = lane + 32 * h;
+                    if (n2i >= n2c) break;
+                    int u2 = g.lo[2] + n2i - k2;
+                    if (g.wrap) u2 = red_mod(u2, g.lo[2], g.n[2]);
+                    const int r2 = u2 - tlo2;
+                    if (r2 < 0 || r2 >= nt2) continue;
+                    const double2 sv = Srow[r2];
+                    acc[h].x = fma(gk.x, sv.x, fma(-gk.y, sv.y, acc[h].x));
+                    acc[h].y = fma(gk.x, sv.y, fma(gk.y, sv.x, acc[h].y));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (lane + 32 * h < 64) red[warp][lane + 32 * h] = acc[h];
+    __syncthreads();
+    for (int n2i = threadIdx.x; n2i < n2c; n2i += blockDim.x) {
+        double rx = 0, ry = 0;
+        for (int w = 0; w < nw; ++w) { rx += red[w][n2i].x; ry += red[w][n2i].y; }
+        const int m = mode_index(g, n0, n1, g.lo[2] + n2i);
+        double2 q = quad[m];
+        if (cubic) {
+            q.x += eps * (q1q[m].x + rx);
+            q.y += eps * (q1q[m].y + ry);
+        }
+        Qhat[m] = q;
+    }
+}
+
+// I_N restriction of an extended-box alpha table and FP32 copies
+template <typename Real>
+__global__ void k_alpha_restrict(NdGeo g, int P, const double* __restrict__ src, Real* __restrict__ dst) {
+    const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t nE = (size_t)(g.d == 3 ? 8 : 4) * g.N * g.N * (g.d == 3 ? g.N : 1);
+    const size_t tot = (size_t)P * nm;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / nm), m = (int)(i % nm);
+        const int a2 = m % g.n[2] + g.lo[2], r = m / g.n[2];
+        const int a1 = r % g.n[1] + g.lo[1], a0 = r / g.n[1] + g.lo[0];
+        dst[i] = (Real)src[(size_t)p * nE + ext_index(g, a0, a1, a2)];
+    }
+}
+__global__ void k_to_f32(size_t n, const double* __restrict__ src, float* __restrict__ dst) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host plan
+struct NdRound {
+    size_t slice_bytes = 0;
+    int ngroups = 0, nwork = 0, nitems = 0;
+    NdGroup* d_groups = nullptr;
+    int* d_group_b = nullptr;
+    uint32_t* d_off16 = nullptr;     // per group member (same order as group_b)
+    int2* d_work = nullptr;
+    NdItem* d_items = nullptr;
+    int* d_cta_off = nullptr;
+};
+
+struct NdPlan {
+    NdGeo g{};
+    int RW = 8, threads = 256, T0 = 1, nCTA = 0;
+    int PB = 0, PS = 0, PP = 0;
+    size_t smem = 0, smem_pair = 0;
+    int TXp = 4;
+    int pair_threads = 256;
+    int nt[3] = {1, 1, 1}, tlo[3] = {0, 0, 0};
+    std::vector<NdRound> rounds;
+    size_t slice_cap = 0;             // bytes of the slice buffer
+    void* slices = nullptr;
+    void* partials = nullptr;
+    size_t partial_bytes = 0;
+    double2* quad = nullptr;
+    double2* S = nullptr;
+    double2* q1q = nullptr;
+    bool resident = false;            // slices produced once and kept (single round)
+    bool produced = false;
+    double terms = 0;                 // Q_{1,q} terms per evaluation
+};
+
+namespace {
+
+NdGeo make_geo(const bn_solver* s) {
+    NdGeo g{};
+    g.d = s->g.d;
+    g.N = s->g.N;
+    g.wrap = s->opt.wrap ? 1 : 0;
+    for (int x = 0; x < 3; ++x) {
+        const bool trivial = g.d == 2 && x == 0;
+        g.n[x] = trivial ? 1 : g.N;
+        g.lo[x] = trivial ? 0 : -g.N / 2;
+        const int lo = g.lo[x], hi = lo + g.n[x] - 1;
+        if (g.wrap) { g.blo[x] = lo; g.nb[x] = g.n[x]; }
+        else {
+            const int bl = std::max(2 * lo, lo - hi), bh = std::min(2 * hi, hi - lo);
+            g.blo[x] = bl;
+            g.nb[x] = bh - bl + 1;
+        }
+    }
+    g.nbTotal = g.nb[0] * g.nb[1] * g.nb[2];
+    return g;
+}
+
+// c-class of b per axis (LINEAR): boxes A(b) of equal c coincide: c = max(b + 1, -b) (b_x in the
+// non-trivial axes); 0 on a trivial axis.
+int cls(const NdGeo& g, int x, int b) {
+    if (g.n[x] == 1) return 0;
+    return std::max(b + 1, -b);
+}
+
+template <typename T>
+bn_status upload(T** dst, const std::vector<T>& v, std::string* err) {
+    if (v.empty()) { *dst = nullptr; return BN_OK; }
+    if (cudaMalloc(dst, sizeof(T) * v.size()) != cudaSuccess ||
+        cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        *err = "operator plan upload failed";
+        return BN_ERR_NOMEM;
+    }
+    return BN_OK;
+}
+
+}  // namespace
+
+bool use_nd(const bn_solver* s) { return s->g.d == 3 || s->opt.wrap != 0; }
+
+size_t nd_estimate_bytes(const bn_solver* s) { return s->nd ? s->nd->slice_cap + s->nd->partial_bytes : 0; }
+
+void free_nd(bn_solver* s) {
+    NdPlan* p = s->nd;
+    if (!p) return;
+    for (NdRound& r : p->rounds) {
+        cudaFree(r.d_groups); cudaFree(r.d_group_b); cudaFree(r.d_off16); cudaFree(r.d_work);
+        cudaFree(r.d_items); cudaFree(r.d_cta_off);
+    }
+    cudaFree(p->slices);
+    cudaFree(p->partials);
+    cudaFree(p->quad);
+    cudaFree(p->S);
+    cudaFree(p->q1q);
+    delete p;
+    s->nd = nullptr;
+}
+
+template <typename Real, int RW>
+static void configure_triple_nd(size_t smem) {
+    cudaFuncSetAttribute(k_triple_nd<Real, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template <typename Real, int TX>
+static void configure_pair_nd(size_t smem) {
+    cudaFuncSetAttribute(k_pair_nd<Real, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+bn_status plan_nd(bn_solver* s, std::string* err) {
+    NdPlan* p = new NdPlan();
+    s->nd = p;
+    NdGeo& g = p->g;
+    g = make_geo(s);
+    const bool fp32 = s->opt.precision == BN_MIXED;
+    const int elem = fp32 ? 4 : 8;
+    const int N = g.N;
+    // outputs per thread along axis 2: 8 (FP32), 4 (FP64; 8 when one plane would need more than
+    // 512 threads)
+    p->RW = fp32 ? 8 : (g.n[1] * ((g.n[2] + 3) / 4) > 512 ? 8 : 4);
+    const int RW = p->RW;
+    // outputs per CTA: T0 planes of L1 x ceil(L2/RW) tasks, up to 256 threads (more when one plane
+    // alone needs more: N = 48 has 48 x 6 tasks per plane)
+    const int perPlane = g.n[1] * ((g.n[2] + RW - 1) / RW);
+    p->T0 = std::max(1, std::min(g.n[0], 256 / perPlane));
+    p->threads = std::max(64, (p->T0 * perPlane + 31) / 32 * 32);
+    if (p->threads > 512) {
+        *err = "operator size beyond the 3-D kernel's thread limit";
+        return BN_ERR_UNSUPPORTED;
+    }
+    // largest slice plane and P plane
+    int maxA1 = 1, maxRS = 1, maxS1 = 1, maxS2 = 1;
+    for (int x = 1; x < 3; ++x) {
+        const int Amax = g.wrap ? 2 * g.n[x] - 1 : (g.n[x] == 1 ? 1 : 2 * N - 2);
+        const int Smax = g.n[x];   // box_s(b) spans all of I_x at b = -1 (LINEAR) and always (CIRCULAR)
+        if (x == 1) { maxA1 = Amax; maxS1 = Smax; }
+        else { maxRS = slice_rs(Amax, elem); maxS2 = Smax; }
+    }
+    p->PB = maxA1 * maxRS + RW;
+    p->PS = maxS2;
+    p->PP = maxS1 * maxS2;
+    const size_t Csz = 2 * (size_t)elem;
+    p->smem = 2 * (size_t)p->PB * elem + (size_t)(p->T0 + 1) * p->PP * Csz + 16;
+    p->smem = (p->smem + 15) / 16 * 16 + 16;
+    if (p->smem > 227 * 1024) {
+        *err = "the 3-D kernel's staging does not fit in shared memory";
+        return BN_ERR_UNSUPPORTED;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (sms <= 0) sms = 152;
+    int per_sm = 0;
+    if (fp32) {
+        configure_triple_nd<float, 8>(p->smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<float, 8>, p->threads, p->smem);
+    } else if (RW == 4) {
+        configure_triple_nd<double, 4>(p->smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double, 4>, p->threads, p->smem);
+    } else {
+        configure_triple_nd<double, 8>(p->smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double, 8>, p->threads, p->smem);
+    }
+    cudaGetLastError();
+    per_sm = std::max(1, per_sm);
+    p->nCTA = per_sm * sms;
+
+    // b list and groups
+    std::vector<std::vector<int>> members;
+    std::vector<NdGroup> groups;
+    {
+        std::vector<std::pair<long long, int>> keyed;
+        keyed.reserve(g.nbTotal);
+        const int W2 = g.d == 3 ? 8 : 16;   // c_2 band width: 2 x 2 x 2 x 8 = 64 b per group in 3-D
+        for (int f = 0; f < g.nbTotal; ++f) {
+            int b[3];
+            b_of_flat(g, f, b);
+            long long key;
+            if (g.wrap) key = f / kMaxGroup;
+            else key = ((long long)cls(g, 0, b[0]) * 4096 + cls(g, 1, b[1])) * 4096 + (cls(g, 2, b[2]) - 1) / W2;
+            keyed.push_back({key, f});
+        }
+        std::stable_sort(keyed.begin(), keyed.end());
+        size_t i = 0;
+        while (i < keyed.size()) {
+            size_t j = i;
+            std::vector<int> mem;
+            while (j < keyed.size() && keyed[j].first == keyed[i].first && mem.size() < (size_t)kMaxGroup) {
+                mem.push_back(keyed[j].second);
+                ++j;
+            }
+            NdGroup G{};
+            int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+            for (int f : mem) {
+                int b[3];
+                b_of_flat(g, f, b);
+                Box3 B;
+                box_of(g, b, B);
+                for (int x = 0; x < 3; ++x) {
+                    lo[x] = std::min(lo[x], B.alo[x]);
+                    hi[x] = std::max(hi[x], B.alo[x] + B.A[x] - 1);
+                }
+            }
+            for (int x = 0; x < 3; ++x) { G.ulo[x] = lo[x]; G.uA[x] = hi[x] - lo[x] + 1; }
+            G.nb = (int)mem.size();
+            groups.push_back(G);
+            members.push_back(mem);
+            i = j;
+        }
+    }
+    // slice bytes per b
+    auto slice_bytes = [&](int f) {
+        int b[3];
+        b_of_flat(g, f, b);
+        Box3 B;
+        box_of(g, b, B);
+        return (size_t)B.A[0] * B.A[1] * slice_rs(B.A[2], elem) * elem;
+    };
+    size_t total = 0;
+    for (auto& mem : members)
+        for (int f : mem) total += (slice_bytes(f) + 15) / 16 * 16;
+    // slice buffer: everything when it fits the budget (then produced once if resident), else rounds
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    cudaGetLastError();
+    size_t budget = s->opt.beta_budget_mb > 0 ? (size_t)s->opt.beta_budget_mb << 20
+                                              : std::min<size_t>((size_t)(0.4 * (double)freeb), (size_t)40 << 30);
+    budget = std::max<size_t>(budget, (size_t)64 << 20);
+    // every group must fit on its own
+    size_t maxGroup = 0;
+    for (auto& mem : members) {
+        size_t gb = 0;
+        for (int f : mem) gb += (slice_bytes(f) + 15) / 16 * 16;
+        maxGroup = std::max(maxGroup, gb);
+    }
+    budget = std::max(budget, maxGroup);
+    // rounds: groups in order, largest groups first
+    std::vector<int> gorder(groups.size());
+    std::iota(gorder.begin(), gorder.end(), 0);
+    {
+        std::vector<size_t> gbytes(groups.size(), 0);
+        for (size_t k = 0; k < groups.size(); ++k)
+            for (int f : members[k]) gbytes[k] += (slice_bytes(f) + 15) / 16 * 16;
+        std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int c) { return gbytes[a] > gbytes[c]; });
+        std::vector<std::vector<int>> rgroups(1);
+        size_t used = 0;
+        for (int k : gorder) {
+            if (used + gbytes[k] > budget && !rgroups.back().empty()) {
+                rgroups.emplace_back();
+                used = 0;
+            }
+            rgroups.back().push_back(k);
+            used += gbytes[k];
+        }
+        p->slice_cap = 0;
+        for (auto& rg : rgroups) {
+            size_t u = 0;
+            for (int k : rg) u += gbytes[k];
+            p->slice_cap = std::max(p->slice_cap, u);
+        }
+        p->resident = rgroups.size() == 1 && s->opt.beta_resident != 0;
+        // per round: groups, members with offsets, producer work, items dealt to CTAs
+        const int T0 = p->T0;
+        for (auto& rg : rgroups) {
+            NdRound R;
+            std::vector<NdGroup> rgs;
+            std::vector<int> gb;
+            std::vector<uint32_t> off;
+            std::vector<int2> work;
+            struct It { long long cost; NdItem it; };
+            std::vector<It> items;
+            size_t cur = 0;
+            for (int k : rg) {
+                NdGroup G = groups[k];
+                G.first = (int)gb.size();
+                const int gi = (int)rgs.size();
+                for (int f : members[k]) {
+                    gb.push_back(f);
+                    off.push_back((uint32_t)(cur / 16));
+                    int b[3];
+                    b_of_flat(g, f, b);
+                    Box3 B;
+                    box_of(g, b, B);
+                    for (int t = 0; t < B.L[0]; t += T0) {
+                        const int tn = std::min(T0, B.L[0] - t);
+                        NdItem it;
+                        it.w0 = (uint32_t)f | ((uint32_t)t << 20) | ((uint32_t)tn << 26);
+                        it.off16 = (uint32_t)(cur / 16);
+                        const long long terms = (long long)tn * B.L[1] * B.L[2] * B.S[0] * B.S[1] * B.S[2];
+                        const long long cost = terms + 2000LL * (tn + B.S[0]) + 20000;
+                        items.push_back({cost, it});
+                        p->terms += (double)terms;
+                    }
+                    cur += (slice_bytes(f) + 15) / 16 * 16;
+                }
+                const int uTot = G.uA[0] * G.uA[1] * G.uA[2];
+                for (int t = 0; t * kPA < uTot; ++t) work.push_back(make_int2(gi, t));
+                rgs.push_back(G);
+            }
+            // deal items: by cost descending, snake order over the CTAs
+            std::stable_sort(items.begin(), items.end(), [](const It& a, const It& c) { return a.cost > c.cost; });
+            std::vector<std::vector<NdItem>> per(p->nCTA);
+            std::vector<long long> load(p->nCTA, 0);
+            for (size_t q = 0; q < items.size(); ++q) {
+                const size_t rr = q / p->nCTA, c = q % p->nCTA;
+                const size_t cta = (rr & 1) ? p->nCTA - 1 - c : c;
+                per[cta].push_back(items[q].it);
+                load[cta] += items[q].cost;
+            }
+            std::vector<NdItem> flat;
+            std::vector<int> ctaoff(p->nCTA + 1, 0);
+            for (int c = 0; c < p->nCTA; ++c) {
+                ctaoff[c] = (int)flat.size();
+                flat.insert(flat.end(), per[c].begin(), per[c].end());
+            }
+            ctaoff[p->nCTA] = (int)flat.size();
+            R.slice_bytes = cur;
+            R.ngroups = (int)rgs.size();
+            R.nwork = (int)work.size();
+            R.nitems = (int)flat.size();
+            bn_status st = upload(&R.d_groups, rgs, err);
+            if (st == BN_OK) st = upload(&R.d_group_b, gb, err);
+            if (st == BN_OK) st = upload(&R.d_off16, off, err);
+            if (st == BN_OK) st = upload(&R.d_work, work, err);
+            if (st == BN_OK) st = upload(&R.d_items, flat, err);
+            if (st == BN_OK) st = upload(&R.d_cta_off, ctaoff, err);
+            p->rounds.push_back(R);
+            if (st != BN_OK) return st;
+        }
+    }
+    if (s->eps == 0.0) p->terms = 0;
+    // quadratic and reducible sums
+    for (int x = 0; x < 3; ++x) {
+        if (g.wrap) { p->nt[x] = g.n[x]; p->tlo[x] = g.lo[x]; }
+        else { p->nt[x] = 2 * g.n[x] - 1; p->tlo[x] = 2 * g.lo[x]; }
+    }
+    p->TXp = g.n[2] > 32 && fp32 ? 6 : 4;
+    {
+        const int TN = (g.n[2] + p->TXp - 1) / p->TXp, tpp = TN * TN;
+        if (tpp > 256) {
+            *err = "operator size beyond the pair kernel's thread limit";
+            return BN_ERR_UNSUPPORTED;
+        }
+        // pairs per CTA: enough threads to fill 256, at most 8 pairs
+        const int PPC = std::max(1, std::min(256 / tpp, 8));
+        p->pair_threads = PPC * tpp;
+        const int W = 2 * g.n[2] - 1;
+        p->smem_pair = (size_t)PPC * 4 * 8 * g.n[2] * elem + 2 * 8 * (size_t)W * elem +
+                       (size_t)PPC * tpp * (2 * p->TXp - 1) * 2 * Csz + 2 * (size_t)p->nt[2] * sizeof(double2) + 64;
+        if (fp32) {
+            if (p->TXp == 4) configure_pair_nd<float, 4>(p->smem_pair);
+            else configure_pair_nd<float, 6>(p->smem_pair);
+        } else {
+            configure_pair_nd<double, 4>(p->smem_pair);
+        }
+    }
+    const size_t nm = (size_t)s->g.nModes;
+    const size_t nS = (size_t)p->nt[0] * p->nt[1] * p->nt[2];
+    p->partial_bytes = (size_t)p->nCTA * nm * 16;
+    cudaError_t e = cudaMalloc(&p->slices, std::max<size_t>(p->slice_cap, 16) + 64);
+    if (e == cudaSuccess) e = cudaMalloc(&p->partials, p->partial_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->quad, nm * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->S, std::max<size_t>(nS, 1) * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->q1q, nm * sizeof(double2));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("3-D operator buffers: ") + cudaGetErrorString(e);
+        return BN_ERR_NOMEM;
+    }
+    cudaMemsetAsync(p->S, 0, std::max<size_t>(nS, 1) * sizeof(double2), s->stream);
+    cudaMemsetAsync(p->q1q, 0, nm * sizeof(double2), s->stream);
+    return BN_OK;
+}
+
+// Build the FP32 copies and the I_N restrictions of the alpha tables (once per table set).
+bn_status build_nd_tables(bn_solver* s, KernelTables* t, std::string* err) {
+    NdGeo g = make_geo(s);
+    g.wrap = 0;
+    const size_t nE = (size_t)s->g.nExt, nm = (size_t)s->g.nModes, P = (size_t)t->P;
+    cudaError_t e = cudaMalloc(&t->alpha32, sizeof(float) * P * nE);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphap32, sizeof(float) * P * nE);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphaI64, sizeof(double) * P * nm);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphapI64, sizeof(double) * P * nm);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphaI32, sizeof(float) * P * nm);
+    if (e == cudaSuccess) e = cudaMalloc(&t->alphapI32, sizeof(float) * P * nm);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("alpha table copies: ") + cudaGetErrorString(e);
+        return BN_ERR_NOMEM;
+    }
+    t->bytes += (sizeof(float) * 2) * P * nE + (sizeof(double) + sizeof(float)) * 2 * P * nm;
+    k_to_f32<<<2048, 256, 0, s->stream>>>(P * nE, t->alpha64, t->alpha32);
+    k_to_f32<<<2048, 256, 0, s->stream>>>(P * nE, t->alphap64, t->alphap32);
+    k_alpha_restrict<double><<<1024, 256, 0, s->stream>>>(g, (int)P, t->alpha64, t->alphaI64);
+    k_alpha_restrict<double><<<1024, 256, 0, s->stream>>>(g, (int)P, t->alphap64, t->alphapI64);
+    k_alpha_restrict<float><<<1024, 256, 0, s->stream>>>(g, (int)P, t->alpha64, t->alphaI32);
+    k_alpha_restrict<float><<<1024, 256, 0, s->stream>>>(g, (int)P, t->alphap64, t->alphapI32);
+    s->launches += 6;
+    return BN_OK;
+}
+
+// The whole operator from s->Ghat (and s->Ghat32) into s->Qhat.
+template <typename Real, int RW>
+static void launch_nd_t(bn_solver* s, cudaStream_t st, unsigned long long* stamps) {
+    NdPlan* p = s->nd;
+    const NdGeo& g = p->g;
+    const KernelTables* t = s->tabs;
+    const size_t nm = (size_t)s->g.nModes;
+    const bool fp32 = sizeof(Real) == 4;
+    const void* G = fp32 ? (const void*)s->Ghat32 : (const void*)s->Ghat;
+    const int cubic = s->eps != 0.0;
+    // quadratic and reducible sums
+    PairNdArgs PA;
+    PA.g = g;
+    PA.P = t->P;
+    PA.alphaI = fp32 ? (const void*)t->alphaI32 : (const void*)t->alphaI64;
+    PA.alphapI = fp32 ? (const void*)t->alphapI32 : (const void*)t->alphapI64;
+    PA.alphaE = fp32 ? (const void*)t->alpha32 : (const void*)t->alpha64;
+    PA.alphapE = fp32 ? (const void*)t->alphap32 : (const void*)t->alphap64;
+    PA.G = G;
+    PA.quad = p->quad;
+    PA.S = p->S;
+    PA.cubic = cubic;
+    for (int x = 0; x < 3; ++x) { PA.nt[x] = p->nt[x]; PA.tlo[x] = p->tlo[x]; }
+    // LINEAR without the cubic part needs only the t rows inside I_N, but the kernel is cheap
+    const int nrows = p->nt[0] * p->nt[1];
+    const int pthreads = p->pair_threads;
+    if constexpr (sizeof(Real) == 4) {
+        if (p->TXp == 6) k_pair_nd<Real, 6><<<nrows, pthreads, p->smem_pair, st>>>(PA);
+        else k_pair_nd<Real, 4><<<nrows, pthreads, p->smem_pair, st>>>(PA);
+    } else {
+        k_pair_nd<Real, 4><<<nrows, pthreads, p->smem_pair, st>>>(PA);
+    }
+    s->launches++;
+    if (cubic) {
+        cudaMemsetAsync(p->partials, 0, p->partial_bytes, st);
+        for (const NdRound& R : p->rounds) {
+            if (!(p->resident && p->produced)) {
+                k_beta_slices<Real><<<R.nwork, 256, 0, st>>>(g, t->P, fp32 ? (const Real*)t->alpha32 : (const Real*)t->alpha64,
+                                                             fp32 ? (const Real*)t->alphap32 : (const Real*)t->alphap64,
+                                                             R.d_groups, R.d_group_b, R.d_off16, R.d_work, (Real*)p->slices);
+                s->launches++;
+            }
+            TripleNdArgs TA;
+            TA.g = g;
+            TA.G = G;
+            TA.items = R.d_items;
+            TA.cta_off = R.d_cta_off;
+            TA.slices = p->slices;
+            TA.partials = p->partials;
+            TA.err = s->flags + 2;
+            TA.PB = p->PB;
+            TA.PS = p->PS;
+            TA.PP = p->PP;
+            TA.T0max = p->T0;
+            TA.stamps = stamps;
+            k_triple_nd<Real, RW><<<p->nCTA, p->threads, p->smem, st>>>(TA);
+            s->launches++;
+        }
+        if (p->resident) p->produced = true;
+        if (fp32) k_sum_partials_nd<float><<<(int)((nm + kPartModes - 1) / kPartModes), 256, 0, st>>>((int)nm, p->nCTA, p->partials, p->q1q);
+        else k_sum_partials_nd<double><<<(int)std::min<size_t>((nm + 255) / 256, 4096), 256, 0, st>>>((int)nm, p->nCTA, p->partials, p->q1q);
+        s->launches++;
+    }
+    k_red_combine_nd<<<g.n[0] * g.n[1], 256, 0, st>>>(g, s->eps, cubic, s->Ghat, p->quad, p->q1q, p->S, p->nt[0], p->nt[1],
+                                                       p->nt[2], p->tlo[0], p->tlo[1], p->tlo[2], s->Qhat);
+    s->launches++;
+}
+
+void launch_nd(bn_solver* s, unsigned long long* stamps) {
+    if (s->opt.precision == BN_MIXED) launch_nd_t<float, 8>(s, s->stream, stamps);
+    else if (s->nd->RW == 4) launch_nd_t<double, 4>(s, s->stream, stamps);
+    else launch_nd_t<double, 8>(s, s->stream, stamps);
+}
+
+// Produce the slices once (resident mode), outside any capture.
+bn_status prepare_nd(bn_solver* s) {
+    NdPlan* p = s->nd;
+    if (!p || !p->resident || p->produced || s->eps == 0.0) return BN_OK;
+    const bool fp32 = s->opt.precision == BN_MIXED;
+    const KernelTables* t = s->tabs;
+    const NdRound& R = p->rounds[0];
+    if (fp32)
+        k_beta_slices<float><<<R.nwork, 256, 0, s->stream>>>(p->g, t->P, t->alpha32, t->alphap32, R.d_groups, R.d_group_b,
+                                                              R.d_off16, R.d_work, (float*)p->slices);
+    else
+        k_beta_slices<double><<<R.nwork, 256, 0, s->stream>>>(p->g, t->P, t->alpha64, t->alphap64, R.d_groups,
+                                                               R.d_group_b, R.d_off16, R.d_work, (double*)p->slices);
+    s->launches++;
+    p->produced = true;
+    return cudaGetLastError() == cudaSuccess ? BN_OK : BN_ERR_CUDA;
+}
+
+double nd_triple_terms(const bn_solver* s) { return s->nd ? s->nd->terms : 0.0; }
+int nd_rounds(const bn_solver* s) { return s->nd ? (int)s->nd->rounds.size() : 0; }
+int nd_ctas(const bn_solver* s) { return s->nd ? s->nd->nCTA : 0; }
+size_t nd_slice_bytes(const bn_solver* s) { return s->nd ? s->nd->slice_cap : 0; }
+
+}  // namespace bn

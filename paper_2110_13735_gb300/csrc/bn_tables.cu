@@ -277,7 +277,9 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
             }
     }
     t->P = (int)nodes.size();
-    const size_t nAl = (size_t)t->P * nExt, nBeta = (size_t)nExt * nExt;
+    // 2-D: the full table beta(a, b) over the extended box; 3-D never forms it (the operator
+    // recomputes its slices from the alpha tables)
+    const size_t nAl = (size_t)t->P * nExt, nBeta = d == 2 ? (size_t)nExt * nExt : 0;
     Node* d_nodes = nullptr;
     double2* d_rad = nullptr;
     cudaError_t e = cudaSuccess;
@@ -285,8 +287,8 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e == cudaSuccess && !rad.empty()) e = cudaMalloc(&d_rad, sizeof(double2) * rad.size());
     if (e == cudaSuccess) e = cudaMalloc(&t->alpha64, sizeof(double) * nAl);
     if (e == cudaSuccess) e = cudaMalloc(&t->alphap64, sizeof(double) * nAl);
-    if (e == cudaSuccess) e = cudaMalloc(&t->beta64, sizeof(double) * nBeta);
-    if (e == cudaSuccess) e = cudaMalloc(&t->beta32, sizeof(float) * nBeta);
+    if (e == cudaSuccess && nBeta) e = cudaMalloc(&t->beta64, sizeof(double) * nBeta);
+    if (e == cudaSuccess && nBeta) e = cudaMalloc(&t->beta32, sizeof(float) * nBeta);
     const size_t nSw = d == 2 ? (size_t)nExt * s->g.nModes : 0;
     if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw64, sizeof(double) * nSw);
     if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw32, sizeof(float) * nSw);
@@ -309,9 +311,27 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (d_rad) cudaMemcpyAsync(d_rad, rad.data(), sizeof(double2) * rad.size(), cudaMemcpyHostToDevice, s->stream);
     k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, s->kernel, (int)rad.size(),
                                                d_rad, d_nodes, t->alpha64, t->alphap64);
-    const dim3 gb((nExt + kBT - 1) / kBT, (nExt + kBT - 1) / kBT);
-    k_beta_table<<<gb, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
-    s->launches += 2;
+    s->launches++;
+    if (nBeta) {
+        const dim3 gb((nExt + kBT - 1) / kBT, (nExt + kBT - 1) / kBT);
+        k_beta_table<<<gb, 256, 0, s->stream>>>(nExt, t->P, t->alpha64, t->alphap64, t->beta64, t->beta32);
+        s->launches++;
+    }
+    {
+        std::string e2;
+        if (build_nd_tables(s, t, &e2) != BN_OK) {
+            *err = e2;
+            cudaStreamSynchronize(s->stream);
+            cudaFree(d_nodes);
+            cudaFree(d_rad);
+            cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
+            cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
+            cudaFree(t->alpha32); cudaFree(t->alphap32); cudaFree(t->alphaI64); cudaFree(t->alphapI64);
+            cudaFree(t->alphaI32); cudaFree(t->alphapI32);
+            delete t;
+            return BN_ERR_NOMEM;
+        }
+    }
     if (nSw) {
         k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
         k_dq_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->dq32);
@@ -330,6 +350,8 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
         cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
+        cudaFree(t->alpha32); cudaFree(t->alphap32); cudaFree(t->alphaI64); cudaFree(t->alphapI64);
+        cudaFree(t->alphaI32); cudaFree(t->alphapI32);
         delete t;
         return BN_ERR_CUDA;
     }
@@ -352,6 +374,12 @@ void release_tables(KernelTables* t) {
     cudaFree(t->sw32);
     cudaFree(t->dq32);
     cudaFree(t->beta32T);
+    cudaFree(t->alpha32);
+    cudaFree(t->alphap32);
+    cudaFree(t->alphaI64);
+    cudaFree(t->alphapI64);
+    cudaFree(t->alphaI32);
+    cudaFree(t->alphapI32);
     delete t;
 }
 
