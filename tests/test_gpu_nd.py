@@ -9,7 +9,8 @@ printed per case.
 Sizes: every output at 3-D N <= 16; at N = 32 the oracle evaluates sampled modes (the corners of
 I_N, edges and the centre) one by one; at N = 32 and 48 with the default quadrature a state whose
 modes are a few random trigonometric modes (the GPU still evaluates every term; the oracle skips
-exact zeros) is compared on several hundred sampled modes.
+exact zeros) is compared on several hundred sampled modes.  FP64 at N = 48 is not run here: one
+evaluation takes about 26 minutes on a GB300 (4e14 terms at the FP64 rate).
 """
 from __future__ import annotations
 
@@ -122,7 +123,9 @@ def _sparse_state(d, N, K, seed):
 @pytest.mark.parametrize("N", [32, 48])
 def test_3d_sparse_modes_default_quadrature(B, N):
     """3-D N = 32 and 48, default quadrature (M1 = M2 = N/2), mixed precision: a state made of a
-    few modes; every GPU term is still evaluated.  Compared on the corners and 400 sampled modes."""
+    few modes; every GPU term is still evaluated.  Compared on the corners and 400 sampled modes.
+    The gain term of such a state vanishes at most sampled modes, so the error is normalised by
+    ||Q^_oracle|| over the compared modes instead."""
     eps = 1.0
     f, G = _sparse_state(3, N, 12, N)
     ora = O.Operator(3, N, T6, R6, 1, eps)
@@ -131,8 +134,8 @@ def test_3d_sparse_modes_default_quadrature(B, N):
     Qg = _gpu_modes(B, 3, N, eps, f, "mixed")
     h = N // 2
     Qg_s = np.array([Qg[tuple(n + h)] for n in nl])
-    err = _e(Qg_s, Qo, gain)
-    print(f"3-D N={N} sparse state, {len(nl)} modes, mixed: e_Q = {err:.3e}")
+    err = _e(Qg_s, Qo, Qo)
+    print(f"3-D N={N} sparse state, {len(nl)} modes, mixed: ||dQ^|| / ||Q^|| = {err:.3e}")
     assert err <= 2e-6
 
 
