@@ -168,6 +168,93 @@ def make_pair(bn, I, precision, stream, mixed_rw=0):
     return [bkw, bos], [f_bkw, f_bos]
 
 
+def fma_peaks(bn, stream):
+    """Measured FMA rates of this GPU (FP32, paired FP32, FP64) with the SM clock sampled around
+    them: the roofline denominators of the operator kernels."""
+    clk = os.path.join(tempfile.gettempdir(), f"bn_bench_peak_clocks_{os.getpid()}.csv")
+    p, fh = clocks_sampler_start(clk)
+    t0 = time.time()
+    res = {}
+    for kind, name in ((0, "fp32"), (1, "fp32x2"), (2, "fp64")):
+        best = 0.0
+        for _ in range(2):
+            best = max(best, bn.measure_fma_peak(kind, stream)[0])
+        res[name] = best
+    clocks = clocks_sampler_stop(p, fh, clk, 0, (t0, time.time()))
+    res["unit"] = "TFLOP/s"
+    res["sm_mhz"] = clocks["sm_mhz"] if clocks else None
+    res["how"] = ("4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, fastest of 3 timed launches "
+                  "(CUDA events)")
+    return res
+
+
+def leg_3d(bn, I, which: str, steps: int, peak_fp32: float):
+    """A 3-D configuration in mixed precision with FP64 moments and the conservation projection:
+    'config2' = hard spheres N=32, eps=-1, two Gaussians (variance 0.8, centres +-(1.5,0,0), max 0.9),
+    RK4 dt=0.01; 'config4' = hard spheres N=48, eps=+1, Gaussian of mass 8 and temperature 0.4, RK4
+    dt=0.002 (one evaluation only: 4e14 terms).  The kernel-mode slices are recomputed from the
+    quadrature factors at every evaluation.  Times RK4 steps (config2) or evaluations (config4) with
+    CUDA events on the solver's stream, the phases of every evaluation with the library's events."""
+    import torch
+    N, eps, dt, f0 = (32, -1.0, 0.01, I.config2_f0(32, R_TRUNC)) if which == "config2" else \
+        (48, 1.0, 0.002, I.config4_f0(48, R_TRUNC))
+    T = I.box_half_width(R_TRUNC)
+    stream = torch.cuda.Stream()
+    t_create = time.perf_counter()
+    s = bn.Solver(3, N, T, R_TRUNC, bn.HARD_SPHERE, eps, stream=stream, precision=bn.MIXED, conserve=1)
+    t_create = time.perf_counter() - t_create
+    s.set_state(f0)
+    s.profile_enable(True)
+    wc = s.work_counts()
+    terms_eval = float(wc[0] + wc[1] + wc[2])
+    out = {"workload": f"3-D hard spheres N={N}, eps={eps:+g}, mixed precision, conservation projection, "
+                       f"RK4 dt={dt}", "create_s": t_create}
+    ms = []
+    if which == "config2":
+        s.step_rk(dt, 1)   # warm-up: captures the step graph
+        s.profile_nd()
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step_rk(dt, 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        evals = 4 * steps
+        ph = s.profile_nd()
+        out.update({"steps": steps, "ms_per_step": float(np.mean(ms)),
+                    "value": terms_eval * evals / (np.sum(ms) * 1e-3), "unit": UNIT})
+    else:
+        s.eval_collision()   # warm-up evaluation is the same size as the timed one: time one only
+        s.profile_nd()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.eval_collision()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        evals = 1
+        ph = s.profile_nd()
+        out.update({"evaluations": 1, "ms_per_eval": ms[0], "value": terms_eval / (ms[0] * 1e-3), "unit": UNIT})
+    m = s.moments()
+    s.close()
+    n_ev = max(1.0, ph["evals"])
+    sweep_ms = ph["sweep_ms"] / n_ev
+    achieved = 4.0 * ph["terms"] / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else None
+    out["phases_ms_per_eval"] = {k: ph[k] / n_ev for k in ("pair_ms", "beta_ms", "sweep_ms", "tail_ms")}
+    out["rounds"], out["ctas"] = int(ph["rounds"]), int(ph["ctas"])
+    out["terms_per_eval"] = {"quadratic": float(wc[0]), "reducible": float(wc[1]), "triple": float(wc[2])}
+    out["roofline"] = {"bound": "alu", "kernel": "k_triple_nd<float,8> (Q_{1,q} Toeplitz sweeps)",
+                       "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                       "frac": achieved / peak_fp32 if achieved else None,
+                       "basis": "4 flop (2 FP32 FMA) per Q_{1,q} term / summed sweep-launch event time per evaluation",
+                       "peak_basis": "measured paired-FP32 FMA rate (bn_measure_fma_peak)"}
+    out["moments_after"] = {"rho": m[0], "e": m[4], "max_f": m[7], "t": m[8]}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -187,6 +274,7 @@ def run_ours(args):
     bn.load()
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peaks = fma_peaks(bn, stream)
 
     terms_step = 4.0 * (lemma_terms(2, N_MODES, False) + lemma_terms(2, N_MODES, True))
 
@@ -263,7 +351,7 @@ def run_ours(args):
     # the Q_{1,q} triple sum of the eps=+1 request, 4 flop (2 FFMA) per term.  The eps=0 request's
     # quadratic terms (0.1% of the work) are not counted.
     flops_launch = 4.0 * (2.0 * (N_MODES ** 3 - N_MODES) / 3.0) ** 2
-    peak = SM_COUNT * FP32_LANES * 2.0 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = peaks["fp32x2"]
     kcfg = solvers[1].kernel_config()
     kern_ms, basis = None, None
     if prof and prof[3] > 0 and prof[2] > 0:
@@ -276,9 +364,11 @@ def run_ours(args):
                           f"{kcfg[0]} outputs/thread chosen by the autotuner, {kcfg[1]} CTAs per request)",
                 "launches_timed": int(prof[3]) if prof else 0, "ms_per_launch": kern_ms,
                 "timing": basis,
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts, max clock)"}
-    if clocks and achieved:
-        roofline["frac_at_median_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+                "peak_basis": f"measured paired-FP32 FMA rate of this GPU (bn_measure_fma_peak) at "
+                              f"{peaks['sm_mhz']} MHz; unit counts at the maximum clock give "
+                              f"{SM_COUNT * FP32_LANES * 2.0 * SM_MAX_MHZ * 1e6 / 1e12:.1f}"}
+    if clocks and achieved and peaks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / (peak * clocks["sm_mhz"] / peaks["sm_mhz"])
     for s in solvers:
         s.close()
 
@@ -296,9 +386,10 @@ def run_ours(args):
             k64_ms = prof64[2] / prof64[3]
             a64 = flops_launch / (k64_ms * 1e-3) / 1e12
             fp64["roofline"] = {"bound": "alu", "kernel": "k_fused2d_batch<double,2,128> (both requests)",
-                                "ms_per_launch": k64_ms, "achieved": a64, "peak": FP64_PEAK_TF, "unit": "TFLOP/s",
-                                "frac": a64 / FP64_PEAK_TF,
-                                "peak_basis": "nominal GB300 FP64 (no measured FP64 figure on this pool)"}
+                                "ms_per_launch": k64_ms, "achieved": a64, "peak": peaks["fp64"], "unit": "TFLOP/s",
+                                "frac": a64 / peaks["fp64"],
+                                "peak_basis": f"measured FP64 FMA rate of this GPU (bn_measure_fma_peak); "
+                                              f"nominal {FP64_PEAK_TF}"}
 
     steps_to_end = {k: int(round(v / DT)) for k, v in T_END.items()}
     solves = {"pair_solve_s_mixed": ms_per_step * max(steps_to_end.values()) / 1e3}
@@ -311,6 +402,12 @@ def run_ours(args):
     if args.serving > 0:
         serving = serving_sample(bn, I, args.serving, 200.0, args.serving_fp64,
                                  Ns=(16, 32, 64) if args.serving_n64 else (16, 32))
+
+    legs = {}
+    if args.leg3d_steps > 0:
+        legs["config2_3d_n32"] = leg_3d(bn, I, "config2", args.leg3d_steps, peaks["fp32x2"])
+    if args.leg48:
+        legs["config4_3d_n48"] = leg_3d(bn, I, "config4", 1, peaks["fp32x2"])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -331,6 +428,8 @@ def run_ours(args):
             "fp64": fp64,
             "solves": solves,
             "serving": serving,
+            "fma_peaks": peaks,
+            "legs": legs,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -479,6 +578,9 @@ def main():
     ap.add_argument("--serving-fp64", type=int, default=12, help="requests re-solved one at a time in FP64")
     ap.add_argument("--serving-n64", action="store_true", help="include N=64 requests in the serving mix")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg (profiling runs)")
+    ap.add_argument("--leg3d-steps", type=int, default=1,
+                    help="timed RK4 steps of the 3-D N=32 configuration (0 = skip)")
+    ap.add_argument("--leg48", action="store_true", help="also time one evaluation of the 3-D N=48 configuration")
     ap.add_argument("--mixed-rw", type=int, default=0, choices=[0, 8, 16],
                     help="outputs per thread of the mixed kernel (0 = autotuner; profiling runs fix it)")
     args = ap.parse_args()

@@ -80,7 +80,8 @@ typedef struct {
     double escalate_at; /* mixed precision only: when |eps| max f >= escalate_at after a
                          bn_step_rk / bn_step_rk_batch call (near Fermi saturation or
                          condensation onset), the solver switches to FP64 for the rest of its
-                         life; 0 = never */
+                         life; 0 = never.  Sizes with no FP64 kernel (3-D N > 32) stay in
+                         mixed precision and clear escalate_at */
     int mixed_rw;     /* mixed precision, d = 2, N <= 32: outputs per thread of the fused
                          kernel's sweep, 8 or 16; 0 = chosen by the autotuner (the variants
                          timed on the solver's stream at creation, cached per device and N;
@@ -97,6 +98,10 @@ typedef struct {
     long long beta_budget_mb; /* 3-D and CIRCULAR: device memory (MiB) for the slices of one round
                          (0 = 40% of the free memory, at most 40 GiB); slices that do not fit are
                          produced and consumed in several rounds per evaluation */
+    int pair_weights; /* 3-D and CIRCULAR: 0 = form the weights of the quadratic and reducible pair
+                         sums over I_N x I_N once, when they fit in 45% of the free memory (the
+                         default); 1 = recompute them from the quadrature factors at every
+                         evaluation */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
@@ -104,7 +109,8 @@ bn_status bn_default_options(bn_options* opt);
 
 /*
  * Create a solver for the operator (d, N, T, R, kernel, eps).  d in {2,3};
- * N even, 4 <= N <= 64 (2-D) or <= 16 (3-D); T > 0 the box half-width; R > 0
+ * N even, 4 <= N <= 64 (2-D) or <= 48 (3-D; FP64 up to 32, CIRCULAR FP64 2-D up
+ * to 62); T > 0 the box half-width; R > 0
  * the truncation radius (velocity units); kernel BN_MAXWELL (d = 2) or
  * BN_HARD_SPHERE (d = 2 or 3); opt may be NULL; cuda_stream is a cudaStream_t or
  * NULL.  Builds the kernel-mode tables in FP64 on the device (once per
@@ -203,6 +209,17 @@ long long bn_kernel_launches(const bn_solver* s);
  */
 bn_status bn_profile_enable(bn_solver* s, int enable);
 bn_status bn_profile_read(bn_solver* s, double* out, size_t count);
+
+/*
+ * Phase timing of the 3-D / CIRCULAR operator (bn_profile_enable must be on; the times of one
+ * bn_step_rk call cover its last step, so call it with nsteps = 1 to time every step).
+ * out[0..3] = summed ms of the quadratic and reducible pair sums, of the production of the
+ * kernel-mode slices (the sum of eq. betadD), of the Toeplitz sweeps of Q_{1,q}, and of the tail
+ * (partial sums, reducible convolution, combination); out[4] = evaluations timed; out[5] = rounds
+ * per evaluation; out[6] = Q_{1,q} terms per evaluation; out[7] = CTAs of the sweep launch; then
+ * resets.  count >= 8.  BN_ERR_UNSUPPORTED for a 2-D LINEAR solver.
+ */
+bn_status bn_profile_nd(bn_solver* s, double* out, size_t count);
 
 /* Precision state: *precision = BN_FP64 or BN_MIXED now in use; *t_escalated = the
  * time at which a mixed-precision solver switched to FP64 (-1 if it has not);

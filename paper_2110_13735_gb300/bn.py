@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
                 ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int), ("wrap", ctypes.c_int),
-                ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong)]
+                ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong), ("pair_weights", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -82,6 +82,7 @@ def load(path: str | None = None):
     lib.bn_last_error.restype = ctypes.c_char_p
     lib.bn_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.bn_profile_read.argtypes = [vp, dp, sz]
+    lib.bn_profile_nd.argtypes = [vp, dp, sz]
     lib.bn_step_rk_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.bn_server_create.argtypes = [sz, ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.bn_server_submit.argtypes = [vp, ctypes.POINTER(Request), dp, sz, ctypes.POINTER(ctypes.c_longlong)]
@@ -130,12 +131,13 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
 
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
-            escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0) -> Options:
+            escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0,
+            pair_weights=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
-    o.wrap, o.beta_resident, o.beta_budget_mb = wrap, beta_resident, beta_budget_mb
+    o.wrap, o.beta_resident, o.beta_budget_mb, o.pair_weights = wrap, beta_resident, beta_budget_mb, pair_weights
     return o
 
 
@@ -260,6 +262,14 @@ class Solver:
 
     def profile_enable(self, on: bool = True):
         _check(_lib.bn_profile_enable(self._h, int(bool(on))))
+
+    def profile_nd(self):
+        """Phase timing of the 3-D / CIRCULAR operator since the last read (include/bn.h:
+        bn_profile_nd): dict of ms per phase, evaluations, rounds, Q_{1,q} terms, CTAs."""
+        out = np.zeros(8)
+        _check(_lib.bn_profile_nd(self._h, _dptr(out), 8))
+        keys = ["pair_ms", "beta_ms", "sweep_ms", "tail_ms", "evals", "rounds", "terms", "ctas"]
+        return dict(zip(keys, out.tolist()))
 
     def profile_read(self):
         """Dominant-kernel timing since the last read:

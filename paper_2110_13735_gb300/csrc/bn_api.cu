@@ -68,10 +68,11 @@ void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
         if (s->opt.conserve) bn::launch_conserve(s, Q_out);
         return;
     }
-    // 3-D and CIRCULAR: kernel-mode slices recomputed per evaluation (bn_opnd.cu)
+    // 3-D and CIRCULAR: kernel-mode slices recomputed per evaluation (bn_opnd.cu); with live
+    // profiling the whole operator is timed per slot, and its phases by bn_profile_nd
     const int slot = s->prof_slot;
     if (s->prof && slot < 8) cudaEventRecord(s->prof_ev[2 * slot], s->stream);
-    bn::launch_nd(s, nullptr);
+    bn::launch_nd(s, s->prof ? slot : -1);
     if (s->prof && slot < 8) {
         cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
         s->prof_slot = slot + 1;
@@ -144,11 +145,14 @@ void check_escalation(bn_solver* s) {
             bn::free_nd(s);
             std::string err;
             if (bn::plan_nd(s, &err) != BN_OK || bn::prepare_nd(s) != BN_OK) {
+                // no FP64 plan for this size (e.g. 3-D N > 32 exceeds the FP64 kernel's shared
+                // memory): stay in mixed precision and stop trying
                 bn::free_nd(s);
                 s->opt.precision = BN_MIXED;
+                s->opt.escalate_at = 0;
                 s->t_escalated = -1;
-                err = "escalation to FP64 failed: " + err;
-                bn::plan_nd(s, &err);
+                std::string err2;
+                bn::plan_nd(s, &err2);
                 bn::prepare_nd(s);
             }
             s->n_partials = bn::nd_ctas(s);
@@ -165,6 +169,7 @@ void check_escalation(bn_solver* s) {
 // or direct evaluation (the stream has been synchronised).
 void harvest_profile(bn_solver* s, int slots) {
     if (!s->prof) return;
+    bn::nd_profile_harvest(s, slots);
     if (s->prof_stamps && slots > 0) {
         unsigned long long st[16];
         if (cudaMemcpy(st, s->prof_stamps, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess) {
@@ -257,9 +262,10 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(BN_ERR_ARG, "wrap must be 0 (LINEAR) or 1 (CIRCULAR)");
     }
-    if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1)) {
+    if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1) ||
+        (s->opt.pair_weights != 0 && s->opt.pair_weights != 1)) {
         delete s;
-        return fail(BN_ERR_ARG, "beta_budget_mb must be >= 0 and beta_resident 0 or 1");
+        return fail(BN_ERR_ARG, "beta_budget_mb must be >= 0, beta_resident and pair_weights 0 or 1");
     }
     if (s->opt.M <= 0) s->opt.M = 2 * N;
     if (s->opt.c_phi <= 0) s->opt.c_phi = d == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI);
@@ -554,6 +560,10 @@ bn_status bn_profile_enable(bn_solver* s, int enable) {
         cudaError_t e = cudaMalloc(&s->prof_stamps, 16 * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(e, "profile stamps");
     }
+    if (s->nd) {
+        bn_status st = bn::nd_profile_enable(s, on);
+        if (st != BN_OK) return fail(st, "profile events");
+    }
     if (on != s->prof && s->step_graph) {
         cudaStreamSynchronize(s->stream);
         cudaGraphExecDestroy(s->step_graph);
@@ -685,4 +695,10 @@ extern "C" bn_status bn_plan_mixed2d(int N, int rw, int oriented, int nblk, int*
         std::copy(rows.begin(), rows.end(), out);
     }
     return BN_OK;
+}
+
+extern "C" bn_status bn_profile_nd(bn_solver* s, double* out, size_t count) {
+    if (!valid_solver(s) || !out || count < 8) return fail(BN_ERR_ARG, "null solver/out or count < 8");
+    if (!s->nd) return fail(BN_ERR_UNSUPPORTED, "bn_profile_nd: not a 3-D or CIRCULAR solver");
+    return bn::nd_profile_read(s, out, count);
 }

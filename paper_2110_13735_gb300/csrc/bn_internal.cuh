@@ -360,7 +360,10 @@ bool use_nd(const bn_solver* s);
 bn_status plan_nd(bn_solver* s, std::string* err);
 bn_status build_nd_tables(bn_solver* s, KernelTables* t, std::string* err);
 bn_status prepare_nd(bn_solver* s);
-void launch_nd(bn_solver* s, unsigned long long* stamps);
+void launch_nd(bn_solver* s, int slot);   // slot: live phase-timing slot, -1 = none
+bn_status nd_profile_enable(bn_solver* s, bool on);
+void nd_profile_harvest(bn_solver* s, int slots);
+bn_status nd_profile_read(bn_solver* s, double* out, size_t count);
 void free_nd(bn_solver* s);
 double nd_triple_terms(const bn_solver* s);
 int nd_rounds(const bn_solver* s);

@@ -127,9 +127,14 @@ struct NdGroup {
 };
 
 struct NdItem {
-    uint32_t w0;          // b flat | (t0 index << 20) | (T0 << 26)
+    uint32_t bflat;       // b (flat index over the b box)
+    uint8_t t0i, T0;      // output planes n_0 in [nlo_0 + t0i, + T0)
+    uint8_t L1t, J;       // output rows per tile along axis 1; lanes splitting the s_1 range
+    uint8_t RW, pad0;     // outputs per thread along axis 2 (4 or 8)
+    uint16_t pad1;
     uint32_t off16;       // slice offset in 16-byte units from the slice buffer
 };
+static_assert(sizeof(NdItem) == 16, "NdItem is 16 bytes");
 
 template <typename Real> struct CT;
 template <> struct CT<float> { using C = float2; using P4 = float4; };
@@ -233,14 +238,6 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 __device__ __forceinline__ void nd_bar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// bulk (TMA engine) copy of `bytes` (multiple of 16, both ends 16-byte aligned) completing on bar
-__device__ __forceinline__ void nd_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
-        "l"(src), "r"(bytes), "r"(su32(bar))
-        : "memory");
 }
 __device__ __forceinline__ bool nd_bar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < kWaitNd; ++i) {
@@ -350,9 +347,11 @@ struct TripleNdArgs {
     const void* slices;       // slice buffer (float or double)
     void* partials;           // [gridDim.x][N^d]: float4 (sum, compensation) or double2
     int* err;                 // [0] set when a bounded wait gives up
-    int PB;                   // elements per staged slice plane (max over items, + RW slack)
-    int PS;                   // P plane row stride (complex entries)
-    int PP;                   // complex entries per P plane
+    int WS;                   // row stride (elements) of a staged slice plane: odd, >= widest row + RW - 1
+    int PB;                   // elements per staged slice plane buffer (max rows x WS + RW slack)
+    int PS;                   // P plane row stride (complex entries, odd)
+    int PP;                   // complex entries per P plane buffer
+    int GP;                   // complex entries per staged mode plane (n1 n2; 0 when axis 0 is trivial)
     int T0max;
     unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
 };
@@ -368,54 +367,124 @@ __device__ __forceinline__ typename CT<Real>::C load_mode(const TripleNdArgs& A,
     return reinterpret_cast<const typename CT<Real>::C*>(A.G)[m];
 }
 
-// Shared memory: two slice-plane buffers, T0max + 1 P planes (a ring), one mbarrier per plane buffer.
+__device__ __forceinline__ void cp_async_el(void* dst, const void* src, int bytes) {
+    if (bytes == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// generic-proxy accesses of shared memory before this point are ordered before later bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared memory: two slice-plane buffers (rows at the odd stride WS, so that the output rows a
+// warp sweeps fall on distinct banks), T0max + 1 P planes (a ring, odd row stride), two slots of
+// the two mode planes a P plane is built from (bulk copies, one mbarrier per slot).
+struct NdShared {
+    void* G;          // [2 slots][2 planes][GP] complex
+    void* P;          // [T0max + 1][PP] complex
+    void* B;          // [2][PB] real
+    uint64_t* bar;    // [2]
+};
+
+// One work item: output planes n_0 in [t0, t0 + T0) of the box of b, in tiles of L1t output rows
+// n_1; RW outputs per thread along axis 2 and the s_1 range split over J lanes.  For each tile the
+// CTA walks the planes a_0 of the slice: the rows of plane a_0 the tile needs are copied into
+// shared memory while the previous plane is swept, and the P plane first needed at the next step
+// is built from mode planes fetched (bulk copy) one step earlier.
 template <typename Real, int RW>
-__global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
+__device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem& item, const NdShared& sm,
+                                            uint32_t& phases) {
     using C = typename CT<Real>::C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* bufB = reinterpret_cast<Real*>(smem_raw);                       // [2][PB]
-    C* bufP = reinterpret_cast<C*>(bufB + 2 * (size_t)A.PB);             // [T0max + 1][PP]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(bufP + (size_t)(A.T0max + 1) * A.PP);   // [2]
     const NdGeo& g = A.g;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    if (A.stamps && tid == 0) atomicMin(A.stamps, nd_now());
-    if (tid == 0) {
-        nd_bar_init(&bar[0]);
-        nd_bar_init(&bar[1]);
-    }
-    __syncthreads();
-    uint32_t phases = 0u;   // bit i: parity of the next completion of bar[i]
-    const int it0 = A.cta_off[blockIdx.x], it1 = A.cta_off[blockIdx.x + 1];
+    C* bufG = reinterpret_cast<C*>(sm.G);
+    C* bufP = reinterpret_cast<C*>(sm.P);
+    Real* bufB = reinterpret_cast<Real*>(sm.B);
+    uint64_t* bar = sm.bar;
     const Real* slices = reinterpret_cast<const Real*>(A.slices);
-    for (int it = it0; it < it1; ++it) {
-        const NdItem item = A.items[it];
-        const int bflat = (int)(item.w0 & 0xFFFFFu);
-        const int t0i = (int)((item.w0 >> 20) & 63u), T0 = (int)(item.w0 >> 26);
-        int b[3];
-        b_of_flat(g, bflat, b);
-        Box3 B;
-        box_of(g, b, B);
-        const int RS = slice_rs(B.A[2], (int)sizeof(Real));
-        const Real* __restrict__ slice = slices + (size_t)item.off16 * (16 / sizeof(Real));
-        const int planeElems = B.A[1] * RS;
-        const int t0 = B.nlo[0] + t0i;
-        const int G2 = (B.L[2] + RW - 1) / RW;
-        const int tasks = T0 * B.L[1] * G2;
-        int J = 1;
-        while (J < 8 && tasks * 2 * J <= nthr && 2 * J <= B.S[1]) J *= 2;
-        const int task = tid / J, jj = tid % J;
+    const C* Gm = reinterpret_cast<const C*>(A.G);
+    const int planeG = g.n[1] * g.n[2];
+    int b[3];
+    b_of_flat(g, (int)item.bflat, b);
+    Box3 B;
+    box_of(g, b, B);
+    const int RS = slice_rs(B.A[2], (int)sizeof(Real));
+    const Real* __restrict__ slice = slices + (size_t)item.off16 * (16 / sizeof(Real));
+    const int planeElems = B.A[1] * RS;
+    const int T0 = item.T0, J = item.J, L1t = item.L1t;
+    const int t0 = B.nlo[0] + item.t0i;
+    const int G2 = (B.L[2] + RW - 1) / RW;
+    const int aHi = t0 + T0 - 1 - B.slo[0];
+    const int aLo = t0 - (B.slo[0] + B.S[0] - 1);
+    const int shi0 = B.slo[0] + B.S[0] - 1;
+    const int ringN = A.T0max + 1;
+    const int task = tid / J, jj = tid % J;
+    const int ch = (B.S[1] + J - 1) / J;
+    const int s1a = B.slo[1] + jj * ch, s1b = min(B.slo[1] + B.S[1], s1a + ch);
+    auto m0_of = [&](int s0) { return g.wrap ? red_mod(b[0] - s0, g.lo[0], g.n[0]) : b[0] - s0; };
+    auto ring = [&](int s0) { return bufP + (size_t)(((s0 - B.slo[0]) % ringN + ringN) % ringN) * A.PP; };
+    // mode planes s0 and b0 - s0 into slot k (one bulk copy each, completing on bar[k])
+    auto fetch_modes = [&](int s0, int k) {
+        if (tid == 0) {
+            fence_proxy_async();
+            C* dst = bufG + (size_t)k * 2 * A.GP;
+            const uint32_t bytes = (uint32_t)(planeG * sizeof(C));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar[k])), "r"(2 * bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+                "l"(Gm + (size_t)(s0 - g.lo[0]) * planeG), "r"(bytes), "r"(su32(&bar[k]))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    su32(dst + A.GP)),
+                "l"(Gm + (size_t)(m0_of(s0) - g.lo[0]) * planeG), "r"(bytes), "r"(su32(&bar[k]))
+                : "memory");
+        }
+    };
+    // P plane s0 from the staged mode planes of slot k, or from global memory (k < 0)
+    auto build_P = [&](int s0, int k) {
+        C* dst = ring(s0);
+        const C* gs = bufG + (size_t)max(k, 0) * 2 * A.GP;
+        const C* gm = gs + A.GP;
+        const int m0 = m0_of(s0);
+        const int tot = B.S[1] * B.S[2];
+        for (int q = tid; q < tot; q += nthr) {
+            const int r1 = q / B.S[2], r2 = q - r1 * B.S[2];
+            const int s1 = B.slo[1] + r1, s2 = B.slo[2] + r2;
+            int m1 = b[1] - s1, m2 = b[2] - s2;
+            if (g.wrap) {
+                m1 = red_mod(m1, g.lo[1], g.n[1]);
+                m2 = red_mod(m2, g.lo[2], g.n[2]);
+            }
+            C v;
+            if (k >= 0) v = cmul2(gs[(s1 - g.lo[1]) * g.n[2] + (s2 - g.lo[2])], gm[(m1 - g.lo[1]) * g.n[2] + (m2 - g.lo[2])]);
+            else v = cmul2(Gm[mode_index(g, s0, s1, s2)], Gm[mode_index(g, m0, m1, m2)]);
+            dst[r1 * A.PS + r2] = v;
+        }
+    };
+    for (int n1i = 0; n1i < B.L[1]; n1i += L1t) {
+        const int L1c = min(L1t, B.L[1] - n1i);
+        const int R1 = L1c + B.S[1] - 1;   // slice rows this tile needs: [n1i, n1i + R1)
+        const int tasks = T0 * L1c * G2;
         const bool active = task < tasks;
-        const int g2 = task % G2, n1 = B.nlo[1] + (task / G2) % B.L[1], i0 = task / (G2 * B.L[1]);
+        const int g2 = task % G2, n1 = B.nlo[1] + n1i + (task / G2) % L1c, i0 = task / (G2 * L1c);
         const int n0 = t0 + i0;
-        const int ch = (B.S[1] + J - 1) / J;
-        const int s1a = B.slo[1] + jj * ch, s1b = min(B.slo[1] + B.S[1], s1a + ch);
         const int n2 = B.nlo[2] + g2 * RW;
         const int c0 = n2 - B.slo[2] - B.alo[2];
-        // planes a0 of the slice met by the outputs t0 .. t0 + T0 - 1
-        const int aHi = t0 + T0 - 1 - B.slo[0];
-        const int aLo = t0 - (B.slo[0] + B.S[0] - 1);
-        const int ringN = A.T0max + 1;
-        // accumulators
+        const int rowoff = n1 - B.alo[1] - n1i;   // staged row of (n1, s1) is rowoff - s1
+        auto stage_plane = [&](int a0, int kb) {
+            const Real* src = slice + (size_t)(a0 - B.alo[0]) * planeElems + (size_t)n1i * RS;
+            Real* dst = bufB + (size_t)kb * A.PB;
+            const int tot = R1 * B.A[2];
+            for (int e = tid; e < tot; e += nthr) {
+                const int r = e / B.A[2], c = e - r * B.A[2];
+                cp_async_el(dst + r * A.WS + c, src + (size_t)r * RS + c, (int)sizeof(Real));
+            }
+            cp_async_commit();
+        };
         uint64_t acc32[RW];
         double2 acc64[RW];
         float ks[2 * RW], kc[2 * RW];
@@ -426,51 +495,39 @@ __global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
             ks[2 * r] = ks[2 * r + 1] = 0.f;
             kc[2 * r] = kc[2 * r + 1] = 0.f;
         }
-        // P plane s0 into ring slot (s0 - slo0) mod ringN
-        auto build_P = [&](int s0) {
-            C* dst = bufP + (size_t)(((s0 - B.slo[0]) % ringN + ringN) % ringN) * A.PP;
-            const int tot = B.S[1] * B.S[2];
-            for (int q = tid; q < tot; q += nthr) {
-                const int r1 = q / B.S[2], r2 = q - r1 * B.S[2];
-                const int s1 = B.slo[1] + r1, s2 = B.slo[2] + r2;
-                int m0 = b[0] - s0, m1 = b[1] - s1, m2 = b[2] - s2;
-                if (g.wrap) {
-                    m0 = red_mod(m0, g.lo[0], g.n[0]);
-                    m1 = red_mod(m1, g.lo[1], g.n[1]);
-                    m2 = red_mod(m2, g.lo[2], g.n[2]);
-                }
-                dst[r1 * A.PS + r2] = cmul2(load_mode<Real>(A, mode_index(g, s0, s1, s2)),
-                                            load_mode<Real>(A, mode_index(g, m0, m1, m2)));
-            }
-        };
-        // previous item's readers are done with every buffer
+        // previous readers are done with every buffer
         __syncthreads();
-        if (tid == 0) {
-            nd_bulk_load(bufB, slice + (size_t)(aHi - B.alo[0]) * planeElems,
-                         (uint32_t)(planeElems * sizeof(Real)), &bar[0]);
+        stage_plane(aHi, 0);
+        // the first step needs P planes s0 = n0 - aHi for n0 in [t0, t0 + T0): only slo0 exists
+        for (int s0 = max(B.slo[0], t0 - aHi); s0 <= min(shi0, t0 + T0 - 1 - aHi); ++s0) build_P(s0, -1);
+        {
+            const int sN = t0 + T0 - aHi;
+            if (aHi > aLo && sN <= shi0) fetch_modes(sN, 0);
         }
-        // P planes needed at the first step: s0 = n0 - aHi for n0 in [t0, t0 + T0)
-        for (int s0 = max(B.slo[0], t0 - aHi); s0 <= min(B.slo[0] + B.S[0] - 1, t0 + T0 - 1 - aHi); ++s0) build_P(s0);
+        cp_async_wait_all();
+        __syncthreads();
         int slot = 0;
         for (int a0 = aHi; a0 >= aLo; --a0) {
-            if (!nd_bar_wait(&bar[slot], (phases >> slot) & 1u)) {
-                if (tid == 0) atomicExch(A.err, 1);
-            }
-            phases ^= 1u << slot;
-            __syncthreads();   // the plane has landed and the P planes of this step are built
+            const int k = (aHi - a0) & 1;   // mode-plane slot of this step
             if (a0 > aLo) {
-                if (tid == 0)
-                    nd_bulk_load(bufB + (size_t)(slot ^ 1) * A.PB, slice + (size_t)(a0 - 1 - B.alo[0]) * planeElems,
-                                 (uint32_t)(planeElems * sizeof(Real)), &bar[slot ^ 1]);
-                const int sNew = t0 + T0 - 1 - (a0 - 1);   // the one P plane first needed at a0 - 1
-                if (sNew >= B.slo[0] && sNew < B.slo[0] + B.S[0]) build_P(sNew);
+                stage_plane(a0 - 1, slot ^ 1);
+                const int sNew = t0 + T0 - a0;   // first needed at step a0 - 1; its modes are in slot k
+                if (sNew <= shi0) {
+                    const int sNext = sNew + 1;
+                    if (a0 - 1 > aLo && sNext <= shi0) fetch_modes(sNext, k ^ 1);
+                    if (!nd_bar_wait(&bar[k], (phases >> k) & 1u)) {
+                        if (tid == 0) atomicExch(A.err, 1);
+                    }
+                    phases ^= 1u << k;
+                    build_P(sNew, k);
+                }
             }
             const int s0 = n0 - a0;
-            if (active && s0 >= B.slo[0] && s0 < B.slo[0] + B.S[0]) {
+            if (active && s0 >= B.slo[0] && s0 <= shi0) {
                 const Real* __restrict__ plane = bufB + (size_t)slot * A.PB;
-                const C* __restrict__ pplane = bufP + (size_t)(((s0 - B.slo[0]) % ringN + ringN) % ringN) * A.PP;
+                const C* __restrict__ pplane = ring(s0);
                 for (int s1 = s1a; s1 < s1b; ++s1) {
-                    const Real* brow = plane + (size_t)(n1 - s1 - B.alo[1]) * RS;
+                    const Real* brow = plane + (size_t)(rowoff - s1) * A.WS;
                     const C* prow = pplane + (size_t)(s1 - B.slo[1]) * A.PS;
                     if constexpr (sizeof(Real) == 4)
                         sweep_row_f32<RW>(reinterpret_cast<const float*>(brow), c0,
@@ -491,7 +548,8 @@ __global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
                     }
                 }
             }
-            __syncthreads();   // this plane buffer and the oldest P plane are free again
+            cp_async_wait_all();
+            __syncthreads();   // the next slice plane and P plane are in; this plane buffer is free
             slot ^= 1;
         }
         // meet the J chunks of a task (lanes task*J .. task*J + J - 1 of one warp)
@@ -515,6 +573,7 @@ __global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
             }
         }
         if (active && jj == 0) {
+            const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
 #pragma unroll
             for (int r = 0; r < RW; ++r) {
                 const int nn2 = n2 + r;
@@ -525,9 +584,8 @@ __global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
                     k1 = red_mod(k1, g.lo[1], g.n[1]);
                     k2 = red_mod(k2, g.lo[2], g.n[2]);
                 }
-                const C gk = load_mode<Real>(A, mode_index(g, k0, k1, k2));
+                const C gk = Gm[mode_index(g, k0, k1, k2)];
                 const int on = mode_index(g, n0, n1, nn2);
-                const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
                 if constexpr (sizeof(Real) == 4) {
                     const float2 c = make_float2(ks[2 * r], ks[2 * r + 1]);
                     const float2 t = cmul2(gk, c);
@@ -547,8 +605,40 @@ __global__ void __launch_bounds__(512) k_triple_nd(TripleNdArgs A) {
             }
         }
     }
-    // drain: no bulk copy may still be in flight when the CTA exits (every issued copy was
-    // waited for above, since each issued plane is consumed by the next step)
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_triple_nd(TripleNdArgs A) {
+    using C = typename CT<Real>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NdShared sm;
+    C* bufG = reinterpret_cast<C*>(smem_raw);
+    C* bufP = bufG + 4 * (size_t)A.GP;
+    Real* bufB = reinterpret_cast<Real*>(bufP + (size_t)(A.T0max + 1) * A.PP);
+    sm.G = bufG;
+    sm.P = bufP;
+    sm.B = bufB;
+    sm.bar = reinterpret_cast<uint64_t*>(bufB + 2 * (size_t)A.PB);
+    const int tid = threadIdx.x;
+    if (A.stamps && tid == 0) atomicMin(A.stamps, nd_now());
+    if (tid == 0) {
+        nd_bar_init(&sm.bar[0]);
+        nd_bar_init(&sm.bar[1]);
+    }
+    __syncthreads();
+    uint32_t phases = 0u;   // bit i: parity of the next completion of bar[i]
+    const int it0 = A.cta_off[blockIdx.x], it1 = A.cta_off[blockIdx.x + 1];
+    for (int it = it0; it < it1; ++it) {
+        const NdItem item = A.items[it];
+        if constexpr (sizeof(Real) == 4) {
+            if (item.RW == 8) triple_item<Real, 8>(A, item, sm, phases);
+            else triple_item<Real, 4>(A, item, sm, phases);
+        } else {
+            triple_item<Real, 4>(A, item, sm, phases);
+        }
+    }
+    // every bulk copy issued was waited for (each fetch is consumed one step later) and every
+    // element copy waited at the end of its step: nothing is in flight when the CTA exits
     __syncthreads();
     if (A.stamps && tid == 0) atomicMax(A.stamps + 1, nd_now());
 }
@@ -571,6 +661,8 @@ struct PairNdArgs {
     double2* S;            // t box: LINEAR (2n_x - 1) per axis, CIRCULAR I_N
     int cubic;
     int nt[3], tlo[3];     // t range per axis
+    void* Wq;              // when set: write the weights wq(x, y), wr(x, y) to [x][y] tables (x, y
+    void* Wr;              // flat indices in I_N) instead of forming quad and S
 };
 
 template <typename Real, int TX>
@@ -692,6 +784,28 @@ __global__ void __launch_bounds__(256) k_pair_nd(PairNdArgs A) {
                 }
             }
         }
+        if (A.Wq) {
+            // weight tables: every (x, y) of I_N x I_N belongs to exactly one (t-row, pair, tile)
+            if (pvalid) {
+                Real* wq_t = reinterpret_cast<Real*>(A.Wq);
+                Real* wr_t = reinterpret_cast<Real*>(A.Wr);
+#pragma unroll
+                for (int i = 0; i < TX; ++i) {
+                    const int x2 = g.lo[2] + tx * TX + i;
+                    if (x2 >= g.lo[2] + n2) break;
+                    const size_t xf = (size_t)mode_index(g, x0, x1, x2);
+#pragma unroll
+                    for (int j = 0; j < TX; ++j) {
+                        const int y2 = g.lo[2] + ty * TX + j;
+                        if (y2 >= g.lo[2] + n2) break;
+                        const size_t o = xf * nm + mode_index(g, y0, y1, y2);
+                        wq_t[o] = wq[i][j];
+                        if (A.cubic) wr_t[o] = wr[i][j];
+                    }
+                }
+            }
+            continue;
+        }
         // products with G^_x G^_y, anti-diagonal partials of this thread
         C* mypart = part + ((size_t)(slotp * tpp + lt)) * (2 * TX - 1) * 2;
         if (slotp < PPC) {
@@ -759,6 +873,92 @@ __global__ void __launch_bounds__(256) k_pair_nd(PairNdArgs A) {
         const int t2 = A.tlo[2] + ti;
         if (qrow && t2 >= g.lo[2] && t2 < g.lo[2] + n2) A.quad[mode_index(g, t0, t1, t2)] = accQ[ti];
         if (A.cubic) A.S[((size_t)blockIdx.x) * nT2 + ti] = accS[ti];
+    }
+}
+
+// quad and S from stored weight tables: CTA per t-row (t_0, t_1); its threads form groups of
+// 64, thread u of a group owns the output t_2 = tlo_2 + u and walks the pairs (x_0, x_1) of its
+// group and, for each, x_2 with y_2 = t_2 - x_2 in I_N (reduced in CIRCULAR mode): the table row
+// x is read along y_2, so a warp reads consecutive entries.  The group sums meet in a fixed order.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_pairw_nd(NdGeo g, const Real* __restrict__ Wq, const Real* __restrict__ Wr,
+                                                  const void* __restrict__ Gv, double2* __restrict__ quad,
+                                                  double2* __restrict__ S, int cubic, int nt1, int nT2, int tlo0,
+                                                  int tlo1, int tlo2) {
+    using C = typename CT<Real>::C;
+    __shared__ double2 red[4][2][96];
+    const C* G = reinterpret_cast<const C*>(Gv);
+    const int t0 = tlo0 + (int)blockIdx.x / nt1, t1 = tlo1 + (int)blockIdx.x % nt1;
+    const int grp = threadIdx.x >> 6, u = threadIdx.x & 63;
+    const int ngrp = blockDim.x >> 6;
+    const size_t nm = (size_t)g.n[0] * g.n[1] * g.n[2];
+    int xlo[2], xn[2];
+    for (int x = 0; x < 2; ++x) {
+        const int lo = g.lo[x], hi = g.lo[x] + g.n[x] - 1, t = x == 0 ? t0 : t1;
+        if (g.wrap) { xlo[x] = lo; xn[x] = g.n[x]; }
+        else { xlo[x] = max(lo, t - hi); xn[x] = min(hi, t - lo) - xlo[x] + 1; }
+    }
+    const int n2 = g.n[2], lo2 = g.lo[2];
+    for (int half = 0; half < 2; ++half) {   // t_2 indices u and u + 64 (nT2 <= 127)
+        const int ti = u + 64 * half;
+        double qx = 0, qy = 0, rx = 0, ry = 0;
+        if (ti < nT2) {
+            const int t2 = tlo2 + ti;
+            for (int pi = grp; pi < xn[0] * xn[1]; pi += ngrp) {
+                const int x0 = xlo[0] + pi / xn[1], x1 = xlo[1] + pi % xn[1];
+                int y0 = t0 - x0, y1 = t1 - x1;
+                if (g.wrap) { y0 = red_mod(y0, g.lo[0], g.n[0]); y1 = red_mod(y1, g.lo[1], g.n[1]); }
+                const size_t xrow = (size_t)mode_index(g, x0, x1, lo2);
+                const size_t yrow = (size_t)mode_index(g, y0, y1, lo2);
+                float sqx = 0.f, sqy = 0.f, srx = 0.f, sry = 0.f;   // FP32 pair sums (FP64 for Real = double below)
+                double dqx = 0, dqy = 0, drx = 0, dry = 0;
+                for (int x2 = lo2; x2 < lo2 + n2; ++x2) {
+                    int y2 = t2 - x2;
+                    if (g.wrap) y2 = red_mod(y2, lo2, n2);
+                    else if (y2 < lo2 || y2 >= lo2 + n2) continue;
+                    const size_t xi = xrow + (x2 - lo2), yi = yrow + (y2 - lo2);
+                    const C gx = G[xi], gy = G[yi];
+                    const C gxy = cmul2(gx, gy);
+                    const size_t o = xi * nm + yi;
+                    const Real wq = Wq[o];
+                    if constexpr (sizeof(Real) == 4) {
+                        sqx = fmaf(wq, gxy.x, sqx);
+                        sqy = fmaf(wq, gxy.y, sqy);
+                        if (cubic) {
+                            const float wr = Wr[o];
+                            srx = fmaf(wr, gxy.x, srx);
+                            sry = fmaf(wr, gxy.y, sry);
+                        }
+                    } else {
+                        dqx = fma(wq, gxy.x, dqx);
+                        dqy = fma(wq, gxy.y, dqy);
+                        if (cubic) {
+                            const double wr = Wr[o];
+                            drx = fma(wr, gxy.x, drx);
+                            dry = fma(wr, gxy.y, dry);
+                        }
+                    }
+                }
+                qx += (double)sqx + dqx; qy += (double)sqy + dqy;
+                rx += (double)srx + drx; ry += (double)sry + dry;
+            }
+        }
+        if (ti < 96) {
+            red[grp][0][ti] = make_double2(qx, qy);
+            red[grp][1][ti] = make_double2(rx, ry);
+        }
+    }
+    __syncthreads();
+    const bool qrow = g.wrap || (t0 >= g.lo[0] && t0 < g.lo[0] + g.n[0] && t1 >= g.lo[1] && t1 < g.lo[1] + g.n[1]);
+    for (int ti = threadIdx.x; ti < nT2; ti += blockDim.x) {
+        double qx = 0, qy = 0, rx = 0, ry = 0;
+        for (int k = 0; k < ngrp; ++k) {
+            qx += red[k][0][ti].x; qy += red[k][0][ti].y;
+            rx += red[k][1][ti].x; ry += red[k][1][ti].y;
+        }
+        const int t2 = tlo2 + ti;
+        if (qrow && t2 >= g.lo[2] && t2 < g.lo[2] + n2) quad[mode_index(g, t0, t1, t2)] = make_double2(qx, qy);
+        if (cubic) S[(size_t)blockIdx.x * nT2 + ti] = make_double2(rx, ry);
     }
 }
 
@@ -872,7 +1072,7 @@ struct NdRound {
 struct NdPlan {
     NdGeo g{};
     int RW = 8, threads = 256, T0 = 1, nCTA = 0;
-    int PB = 0, PS = 0, PP = 0;
+    int WS = 0, PB = 0, PS = 0, PP = 0, GP = 0;
     size_t smem = 0, smem_pair = 0;
     int TXp = 4;
     int pair_threads = 256;
@@ -885,9 +1085,19 @@ struct NdPlan {
     double2* quad = nullptr;
     double2* S = nullptr;
     double2* q1q = nullptr;
+    void* Wq = nullptr;               // pair weight tables [x][y] over I_N x I_N (when they fit)
+    void* Wr = nullptr;
+    size_t W_bytes = 0;
     bool resident = false;            // slices produced once and kept (single round)
     bool produced = false;
     double terms = 0;                 // Q_{1,q} terms per evaluation
+    // live phase timing: per evaluation slot, events around the pair sums, each round's slice
+    // production and sweep, and the tail (partial sums, reducible convolution, combination)
+    static constexpr int kSlots = 4;
+    std::vector<cudaEvent_t> ev;      // kSlots x (4 + 4 rounds)
+    double ms[4] = {0, 0, 0, 0};      // pair, production, sweep, tail
+    long long evals = 0;
+    int per_slot() const { return 4 + 4 * (int)rounds.size(); }
 };
 
 namespace {
@@ -945,8 +1155,12 @@ void free_nd(bn_solver* s) {
         cudaFree(r.d_groups); cudaFree(r.d_group_b); cudaFree(r.d_off16); cudaFree(r.d_work);
         cudaFree(r.d_items); cudaFree(r.d_cta_off);
     }
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(p->slices);
     cudaFree(p->partials);
+    cudaFree(p->Wq);
+    cudaFree(p->Wr);
     cudaFree(p->quad);
     cudaFree(p->S);
     cudaFree(p->q1q);
@@ -954,13 +1168,45 @@ void free_nd(bn_solver* s) {
     s->nd = nullptr;
 }
 
-template <typename Real, int RW>
+template <typename Real>
 static void configure_triple_nd(size_t smem) {
-    cudaFuncSetAttribute(k_triple_nd<Real, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_triple_nd<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 template <typename Real, int TX>
 static void configure_pair_nd(size_t smem) {
     cudaFuncSetAttribute(k_pair_nd<Real, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Work split of the boxes of one b (host): outputs per thread along axis 2 (RW), output planes per
+// item (T0), output rows per tile (L1t) and lanes per task splitting the s_1 range (J), chosen to
+// minimise a per-thread time model of the sweep: per item and tile, (T0 + S0 - 1) plane steps of
+// ceil(S1 / J) rows of S2 steps of RW paired multiply-adds, plus per-row, per-plane and per-item
+// overheads (instruction counts of the kernel's row setup, plane barrier and item setup).
+struct ItemShape { int RW, T0, J, L1t; };
+constexpr long long kRowOvh = 24, kPlaneOvh = 200, kTileOvh = 1500;
+static long long shape_cost(const Box3& B, int T0, const ItemShape& sh) {
+    const long long ntile = (B.L[1] + sh.L1t - 1) / sh.L1t;
+    const long long rows = (B.S[1] + sh.J - 1) / sh.J;
+    return ntile * ((T0 + B.S[0] - 1) * (rows * ((long long)B.S[2] * sh.RW + kRowOvh) + kPlaneOvh) + kTileOvh);
+}
+static ItemShape choose_shape(const Box3& B, bool fp32, int T0max, int nthr) {
+    ItemShape best{fp32 ? 8 : 4, 1, 1, 1};
+    long long bestc = -1;
+    const int rws[2] = {8, 4};
+    for (int ri = fp32 ? 0 : 1; ri < 2; ++ri) {
+        const int RW = rws[ri];
+        const int G2 = (B.L[2] + RW - 1) / RW;
+        for (int T0 = 1; T0 <= std::min(T0max, B.L[0]); ++T0)
+            for (int J = 1; J <= 8 && J <= B.S[1]; J *= 2) {
+                const int maxL1 = nthr / (T0 * G2 * J);
+                if (maxL1 < 1) continue;
+                const int ntile = (B.L[1] + maxL1 - 1) / maxL1;
+                const ItemShape sh{RW, T0, J, (B.L[1] + ntile - 1) / ntile};
+                const long long c = ((B.L[0] + T0 - 1) / T0) * shape_cost(B, T0, sh);
+                if (bestc < 0 || c < bestc) { bestc = c; best = sh; }
+            }
+    }
+    return best;
 }
 
 bn_status plan_nd(bn_solver* s, std::string* err) {
@@ -971,32 +1217,28 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     const bool fp32 = s->opt.precision == BN_MIXED;
     const int elem = fp32 ? 4 : 8;
     const int N = g.N;
-    // outputs per thread along axis 2: 8 (FP32), 4 (FP64; 8 when one plane would need more than
-    // 512 threads)
-    p->RW = fp32 ? 8 : (g.n[1] * ((g.n[2] + 3) / 4) > 512 ? 8 : 4);
+    // 256 threads per CTA; per box, outputs per thread along axis 2 (RW = 8 or 4 in FP32, 4 in
+    // FP64), planes per item (T0 <= T0max) and s_1 split (J) are chosen on the host below
+    p->RW = fp32 ? 8 : 4;                    // the widest RW (sizes the staged row slack)
     const int RW = p->RW;
-    // outputs per CTA: T0 planes of L1 x ceil(L2/RW) tasks, up to 256 threads (more when one plane
-    // alone needs more: N = 48 has 48 x 6 tasks per plane)
-    const int perPlane = g.n[1] * ((g.n[2] + RW - 1) / RW);
-    p->T0 = std::max(1, std::min(g.n[0], 256 / perPlane));
-    p->threads = std::max(64, (p->T0 * perPlane + 31) / 32 * 32);
-    if (p->threads > 512) {
-        *err = "operator size beyond the 3-D kernel's thread limit";
-        return BN_ERR_UNSUPPORTED;
-    }
-    // largest slice plane and P plane
-    int maxA1 = 1, maxRS = 1, maxS1 = 1, maxS2 = 1;
+    p->T0 = N > 32 ? 1 : 3;                  // T0max: the P-plane ring holds T0max + 1 planes
+    p->threads = 256;
+    // largest slice plane and P plane; staged rows at odd strides (distinct banks for the rows a
+    // warp sweeps)
+    int maxA1 = 1, maxA2 = 1, maxS1 = 1, maxS2 = 1;
     for (int x = 1; x < 3; ++x) {
         const int Amax = g.wrap ? 2 * g.n[x] - 1 : (g.n[x] == 1 ? 1 : 2 * N - 2);
         const int Smax = g.n[x];   // box_s(b) spans all of I_x at b = -1 (LINEAR) and always (CIRCULAR)
         if (x == 1) { maxA1 = Amax; maxS1 = Smax; }
-        else { maxRS = slice_rs(Amax, elem); maxS2 = Smax; }
+        else { maxA2 = Amax; maxS2 = Smax; }
     }
-    p->PB = maxA1 * maxRS + RW;
-    p->PS = maxS2;
-    p->PP = maxS1 * maxS2;
+    p->WS = (maxA2 + RW - 1) | 1;
+    p->PB = maxA1 * p->WS + RW;
+    p->PS = maxS2 | 1;
+    p->PP = maxS1 * p->PS;
+    p->GP = g.n[0] > 1 ? g.n[1] * g.n[2] : 0;
     const size_t Csz = 2 * (size_t)elem;
-    p->smem = 2 * (size_t)p->PB * elem + (size_t)(p->T0 + 1) * p->PP * Csz + 16;
+    p->smem = 4 * (size_t)p->GP * Csz + (size_t)(p->T0 + 1) * p->PP * Csz + 2 * (size_t)p->PB * elem;
     p->smem = (p->smem + 15) / 16 * 16 + 16;
     if (p->smem > 227 * 1024) {
         *err = "the 3-D kernel's staging does not fit in shared memory";
@@ -1007,14 +1249,11 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     if (sms <= 0) sms = 152;
     int per_sm = 0;
     if (fp32) {
-        configure_triple_nd<float, 8>(p->smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<float, 8>, p->threads, p->smem);
-    } else if (RW == 4) {
-        configure_triple_nd<double, 4>(p->smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double, 4>, p->threads, p->smem);
+        configure_triple_nd<float>(p->smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<float>, p->threads, p->smem);
     } else {
-        configure_triple_nd<double, 8>(p->smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double, 8>, p->threads, p->smem);
+        configure_triple_nd<double>(p->smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double>, p->threads, p->smem);
     }
     cudaGetLastError();
     per_sm = std::max(1, per_sm);
@@ -1074,10 +1313,30 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     size_t total = 0;
     for (auto& mem : members)
         for (int f : mem) total += (slice_bytes(f) + 15) / 16 * 16;
-    // slice buffer: everything when it fits the budget (then produced once if resident), else rounds
+    // pair weight tables wq, wr over I_N x I_N: formed once when they fit in 45% of the free memory
+    // (8.6 GB FP32 at 3-D N = 32), else recomputed from the alpha tables at every evaluation
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
     cudaGetLastError();
+    {
+        const size_t nmS = (size_t)g.n[0] * g.n[1] * g.n[2];
+        const size_t one = nmS * nmS * (size_t)elem;
+        const size_t need = one * (s->eps != 0.0 ? 2 : 1);
+        if (s->opt.pair_weights == 0 && need <= (size_t)(0.45 * (double)freeb)) {
+            cudaError_t e1 = cudaMalloc(&p->Wq, one);
+            if (e1 == cudaSuccess && s->eps != 0.0) e1 = cudaMalloc(&p->Wr, one);
+            if (e1 != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(p->Wq);
+                cudaFree(p->Wr);
+                p->Wq = p->Wr = nullptr;
+            } else {
+                p->W_bytes = need;
+                freeb = freeb > need ? freeb - need : 0;
+            }
+        }
+    }
+    // slice buffer: everything when it fits the budget (then produced once if resident), else rounds
     size_t budget = s->opt.beta_budget_mb > 0 ? (size_t)s->opt.beta_budget_mb << 20
                                               : std::min<size_t>((size_t)(0.4 * (double)freeb), (size_t)40 << 30);
     budget = std::max<size_t>(budget, (size_t)64 << 20);
@@ -1136,14 +1395,19 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
                     b_of_flat(g, f, b);
                     Box3 B;
                     box_of(g, b, B);
-                    for (int t = 0; t < B.L[0]; t += T0) {
-                        const int tn = std::min(T0, B.L[0] - t);
-                        NdItem it;
-                        it.w0 = (uint32_t)f | ((uint32_t)t << 20) | ((uint32_t)tn << 26);
+                    const ItemShape sh = choose_shape(B, fp32, T0, p->threads);
+                    for (int t = 0; t < B.L[0]; t += sh.T0) {
+                        const int tn = std::min(sh.T0, B.L[0] - t);
+                        NdItem it{};
+                        it.bflat = (uint32_t)f;
+                        it.t0i = (uint8_t)t;
+                        it.T0 = (uint8_t)tn;
+                        it.L1t = (uint8_t)sh.L1t;
+                        it.J = (uint8_t)sh.J;
+                        it.RW = (uint8_t)sh.RW;
                         it.off16 = (uint32_t)(cur / 16);
                         const long long terms = (long long)tn * B.L[1] * B.L[2] * B.S[0] * B.S[1] * B.S[2];
-                        const long long cost = terms + 2000LL * (tn + B.S[0]) + 20000;
-                        items.push_back({cost, it});
+                        items.push_back({shape_cost(B, tn, sh), it});
                         p->terms += (double)terms;
                     }
                     cur += (slice_bytes(f) + 15) / 16 * 16;
@@ -1255,9 +1519,19 @@ bn_status build_nd_tables(bn_solver* s, KernelTables* t, std::string* err) {
 }
 
 // The whole operator from s->Ghat (and s->Ghat32) into s->Qhat.
-template <typename Real, int RW>
-static void launch_nd_t(bn_solver* s, cudaStream_t st, unsigned long long* stamps) {
+template <typename Real>
+static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
     NdPlan* p = s->nd;
+    unsigned long long* stamps = nullptr;
+    cudaEvent_t* ev = (slot >= 0 && slot < NdPlan::kSlots && (int)p->ev.size() == NdPlan::kSlots * p->per_slot())
+                          ? p->ev.data() + (size_t)slot * p->per_slot()
+                          : nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (ev) cudaStreamIsCapturing(st, &cap);
+    auto mark = [&](int i) {
+        // inside a stream capture the record must be an external event node to be timeable
+        if (ev) cudaEventRecordWithFlags(ev[i], st, cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0);
+    };
     const NdGeo& g = p->g;
     const KernelTables* t = s->tabs;
     const size_t nm = (size_t)s->g.nModes;
@@ -1276,26 +1550,38 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, unsigned long long* stamp
     PA.quad = p->quad;
     PA.S = p->S;
     PA.cubic = cubic;
+    PA.Wq = PA.Wr = nullptr;
     for (int x = 0; x < 3; ++x) { PA.nt[x] = p->nt[x]; PA.tlo[x] = p->tlo[x]; }
     // LINEAR without the cubic part needs only the t rows inside I_N, but the kernel is cheap
     const int nrows = p->nt[0] * p->nt[1];
     const int pthreads = p->pair_threads;
+    mark(0);
+    if (p->Wq) {
+        k_pairw_nd<Real><<<nrows, 256, 0, st>>>(g, (const Real*)p->Wq, (const Real*)p->Wr, G, p->quad, p->S, cubic,
+                                                p->nt[1], p->nt[2], p->tlo[0], p->tlo[1], p->tlo[2]);
+    } else
     if constexpr (sizeof(Real) == 4) {
         if (p->TXp == 6) k_pair_nd<Real, 6><<<nrows, pthreads, p->smem_pair, st>>>(PA);
         else k_pair_nd<Real, 4><<<nrows, pthreads, p->smem_pair, st>>>(PA);
     } else {
         k_pair_nd<Real, 4><<<nrows, pthreads, p->smem_pair, st>>>(PA);
     }
+    PA.Wq = PA.Wr = nullptr;
     s->launches++;
+    mark(1);
     if (cubic) {
         cudaMemsetAsync(p->partials, 0, p->partial_bytes, st);
-        for (const NdRound& R : p->rounds) {
+        for (size_t r = 0; r < p->rounds.size(); ++r) {
+            const NdRound& R = p->rounds[r];
+            mark(4 + 4 * (int)r);
             if (!(p->resident && p->produced)) {
                 k_beta_slices<Real><<<R.nwork, 256, 0, st>>>(g, t->P, fp32 ? (const Real*)t->alpha32 : (const Real*)t->alpha64,
                                                              fp32 ? (const Real*)t->alphap32 : (const Real*)t->alphap64,
                                                              R.d_groups, R.d_group_b, R.d_off16, R.d_work, (Real*)p->slices);
                 s->launches++;
             }
+            mark(5 + 4 * (int)r);
+            mark(6 + 4 * (int)r);
             TripleNdArgs TA;
             TA.g = g;
             TA.G = G;
@@ -1304,34 +1590,129 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, unsigned long long* stamp
             TA.slices = p->slices;
             TA.partials = p->partials;
             TA.err = s->flags + 2;
+            TA.WS = p->WS;
             TA.PB = p->PB;
             TA.PS = p->PS;
             TA.PP = p->PP;
+            TA.GP = p->GP;
             TA.T0max = p->T0;
             TA.stamps = stamps;
-            k_triple_nd<Real, RW><<<p->nCTA, p->threads, p->smem, st>>>(TA);
+            k_triple_nd<Real><<<p->nCTA, p->threads, p->smem, st>>>(TA);
             s->launches++;
+            mark(7 + 4 * (int)r);
         }
         if (p->resident) p->produced = true;
         if (fp32) k_sum_partials_nd<float><<<(int)((nm + kPartModes - 1) / kPartModes), 256, 0, st>>>((int)nm, p->nCTA, p->partials, p->q1q);
         else k_sum_partials_nd<double><<<(int)std::min<size_t>((nm + 255) / 256, 4096), 256, 0, st>>>((int)nm, p->nCTA, p->partials, p->q1q);
         s->launches++;
     }
+    mark(2);
     k_red_combine_nd<<<g.n[0] * g.n[1], 256, 0, st>>>(g, s->eps, cubic, s->Ghat, p->quad, p->q1q, p->S, p->nt[0], p->nt[1],
                                                        p->nt[2], p->tlo[0], p->tlo[1], p->tlo[2], s->Qhat);
     s->launches++;
+    mark(3);
 }
 
-void launch_nd(bn_solver* s, unsigned long long* stamps) {
-    if (s->opt.precision == BN_MIXED) launch_nd_t<float, 8>(s, s->stream, stamps);
-    else if (s->nd->RW == 4) launch_nd_t<double, 4>(s, s->stream, stamps);
-    else launch_nd_t<double, 8>(s, s->stream, stamps);
+void launch_nd(bn_solver* s, int slot) {
+    if (s->opt.precision == BN_MIXED) launch_nd_t<float>(s, s->stream, slot);
+    else launch_nd_t<double>(s, s->stream, slot);
 }
 
-// Produce the slices once (resident mode), outside any capture.
+bn_status nd_profile_enable(bn_solver* s, bool on) {
+    NdPlan* p = s->nd;
+    if (!p) return BN_OK;
+    if (on && p->ev.empty()) {
+        p->ev.assign((size_t)NdPlan::kSlots * p->per_slot(), nullptr);
+        for (cudaEvent_t& e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return BN_ERR_CUDA;
+            }
+    }
+    for (double& m : p->ms) m = 0;
+    p->evals = 0;
+    return BN_OK;
+}
+
+// Add the phase times of the evaluation slots recorded since the last harvest (the stream has
+// been synchronised).
+void nd_profile_harvest(bn_solver* s, int slots) {
+    NdPlan* p = s->nd;
+    if (!p || p->ev.empty()) return;
+    const int ps = p->per_slot();
+    for (int k = 0; k < slots && k < NdPlan::kSlots; ++k) {
+        cudaEvent_t* e = p->ev.data() + (size_t)k * ps;
+        float a = 0, b = 0, c = 0, d = 0;
+        if (cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess) { cudaGetLastError(); continue; }
+        for (size_t r = 0; r < p->rounds.size() && s->eps != 0.0; ++r) {
+            float x = 0, y = 0;
+            if (cudaEventElapsedTime(&x, e[4 + 4 * r], e[5 + 4 * r]) == cudaSuccess) b += x;
+            else cudaGetLastError();
+            if (cudaEventElapsedTime(&y, e[6 + 4 * r], e[7 + 4 * r]) == cudaSuccess) c += y;
+            else cudaGetLastError();
+        }
+        if (cudaEventElapsedTime(&d, s->eps != 0.0 ? e[7 + 4 * (p->rounds.size() - 1)] : e[1], e[3]) != cudaSuccess) {
+            cudaGetLastError();
+            d = 0;
+        }
+        p->ms[0] += a; p->ms[1] += b; p->ms[2] += c; p->ms[3] += d;
+        p->evals += 1;
+    }
+}
+
+bn_status nd_profile_read(bn_solver* s, double* out, size_t count) {
+    NdPlan* p = s->nd;
+    if (!p || count < 8) return BN_ERR_ARG;
+    for (int i = 0; i < 4; ++i) out[i] = p->ms[i];
+    out[4] = (double)p->evals;
+    out[5] = (double)p->rounds.size();
+    out[6] = p->terms;
+    out[7] = (double)p->nCTA;
+    for (double& m : p->ms) m = 0;
+    p->evals = 0;
+    return BN_OK;
+}
+
+template <typename Real>
+static void build_pair_weights(bn_solver* s) {
+    NdPlan* p = s->nd;
+    const KernelTables* t = s->tabs;
+    const bool fp32 = sizeof(Real) == 4;
+    PairNdArgs PA;
+    PA.g = p->g;
+    PA.P = t->P;
+    PA.alphaI = fp32 ? (const void*)t->alphaI32 : (const void*)t->alphaI64;
+    PA.alphapI = fp32 ? (const void*)t->alphapI32 : (const void*)t->alphapI64;
+    PA.alphaE = fp32 ? (const void*)t->alpha32 : (const void*)t->alpha64;
+    PA.alphapE = fp32 ? (const void*)t->alphap32 : (const void*)t->alphap64;
+    PA.G = nullptr;
+    PA.quad = p->quad;
+    PA.S = p->S;
+    PA.cubic = s->eps != 0.0;
+    PA.Wq = p->Wq;
+    PA.Wr = p->Wr;
+    for (int x = 0; x < 3; ++x) { PA.nt[x] = p->nt[x]; PA.tlo[x] = p->tlo[x]; }
+    const int nrows = p->nt[0] * p->nt[1];
+    if constexpr (sizeof(Real) == 4) {
+        if (p->TXp == 6) k_pair_nd<Real, 6><<<nrows, p->pair_threads, p->smem_pair, s->stream>>>(PA);
+        else k_pair_nd<Real, 4><<<nrows, p->pair_threads, p->smem_pair, s->stream>>>(PA);
+    } else {
+        k_pair_nd<Real, 4><<<nrows, p->pair_threads, p->smem_pair, s->stream>>>(PA);
+    }
+    s->launches++;
+}
+
+// Form the pair weight tables (when allocated) and, in resident mode, the slices, once, outside
+// any capture.
 bn_status prepare_nd(bn_solver* s) {
     NdPlan* p = s->nd;
-    if (!p || !p->resident || p->produced || s->eps == 0.0) return BN_OK;
+    if (!p) return BN_OK;
+    if (p->Wq) {
+        if (s->opt.precision == BN_MIXED) build_pair_weights<float>(s);
+        else build_pair_weights<double>(s);
+        if (cudaGetLastError() != cudaSuccess) return BN_ERR_CUDA;
+    }
+    if (!p->resident || p->produced || s->eps == 0.0) return BN_OK;
     const bool fp32 = s->opt.precision == BN_MIXED;
     const KernelTables* t = s->tabs;
     const NdRound& R = p->rounds[0];

@@ -231,6 +231,19 @@ def test_3d_rounds_resident_and_determinism(B):
         assert np.abs(c1 - a).max() <= tol * np.abs(a).max()
 
 
+@pytest.mark.parametrize("d,wrap", [(3, 0), (2, 1)])
+def test_pair_weight_tables_equal_recomputed_weights(B, d, wrap):
+    """The quadratic and reducible pair sums from the weight tables formed once and from weights
+    recomputed at every evaluation: the same weights, summed in a different order."""
+    N = 8 if d == 3 else 16
+    f = _f(d, N, 19)
+    kw = dict(M1=4, M2=4) if d == 3 else dict(M=2 * N)
+    for precision, tol in (("fp64", 1e-13), ("mixed", 1e-6)):
+        a = _gpu_modes(B, d, N, -1.0, f, precision, wrap=wrap, **kw)
+        b = _gpu_modes(B, d, N, -1.0, f, precision, wrap=wrap, pair_weights=1, **kw)
+        assert np.abs(a - b).max() <= tol * np.abs(a).max()
+
+
 def test_3d_escalation_rebuilds_the_plan(B):
     N, eps, dt = 8, 1.0, 0.01
     f = _f(3, N, 17)
