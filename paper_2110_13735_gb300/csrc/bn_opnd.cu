@@ -17,22 +17,26 @@
 // d-dimensional Toeplitz product of the kernel-mode slice beta(., b) with P_b.
 //
 // Kernels, per evaluation:
-//  * k_pair_nd: quad and S.  One CTA per row (t_0, t_1) of t = x + y; the weights of a tile of
-//    (x_2, y_2) pairs are summed over the quadrature nodes from the alpha tables (a small dense
-//    contraction per tile), multiplied by G^_x G^_y and reduced along the anti-diagonals in a fixed
-//    order.
+//  * k_pairw_nd (or k_pair_nd): quad and S.  Their weights over I_N x I_N, wq = beta(x,y) -
+//    beta(y,y) and wr = beta(x,y) - beta(t,x) - beta(x,t), are formed once per solver by k_pair_nd
+//    (a small dense contraction over the quadrature nodes per tile) into tables when they fit in
+//    memory, and k_pairw_nd streams them; otherwise k_pair_nd forms them at every evaluation.
+//    One CTA per row (t_0, t_1) of t = x + y; sums in a fixed order, accumulated in FP64.
 //  * k_beta_slices: the slices beta(a, b) for a in the box A(b) of the differences n - s.  The b
 //    whose boxes coincide in the first two axes (and nearly in the third) form groups of up to 64;
 //    a group's slices are one contraction over the nodes (rows: a in the union box, columns: the
 //    group's b), register-tiled 4 x 8 per thread, written to a slice buffer in global memory.
 //    The slices of a "round" (as many groups as fit the buffer) are produced, then consumed.
-//  * k_triple_nd: the Toeplitz products.  A work item is (b, T0 consecutive output planes n_0);
-//    the CTA walks the planes a_0 of the slice, staging each plane with one bulk (TMA) copy and the
-//    P_b planes it meets in shared memory, and each thread sweeps RW consecutive outputs along
-//    axis 2 with a register window of weights (paired FP32 FMA in mixed precision).  The s_1 range
-//    may be split over J lanes (reduced by shuffles) when an item has few output rows.  C_b(n)
-//    times G^_{n-b} is added to the CTA's own partial sums in global memory (FP32 Kahan pairs or
-//    FP64); items are dealt to CTAs on the host, so every sum has a fixed order.
+//  * k_triple_nd: the Toeplitz products.  A work item is (b, T0 consecutive output planes n_0),
+//    swept in tiles of output rows n_1; the host chooses per box the planes per item, the rows per
+//    tile, the outputs per thread along axis 2 (RW = 4 or 8) and the split of the s_1 range over J
+//    lanes (reduced by shuffles), by a cost model of the per-thread work.  The CTA walks the planes
+//    a_0 of the slice: the rows a tile needs are copied into shared memory (odd row stride) while
+//    the previous plane is swept, and each P_b plane is formed from two mode planes fetched by a
+//    bulk (TMA) copy one step earlier.  Each thread sweeps its RW outputs with a register window of
+//    weights and scalar FP32 FMA (FP64 in FP64 mode).  C_b(n) times G^_{n-b} is added to the CTA's
+//    own partial sums in global memory (FP32 Kahan pairs or FP64); items are dealt to CTAs on the
+//    host, so every sum has a fixed order.
 //  * k_sum_partials_nd, then k_red_combine_nd: Q1q from the partials, red(n), and Q^.
 #include <algorithm>
 #include <cmath>
@@ -259,41 +263,57 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// One row of the Toeplitz product in FP32: acc[r] += sum_{sl < S2} w[c0 + r - sl] P[sl], acc as
-// packed (re, im) pairs, the weights of the row in a rotating register window (slot of column x
-// is x mod RW), duplicated into pairs so that one paired FMA serves both halves of P.
+// One row of the Toeplitz product in FP32: acc[r] += sum_{sl < S2} w[c0 + r - sl] P[sl] for the RW
+// outputs r of a thread (acc[r] holds (re, im) as two floats), the weights of the row in a
+// rotating register window (slot of column x is x mod RW): per step one shared load of a weight,
+// one 64-bit load of P and 2 RW scalar FMAs.  (A paired-FMA form with the weights duplicated
+// into register pairs measured 14 % slower here: the duplication moves cost more issue slots
+// than the pairing saves.)
 template <int RW>
-__device__ __forceinline__ void sweep_row_f32(const float* __restrict__ brow, int c0, const uint64_t* __restrict__ prow,
-                                              int S2, uint64_t (&acc)[RW]) {
-    uint64_t w[RW];
+__device__ __forceinline__ void sweep_row_f32s(const float* __restrict__ brow, int c0, const float2* __restrict__ prow,
+                                               int S2, uint64_t (&accp)[RW]) {
+    float re[RW], im[RW];
 #pragma unroll
-    for (int r = 0; r < RW; ++r) w[r] = dup2(brow[c0 + r]);
+    for (int r = 0; r < RW; ++r) split2(accp[r], re[r], im[r]);
+    float w[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) w[r] = brow[c0 + r];
     int sl = 0;
     for (; sl + RW <= S2; sl += RW) {
 #pragma unroll
         for (int kk = 0; kk < RW; ++kk) {
             if (kk == 0) {
-                if (sl > 0) w[0] = dup2(brow[c0 - sl]);
+                if (sl > 0) w[0] = brow[c0 - sl];
             } else {
-                w[RW - kk] = dup2(brow[c0 - sl - kk]);
+                w[RW - kk] = brow[c0 - sl - kk];
             }
-            const uint64_t p = prow[sl + kk];
+            const float2 p = prow[sl + kk];
 #pragma unroll
-            for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
+            for (int r = 0; r < RW; ++r) {
+                const float ww = w[(r - kk + RW) % RW];
+                re[r] = fmaf(ww, p.x, re[r]);
+                im[r] = fmaf(ww, p.y, im[r]);
+            }
         }
     }
 #pragma unroll
     for (int kk = 0; kk < RW; ++kk) {
         if (sl + kk >= S2) break;
         if (kk == 0) {
-            if (sl > 0) w[0] = dup2(brow[c0 - sl]);
+            if (sl > 0) w[0] = brow[c0 - sl];
         } else {
-            w[RW - kk] = dup2(brow[c0 - sl - kk]);
+            w[RW - kk] = brow[c0 - sl - kk];
         }
-        const uint64_t p = prow[sl + kk];
+        const float2 p = prow[sl + kk];
 #pragma unroll
-        for (int r = 0; r < RW; ++r) acc[r] = fma2(w[(r - kk + RW) % RW], p, acc[r]);
+        for (int r = 0; r < RW; ++r) {
+            const float ww = w[(r - kk + RW) % RW];
+            re[r] = fmaf(ww, p.x, re[r]);
+            im[r] = fmaf(ww, p.y, im[r]);
+        }
     }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) accp[r] = pack2(re[r], im[r]);
 }
 
 // The same in FP64 (acc[r] = (re, im)).
@@ -529,12 +549,14 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
                 for (int s1 = s1a; s1 < s1b; ++s1) {
                     const Real* brow = plane + (size_t)(rowoff - s1) * A.WS;
                     const C* prow = pplane + (size_t)(s1 - B.slo[1]) * A.PS;
-                    if constexpr (sizeof(Real) == 4)
-                        sweep_row_f32<RW>(reinterpret_cast<const float*>(brow), c0,
-                                          reinterpret_cast<const uint64_t*>(prow), B.S[2], acc32);
-                    else
+                    if constexpr (sizeof(Real) == 4) {
+                        sweep_row_f32s<RW>(reinterpret_cast<const float*>(brow), c0,
+                                           reinterpret_cast<const float2*>(prow), B.S[2], acc32);
+                    }
+                    else {
                         sweep_row_f64<RW>(reinterpret_cast<const double*>(brow), c0,
                                           reinterpret_cast<const double2*>(prow), B.S[2], acc64);
+                    }
                 }
                 if constexpr (sizeof(Real) == 4) {
                     // compensated accumulation of the plane's sums
