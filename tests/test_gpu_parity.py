@@ -283,6 +283,16 @@ def test_bench_workload_step_vs_oracle(B):
             s.close()
 
 
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(N, eps, dt, nsteps, f0, key):
+    """The oracle's RK4 run, computed once per module (the BKW run takes ~30 s of CPU)."""
+    if key not in _ORACLE_RUNS:
+        _ORACLE_RUNS[key] = O.Operator(2, N, T6, R6, 0, eps, M=2 * N).step(f0, dt, nsteps, 0).reshape(N, N)
+    return _ORACLE_RUNS[key]
+
+
 @pytest.mark.parametrize("cfg", ["fermions_n16", "bkw_n32"])
 def test_full_run_against_oracle(B, cfg):
     """Whole runs of the small configurations against the oracle's run of the same RK4 steps:
@@ -293,7 +303,7 @@ def test_full_run_against_oracle(B, cfg):
         N, eps, dt, nsteps, f0 = 16, -1.0, 0.01, 200, I.config0_f0(16, R6)
     else:
         N, eps, dt, nsteps, f0 = 32, 0.0, 0.005, 800, I.config1_bkw_f0(32, R6)
-    ref = O.Operator(2, N, T6, R6, 0, eps, M=2 * N).step(f0, dt, nsteps, 0).reshape(N, N)
+    ref = _oracle_run(N, eps, dt, nsteps, f0, cfg)
     for precision, tol in ((B.FP64, 1e-12), (B.MIXED, 1e-6)):
         with B.Solver(2, N, T6, R6, B.MAXWELL, eps, precision=precision) as s:
             s.set_state(f0)
@@ -304,3 +314,71 @@ def test_full_run_against_oracle(B, cfg):
         print(f"{cfg} {'fp64' if precision == B.FP64 else 'mixed'}: e_f = {err:.3e} after {nsteps} steps")
         assert t_end == pytest.approx(nsteps * dt, rel=1e-12)
         assert err <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_modes_parity_2d_n64_corners_and_edges(B, precision, tol):
+    """Full-size 2-D N=64, the mixed N > 32 kernel and the FP64 kernel: GPU modes against the oracle
+    (modes evaluated one by one) on 4x4 blocks at two corners of I_N, on an edge and at the centre,
+    where the boxes of the triple sum clip differently.  Normalised by the gain modes of the blocks."""
+    N, eps = 64, 1.0
+    f = I.two_gaussians(2, N, T6, 1.0, (1.5, 0.5), 0.8)
+    ora = O.Operator(2, N, T6, R6, 0, eps, M=2 * N)
+    Gh = ora.dft(f)
+    starts = [(-32, -32), (28, 28), (-32, -2), (28, -32), (-2, -2)]
+    nl = np.array([(a + i, b + j) for a, b in starts for i in range(4) for j in range(4)], dtype=np.int32)
+    Qo, gain_o, _, _ = ora.collision_modes_at(Gh, nl)
+    prec = B.FP64 if precision == "fp64" else B.MIXED
+    with B.Solver(2, N, T6, R6, B.MAXWELL, eps, precision=prec) as s:
+        s.set_state(f)
+        Qg = s.eval_collision_modes()
+    Qg_s = np.array([Qg[n[0] + N // 2, n[1] + N // 2] for n in nl])
+    err = float(np.linalg.norm(Qg_s - Qo) / np.linalg.norm(gain_o))
+    print(f"2-D N=64 {precision} corner/edge/centre blocks ({len(nl)} modes): e_Q = {err:.3e}")
+    assert err <= tol
+
+
+def test_bkw_run_against_the_closed_form(B):
+    """The classical BKW run (N = 32, eps = 0, t0 = 1 to t = 5, dt = 0.005) against the exact BKW
+    solution at t = 5 (literature; Maxwell molecules, C_Phi = 1/(2 pi)): the GPU states (FP64 and
+    mixed) are as close to it as the oracle's own Galerkin run, whose distance to the closed form is
+    the truncation error at N = 32."""
+    N, dt, nsteps = 32, 0.005, 800
+    f0 = I.config1_bkw_f0(N, R6)
+    v = I.grid(2, N, T6)
+    exact = I.bkw_2d(5.0, v)
+    ref = _oracle_run(N, 0.0, dt, nsteps, f0, "bkw_n32")
+    e_ora = rel(ref, exact, exact)
+    for precision in (B.FP64, B.MIXED):
+        with B.Solver(2, N, T6, R6, B.MAXWELL, 0.0, precision=precision) as s:
+            s.set_state(f0)
+            s.step_rk(dt, nsteps)
+            got = s.get_state().reshape(N, N)
+        e_gpu = rel(got, exact, exact)
+        print(f"BKW t=5 vs closed form: oracle {e_ora:.3e}, GPU {'fp64' if precision == B.FP64 else 'mixed'} {e_gpu:.3e}")
+        assert e_ora < 1e-2   # 5.1e-3: the Galerkin truncation error at N = 32
+        # |e_gpu - e_ora| <= ||f_gpu - f_oracle|| / ||f_exact||: the whole-run bounds
+        assert abs(e_gpu - e_ora) <= (1e-12 if precision == B.FP64 else 1e-6)
+
+
+def test_bosonic_configuration_run_mixed_vs_fp64(B):
+    """The bosonic Gaussian of the N = 32 configuration (mass 5, temperature 0.5, eps = +1, RK4
+    dt = 0.005) to t = 5 (1000 steps): the mixed-precision state against the FP64 state (reported;
+    bounded by 5e-6 -- the mixed error grows roughly linearly in time here), and the FP64 GPU run
+    against the oracle's run over the first 10 steps (1e-12)."""
+    N, dt = 32, 0.005
+    f0 = I.config1_boson_f0(N, R6)
+    ref10 = O.Operator(2, N, T6, R6, 0, 1.0, M=2 * N).step(f0, dt, 10, 0).reshape(N, N)
+    states = {}
+    for precision in (B.FP64, B.MIXED):
+        with B.Solver(2, N, T6, R6, B.MAXWELL, 1.0, precision=precision) as s:
+            s.set_state(f0)
+            s.step_rk(dt, 10)
+            if precision == B.FP64:
+                e10 = rel(s.get_state().reshape(N, N), ref10, ref10)
+            s.step_rk(dt, 990)
+            states[precision] = s.get_state().reshape(N, N)
+    e_mixed = rel(states[B.MIXED], states[B.FP64], states[B.FP64])
+    print(f"bosonic N=32 to t=5: mixed vs FP64 e_f = {e_mixed:.3e}; FP64 vs oracle after 10 steps {e10:.3e}")
+    assert e10 <= 1e-12
+    assert e_mixed <= 5e-6
