@@ -102,6 +102,16 @@ typedef struct {
                          sums over I_N x I_N once, when they fit in 45% of the free memory (the
                          default); 1 = recompute them from the quadrature factors at every
                          evaluation */
+    int shard_index, shard_count; /* 3-D and CIRCULAR, one evaluation split over shard_count
+                         solvers (one per GPU): with shard_count > 1, bn_eval_collision_modes returns
+                         the modes Q^_n of the output planes n_0 of shard shard_index of
+                         bn_plan_shards and zero elsewhere, so that the sum of the shard_count
+                         results (one all-reduce of N^d complex values) is Q^; bn_eval_collision and
+                         the stepping calls of such a solver return BN_ERR_UNSUPPORTED.  0 = none */
+    int debug_wait_polls; /* testing only: when > 0, the first bounded wait for a bulk copy in the
+                         operator kernels gives up after this many non-blocking polls, so that the
+                         call reports BN_ERR_TIMEOUT (the kernel still waits, bounded, for its copy
+                         before going on, and the next call starts clean); 0 = normal waits */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
@@ -263,6 +273,16 @@ bn_status bn_plan_mixed2d(int N, int rw, int oriented, int nblk, int* out, size_
  * The rate is that of the SM clock during the run: sample the clock alongside.
  */
 bn_status bn_measure_fma_peak(int kind, void* cuda_stream, double* out, size_t count);
+
+/*
+ * Partition of one 3-D evaluation over `count` GPUs (no GPU needed): the output planes n_0 of I_N
+ * (as indices n_0 + N/2) in contiguous ranges [bounds[r], bounds[r+1]), r < count, with nearly
+ * equal terms of the Q_{1,q} sum (the number of (k_0, l_0, m_0) in I_N^3 with k_0 + l_0 + m_0 = n_0
+ * per plane in the LINEAR truncation, equal planes in the CIRCULAR one).  The shards of a solver's
+ * shard_index / shard_count options.  bounds[0] = 0, bounds[count] = N.  BN_ERR_ARG unless d = 3,
+ * N even in [4, 48], wrap 0 or 1, 1 <= count <= N and nbounds >= count + 1.
+ */
+bn_status bn_plan_shards(int d, int N, int wrap, int count, int* bounds, size_t nbounds);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* bn_last_error(void);

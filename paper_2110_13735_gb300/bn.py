@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("conserve", ctypes.c_int), ("c_phi", ctypes.c_double), ("integrator", ctypes.c_int),
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
                 ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int), ("wrap", ctypes.c_int),
-                ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong), ("pair_weights", ctypes.c_int)]
+                ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong), ("pair_weights", ctypes.c_int),
+                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int), ("debug_wait_polls", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -77,6 +78,7 @@ def load(path: str | None = None):
     ip = ctypes.POINTER(ctypes.c_int)
     lib.bn_plan_mixed2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, sz, ip]
     lib.bn_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp, sz]
+    lib.bn_plan_shards.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), sz]
     lib.bn_kernel_launches.argtypes = [vp]
     lib.bn_kernel_launches.restype = ctypes.c_longlong
     lib.bn_last_error.restype = ctypes.c_char_p
@@ -132,12 +134,13 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
             escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0,
-            pair_weights=0) -> Options:
+            pair_weights=0, shard_index=0, shard_count=0, debug_wait_polls=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
     o.wrap, o.beta_resident, o.beta_budget_mb, o.pair_weights = wrap, beta_resident, beta_budget_mb, pair_weights
+    o.shard_index, o.shard_count, o.debug_wait_polls = shard_index, shard_count, debug_wait_polls
     return o
 
 
@@ -277,6 +280,15 @@ class Solver:
         out = np.zeros(4)
         _check(_lib.bn_profile_read(self._h, _dptr(out), 4))
         return float(out[0]), int(out[1]), float(out[2]), int(out[3])
+
+
+def plan_shards(d: int, N: int, count: int, wrap: int = 0) -> np.ndarray:
+    """Output-plane ranges of `count` shards of one evaluation (include/bn.h: bn_plan_shards); no GPU."""
+    lib = load()
+    out = np.zeros(count + 1, dtype=np.int32)
+    _check(lib.bn_plan_shards(int(d), int(N), int(wrap), int(count), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              out.size))
+    return out
 
 
 def measure_fma_peak(kind: int, stream=None):

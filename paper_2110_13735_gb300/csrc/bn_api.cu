@@ -262,6 +262,16 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(BN_ERR_ARG, "wrap must be 0 (LINEAR) or 1 (CIRCULAR)");
     }
+    if (s->opt.shard_count < 0 || (s->opt.shard_count > 1 && (d != 3 || s->opt.shard_index < 0 ||
+                                                                s->opt.shard_index >= s->opt.shard_count ||
+                                                                s->opt.shard_count > N))) {
+        delete s;
+        return fail(BN_ERR_ARG, "shards: 3-D only, 0 <= shard_index < shard_count <= N");
+    }
+    if (s->opt.debug_wait_polls < 0) {
+        delete s;
+        return fail(BN_ERR_ARG, "debug_wait_polls must be >= 0");
+    }
     if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1) ||
         (s->opt.pair_weights != 0 && s->opt.pair_weights != 1)) {
         delete s;
@@ -437,9 +447,11 @@ bn_status bn_eval_collision_device(bn_solver* s, const double* f_dev, double* Q_
 
 bn_status bn_eval_collision(bn_solver* s, double* Q, size_t count) {
     if (!valid_solver(s) || !Q) return fail(BN_ERR_ARG, "null argument");
+    if (s->opt.shard_count > 1) return fail(BN_ERR_UNSUPPORTED, "a shard solver returns modes only (bn_eval_collision_modes)");
     if (count != (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be N^d");
     if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
     s->prof_slot = 0;
+    cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);   // the wait-timeout flag of this call
     eval_device(s, s->f, s->Qv);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(Q, s->Qv, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -456,6 +468,7 @@ bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count) {
     if (count != 2 * (size_t)s->g.nModes) return fail(BN_ERR_ARG, "count must be 2 N^d");
     if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
     s->prof_slot = 0;
+    cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);   // the wait-timeout flag of this call
     eval_device(s, s->f, s->Qv);   // leaves the combined modes in s->Qhat
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(Qhat, s->Qhat, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -469,12 +482,13 @@ bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count) {
 
 bn_status bn_step_rk(bn_solver* s, double dt, int nsteps) {
     if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
+    if (s->opt.shard_count > 1) return fail(BN_ERR_UNSUPPORTED, "a shard solver does not step on its own");
     if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(BN_ERR_ARG, "dt must be > 0 and nsteps >= 0");
     if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
     if (nsteps == 0) return BN_OK;
     bn_status st = ensure_graph(s, dt);
     if (st != BN_OK) return st;
-    cudaError_t e = cudaMemsetAsync(s->flags, 0, 2 * sizeof(int), s->stream);
+    cudaError_t e = cudaMemsetAsync(s->flags, 0, 3 * sizeof(int), s->stream);   // incl. the wait-timeout flag
     if (e == cudaSuccess) e = cudaMemsetAsync(s->flags + 4, 0, 2 * sizeof(int), s->stream);
     for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
         e = cudaGraphLaunch(s->step_graph, s->stream);
@@ -600,6 +614,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
     for (int i = 0; i < n; ++i) {
         if (!solvers[i]) return fail(BN_ERR_ARG, "null solver in batch");
         if (!solvers[i]->has_state) return fail(BN_ERR_STATE, "solver in batch has no state");
+        if (solvers[i]->opt.shard_count > 1) return fail(BN_ERR_UNSUPPORTED, "a shard solver does not step on its own");
         if (!(dts[i] > 0) || !std::isfinite(dts[i])) return fail(BN_ERR_ARG, "dt must be > 0");
         for (int j = 0; j < i; ++j)
             if (solvers[j] == solvers[i]) return fail(BN_ERR_ARG, "a solver appears twice in the batch");
@@ -618,7 +633,7 @@ bn_status bn_step_rk_batch(bn_solver** solvers, int n, const double* dts, int ns
             cudaEventDestroy(ev);
         }
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaMemsetAsync(solvers[i]->flags, 0, 2 * sizeof(int), st0);
+        e = cudaMemsetAsync(solvers[i]->flags, 0, 3 * sizeof(int), st0);
         if (e == cudaSuccess) e = cudaMemsetAsync(solvers[i]->flags + 4, 0, 2 * sizeof(int), st0);
     }
     if (e != cudaSuccess) return cuda_fail(e, "step_rk_batch");
@@ -701,4 +716,13 @@ extern "C" bn_status bn_profile_nd(bn_solver* s, double* out, size_t count) {
     if (!valid_solver(s) || !out || count < 8) return fail(BN_ERR_ARG, "null solver/out or count < 8");
     if (!s->nd) return fail(BN_ERR_UNSUPPORTED, "bn_profile_nd: not a 3-D or CIRCULAR solver");
     return bn::nd_profile_read(s, out, count);
+}
+
+extern "C" bn_status bn_plan_shards(int d, int N, int wrap, int count, int* bounds, size_t nbounds) {
+    if (d != 3 || N < 4 || N > 48 || (N & 1) || (wrap != 0 && wrap != 1) || count < 1 || count > N || !bounds ||
+        nbounds < (size_t)count + 1)
+        return fail(BN_ERR_ARG, "bn_plan_shards: d = 3, N even in [4, 48], wrap 0/1, 1 <= count <= N, nbounds >= count + 1");
+    const std::vector<int> b = bn::shard_bounds_for(d, N, wrap, count);
+    for (int i = 0; i <= count; ++i) bounds[i] = b[i];
+    return BN_OK;
 }

@@ -373,6 +373,7 @@ struct TripleNdArgs {
     int PP;                   // complex entries per P plane buffer
     int GP;                   // complex entries per staged mode plane (n1 n2; 0 when axis 0 is trivial)
     int T0max;
+    unsigned int wait_first;      // testing: non-blocking polls of each tile's first bounded wait (0 = normal)
     unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
 };
 
@@ -535,8 +536,12 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
                 if (sNew <= shi0) {
                     const int sNext = sNew + 1;
                     if (a0 - 1 > aLo && sNext <= shi0) fetch_modes(sNext, k ^ 1);
-                    if (!nd_bar_wait(&bar[k], (phases >> k) & 1u)) {
+                    const bool first = a0 == aHi && A.wait_first;
+                    if (!(first ? mbar_test_polls(&bar[k], (phases >> k) & 1u, A.wait_first)
+                                : nd_bar_wait(&bar[k], (phases >> k) & 1u))) {
+                        // record it and wait (bounded) for the copy in flight before going on
                         if (tid == 0) atomicExch(A.err, 1);
+                        nd_bar_wait(&bar[k], (phases >> k) & 1u);
                     }
                     phases ^= 1u << k;
                     build_P(sNew, k);
@@ -1008,7 +1013,8 @@ __global__ void k_sum_partials_nd(int nm, int nPart, const void* __restrict__ pa
 __global__ void __launch_bounds__(256) k_red_combine_nd(NdGeo g, double eps, int cubic, const double2* __restrict__ G,
                                                         const double2* __restrict__ quad, const double2* __restrict__ q1q,
                                                         const double2* __restrict__ S, int nt0, int nt1, int nt2, int tlo0,
-                                                        int tlo1, int tlo2, double2* __restrict__ Qhat) {
+                                                        int tlo1, int tlo2, int plane_lo, int plane_hi,
+                                                        double2* __restrict__ Qhat) {
     __shared__ double2 red[8][64];
     const int n0 = g.lo[0] + (int)blockIdx.x / g.n[1], n1 = g.lo[1] + (int)blockIdx.x % g.n[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1055,7 +1061,9 @@ __global__ void __launch_bounds__(256) k_red_combine_nd(NdGeo g, double eps, int
             q.x += eps * (q1q[m].x + rx);
             q.y += eps * (q1q[m].y + ry);
         }
-        Qhat[m] = q;
+        // a shard writes its own output planes n_0 only
+        const bool mine = n0 - g.lo[0] >= plane_lo && n0 - g.lo[0] < plane_hi;
+        Qhat[m] = mine ? q : make_double2(0.0, 0.0);
     }
 }
 
@@ -1110,6 +1118,7 @@ struct NdPlan {
     void* Wq = nullptr;               // pair weight tables [x][y] over I_N x I_N (when they fit)
     void* Wr = nullptr;
     size_t W_bytes = 0;
+    int plane_lo = 0, plane_hi = 1 << 30;   // output planes n_0 - lo_0 of this shard
     bool resident = false;            // slices produced once and kept (single round)
     bool produced = false;
     double terms = 0;                 // Q_{1,q} terms per evaluation
@@ -1199,6 +1208,43 @@ static void configure_pair_nd(size_t smem) {
     cudaFuncSetAttribute(k_pair_nd<Real, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Output planes n_0 (as indices 0 .. n_0 - 1) of `count` shards of one evaluation: contiguous
+// ranges with nearly equal Q_{1,q} terms.  The terms of plane n_0 are w(n_0) = sum over b_0 with
+// n_0 in box_n(b_0) of |box_s(b_0)| (times the same factor for every plane), i.e. the number of
+// (k_0, l_0, m_0) in I^3 with k_0 + l_0 + m_0 = n_0 (LINEAR; every plane alike in CIRCULAR).
+std::vector<int> shard_bounds(const NdGeo& g, int count) {
+    const int n0 = g.n[0];
+    std::vector<double> w(n0, 0.0);
+    for (int b0 = g.blo[0]; b0 < g.blo[0] + g.nb[0]; ++b0) {
+        const int bb[3] = {b0, 0, 0};
+        Box3 B;
+        box_of(g, bb, B);
+        for (int i = 0; i < B.L[0]; ++i) w[B.nlo[0] + i - g.lo[0]] += B.S[0];
+    }
+    double total = 0;
+    for (double x : w) total += x;
+    std::vector<int> bounds(count + 1, n0);
+    bounds[0] = 0;
+    double acc = 0;
+    int k = 1;
+    for (int i = 0; i < n0 && k < count; ++i) {
+        acc += w[i];
+        // close shard k-1 after the plane that brings it nearest to its share
+        if (acc >= total * k / count - 0.5 * w[i]) bounds[k++] = i + 1;
+    }
+    for (; k < count; ++k) bounds[k] = n0;
+    for (int i = 1; i <= count; ++i) bounds[i] = std::max(bounds[i], bounds[i - 1]);
+    return bounds;
+}
+
+std::vector<int> shard_bounds_for(int d, int N, int wrap, int count) {
+    bn_solver tmp;
+    tmp.g.d = d;
+    tmp.g.N = N;
+    tmp.opt.wrap = wrap;
+    return shard_bounds(make_geo(&tmp), count);
+}
+
 // Work split of the boxes of one b (host): outputs per thread along axis 2 (RW), output planes per
 // item (T0), output rows per tile (L1t) and lanes per task splitting the s_1 range (J), chosen to
 // minimise a per-thread time model of the sweep: per item and tile, (T0 + S0 - 1) plane steps of
@@ -1239,6 +1285,14 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     const bool fp32 = s->opt.precision == BN_MIXED;
     const int elem = fp32 ? 4 : 8;
     const int N = g.N;
+    if (s->opt.shard_count > 1) {
+        const std::vector<int> bd = shard_bounds(g, s->opt.shard_count);
+        p->plane_lo = bd[s->opt.shard_index];
+        p->plane_hi = bd[s->opt.shard_index + 1];
+    } else {
+        p->plane_lo = 0;
+        p->plane_hi = g.n[0];
+    }
     // 256 threads per CTA; per box, outputs per thread along axis 2 (RW = 8 or 4 in FP32, 4 in
     // FP64), planes per item (T0 <= T0max) and s_1 split (J) are chosen on the host below
     p->RW = fp32 ? 8 : 4;                    // the widest RW (sizes the staged row slack)
@@ -1418,8 +1472,11 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
                     Box3 B;
                     box_of(g, b, B);
                     const ItemShape sh = choose_shape(B, fp32, T0, p->threads);
-                    for (int t = 0; t < B.L[0]; t += sh.T0) {
-                        const int tn = std::min(sh.T0, B.L[0] - t);
+                    // output planes of this shard inside box_n(b) along axis 0
+                    const int tb = std::max(0, p->plane_lo + g.lo[0] - B.nlo[0]);
+                    const int te = std::min(B.L[0], p->plane_hi + g.lo[0] - B.nlo[0]);
+                    for (int t = tb; t < te; t += sh.T0) {
+                        const int tn = std::min(sh.T0, te - t);
                         NdItem it{};
                         it.bflat = (uint32_t)f;
                         it.t0i = (uint8_t)t;
@@ -1612,6 +1669,7 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
             TA.slices = p->slices;
             TA.partials = p->partials;
             TA.err = s->flags + 2;
+            TA.wait_first = (unsigned int)s->opt.debug_wait_polls;
             TA.WS = p->WS;
             TA.PB = p->PB;
             TA.PS = p->PS;
@@ -1630,7 +1688,8 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
     }
     mark(2);
     k_red_combine_nd<<<g.n[0] * g.n[1], 256, 0, st>>>(g, s->eps, cubic, s->Ghat, p->quad, p->q1q, p->S, p->nt[0], p->nt[1],
-                                                       p->nt[2], p->tlo[0], p->tlo[1], p->tlo[2], s->Qhat);
+                                                       p->nt[2], p->tlo[0], p->tlo[1], p->tlo[2], p->plane_lo,
+                                                       std::min(p->plane_hi, g.n[0]), s->Qhat);
     s->launches++;
     mark(3);
 }

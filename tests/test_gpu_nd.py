@@ -244,6 +244,32 @@ def test_pair_weight_tables_equal_recomputed_weights(B, d, wrap):
         assert np.abs(a - b).max() <= tol * np.abs(a).max()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-6)])
+def test_3d_shards_add_up_to_the_evaluation(B, precision, tol):
+    """One evaluation split over three shard solvers (as over three GPUs): each returns the modes of
+    its output planes (bn_plan_shards) and zero elsewhere; their sum, the one all-reduce of a sharded
+    stage, is the unsharded result (the sweep items of a plane are summed by other CTAs, hence the
+    tolerance of the precision)."""
+    N, eps, count = 12, -1.0, 3
+    f = _f(3, N, 23)
+    full = _gpu_modes(B, 3, N, eps, f, precision, M1=4, M2=4)
+    bounds = B.plan_shards(3, N, count)
+    total = np.zeros_like(full)
+    for r in range(count):
+        part = _gpu_modes(B, 3, N, eps, f, precision, M1=4, M2=4, shard_index=r, shard_count=count)
+        outside = np.ones(N, bool)
+        outside[bounds[r]:bounds[r + 1]] = False
+        assert np.all(part[outside] == 0)
+        total += part
+    assert np.abs(total - full).max() <= tol * np.abs(full).max()
+    prec = B.MIXED if precision == "mixed" else B.FP64
+    with B.Solver(3, N, T6, R6, B.HARD_SPHERE, eps, precision=prec, M1=4, M2=4, shard_index=0, shard_count=2) as s:
+        s.set_state(f)
+        with pytest.raises(B.BNError) as ei:
+            s.step_rk(0.01, 1)
+        assert ei.value.status == -8
+
+
 def test_3d_escalation_rebuilds_the_plan(B):
     N, eps, dt = 8, 1.0, 0.01
     f = _f(3, N, 17)
