@@ -108,10 +108,10 @@ typedef struct {
                          bn_plan_shards and zero elsewhere, so that the sum of the shard_count
                          results (one all-reduce of N^d complex values) is Q^; bn_eval_collision and
                          the stepping calls of such a solver return BN_ERR_UNSUPPORTED.  0 = none */
-    int debug_wait_polls; /* testing only: when > 0, the first bounded wait for a bulk copy in the
-                         operator kernels gives up after this many non-blocking polls, so that the
-                         call reports BN_ERR_TIMEOUT (the kernel still waits, bounded, for its copy
-                         before going on, and the next call starts clean); 0 = normal waits */
+    int debug_wait_giveup; /* testing only: 1 = the first bounded wait for a bulk copy in the
+                         operator kernels gives up at once, so that the call reports BN_ERR_TIMEOUT
+                         (the kernel records it and still waits, bounded, for its copy before going
+                         on or returning; the next call starts clean); 0 = normal waits */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */

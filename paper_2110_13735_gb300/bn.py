@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
                 ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int), ("wrap", ctypes.c_int),
                 ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong), ("pair_weights", ctypes.c_int),
-                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int), ("debug_wait_polls", ctypes.c_int)]
+                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int), ("debug_wait_giveup", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -134,13 +134,13 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
             escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0,
-            pair_weights=0, shard_index=0, shard_count=0, debug_wait_polls=0) -> Options:
+            pair_weights=0, shard_index=0, shard_count=0, debug_wait_giveup=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
     o.wrap, o.beta_resident, o.beta_budget_mb, o.pair_weights = wrap, beta_resident, beta_budget_mb, pair_weights
-    o.shard_index, o.shard_count, o.debug_wait_polls = shard_index, shard_count, debug_wait_polls
+    o.shard_index, o.shard_count, o.debug_wait_giveup = shard_index, shard_count, debug_wait_giveup
     return o
 
 

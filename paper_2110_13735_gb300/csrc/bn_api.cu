@@ -268,9 +268,9 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
         delete s;
         return fail(BN_ERR_ARG, "shards: 3-D only, 0 <= shard_index < shard_count <= N");
     }
-    if (s->opt.debug_wait_polls < 0) {
+    if (s->opt.debug_wait_giveup != 0 && s->opt.debug_wait_giveup != 1) {
         delete s;
-        return fail(BN_ERR_ARG, "debug_wait_polls must be >= 0");
+        return fail(BN_ERR_ARG, "debug_wait_giveup must be 0 or 1");
     }
     if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1) ||
         (s->opt.pair_weights != 0 && s->opt.pair_weights != 1)) {

@@ -353,7 +353,7 @@ __device__ __forceinline__ void fused2d_body(const FusedArgs<Real>& A, int blk, 
         if (AC::kComp) Qc[i] = cmake<C>(0.0, 0.0);
     }
     __syncthreads();
-    if (!(A.wait_first ? mbar_test_polls(bar, 0, A.wait_first) : mbar_wait_bounded(bar, 0, kWaitLimit))) {
+    if (A.giveup_first || !mbar_wait_bounded(bar, 0, kWaitLimit)) {
         // the copy did not complete in time: record it, wait (bounded) once more for the
         // copy in flight, and give up
         atomicOr(A.err, 1);
@@ -585,7 +585,7 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.count = s->eps != 0.0 ? s->work.count : s->work_quad.count;
     A.partials = s->partials;
     A.err = s->flags + 2;
-    A.wait_first = (unsigned int)s->opt.debug_wait_polls;
+    A.giveup_first = s->opt.debug_wait_giveup;
     A.sw = sizeof(Real) == 4 ? (const Real*)(const void*)s->tabs->sw32 : (const Real*)(const void*)s->tabs->sw64;
     A.stamps = nullptr;
     A.Sb = s->S2;

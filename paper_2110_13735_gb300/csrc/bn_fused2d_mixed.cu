@@ -266,7 +266,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
             Qc[i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const bool landed = A.wait_first ? mbar_test_polls(bar, 0, A.wait_first) : bar_wait(bar, 0);
+        const bool landed = !A.giveup_first && bar_wait(bar, 0);
         if (__syncthreads_or(!landed)) {
             if (tid == 0) atomicOr(A.err, 1);
             bar_wait(bar, 0);
@@ -304,7 +304,7 @@ __device__ __forceinline__ void mixed_body(const FusedArgs<float>& A, int blk, i
         __syncthreads();
         if (blk < A.count) stage_beta(B0, A.beta, A.betaT, ring[0], N, WS);
         cp_commit();
-        const bool landed = A.wait_first ? mbar_test_polls(bar, 0, A.wait_first) : bar_wait(bar, 0);
+        const bool landed = !A.giveup_first && bar_wait(bar, 0);
         if (__syncthreads_or(!landed)) {
             // the copy did not complete in time: record it, wait (bounded) for the copies in flight, give up
             if (tid == 0) atomicOr(A.err, 1);

@@ -74,7 +74,7 @@ struct FusedArgs {
     int count;
     double2* partials;       // [gridDim.x][N^2]
     int* err;                // [0] set to 1 if a bounded wait gave up
-    unsigned int wait_first; // testing: non-blocking polls of the first bounded wait (0 = the normal wait)
+    int giveup_first;        // testing: 1 = the first bounded wait gives up at once (0 = the normal wait)
     unsigned long long* stamps;  // optional [2]: min start / max end %globaltimer (ns) over CTAs
     const Real* sw;          // [b][s in I_N] reducible weights beta(s,b-s) - beta(b,s) - beta(s,b)
     void* Sb;                // mixed N <= 32: [b] S(b) (float2), written by the operator kernel
@@ -88,20 +88,6 @@ struct FusedArgs {
 // 256 / kPartModes thread groups adds the partials c = w, w + groups, ... with FP32 compensated
 // (Kahan) summation, and the group results meet in a fixed FP64 tree (deterministic).
 constexpr int kPartModes = 4;
-// Non-blocking bounded wait for the testing option `wait_first`: `polls` tests of the phase
-// (mbarrier.test_wait never suspends the thread), false if none saw it complete.
-__device__ __forceinline__ bool mbar_test_polls(uint64_t* bar, uint32_t parity, uint32_t polls) {
-    for (uint32_t i = 0; i < polls; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
 // Packed FP32 pairs (sm_100 family): a 64-bit register holding two floats, and the paired FMA
 // fma.rn.f32x2, which rounds each half exactly as fmaf does and issues once for both.
 __device__ __forceinline__ uint64_t dup2(float x) {

@@ -373,7 +373,7 @@ struct TripleNdArgs {
     int PP;                   // complex entries per P plane buffer
     int GP;                   // complex entries per staged mode plane (n1 n2; 0 when axis 0 is trivial)
     int T0max;
-    unsigned int wait_first;      // testing: non-blocking polls of each tile's first bounded wait (0 = normal)
+    int giveup_first;             // testing: 1 = each tile's first bounded wait gives up at once
     unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
 };
 
@@ -536,9 +536,8 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
                 if (sNew <= shi0) {
                     const int sNext = sNew + 1;
                     if (a0 - 1 > aLo && sNext <= shi0) fetch_modes(sNext, k ^ 1);
-                    const bool first = a0 == aHi && A.wait_first;
-                    if (!(first ? mbar_test_polls(&bar[k], (phases >> k) & 1u, A.wait_first)
-                                : nd_bar_wait(&bar[k], (phases >> k) & 1u))) {
+                    const bool giveup = a0 == aHi && A.giveup_first;
+                    if (giveup || !nd_bar_wait(&bar[k], (phases >> k) & 1u)) {
                         // record it and wait (bounded) for the copy in flight before going on
                         if (tid == 0) atomicExch(A.err, 1);
                         nd_bar_wait(&bar[k], (phases >> k) & 1u);
@@ -1669,7 +1668,7 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
             TA.slices = p->slices;
             TA.partials = p->partials;
             TA.err = s->flags + 2;
-            TA.wait_first = (unsigned int)s->opt.debug_wait_polls;
+            TA.giveup_first = s->opt.debug_wait_giveup;
             TA.WS = p->WS;
             TA.PB = p->PB;
             TA.PS = p->PS;

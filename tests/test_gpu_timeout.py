@@ -1,9 +1,9 @@
 """The bounded-wait error path of the operator kernels, exercised without any fault.
 
 Every wait of a kernel for a bulk (TMA) copy is bounded; when it runs out the kernel records it,
-waits (bounded) for its copy before going on, and the call returns BN_ERR_TIMEOUT.  The testing
-option debug_wait_polls turns the first wait into a few non-blocking polls, which run out before
-the copy lands, so the path runs on every call of such a solver.  The test checks the status, that
+waits (bounded) for its copy before going on or returning, and the call returns BN_ERR_TIMEOUT.
+The testing option debug_wait_giveup makes the first wait of each operator kernel give up at once,
+so the path runs on every call of such a solver.  The test checks the status, that
 the context stays usable (an ordinary solver evaluates correctly right after), and that the flag
 does not stick to later calls of that ordinary solver.
 """
@@ -41,7 +41,7 @@ def test_wait_runs_out_and_the_context_survives(B, d, N, precision):
     kernel = B.HARD_SPHERE if d == 3 else B.MAXWELL
     kw = dict(M1=4, M2=4) if d == 3 else {}
     f = I.two_gaussians(d, N, T6, 1.0, (1.5, 0.0, 0.0)[:d] if d == 3 else (1.5, 0.5), 0.8)
-    with B.Solver(d, N, T6, R6, kernel, 1.0, precision=prec, debug_wait_polls=1, **kw) as s:
+    with B.Solver(d, N, T6, R6, kernel, 1.0, precision=prec, debug_wait_giveup=1, **kw) as s:
         s.set_state(f)
         with pytest.raises(B.BNError) as ei:
             s.eval_collision()
