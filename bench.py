@@ -188,20 +188,23 @@ def fma_peaks(bn, stream):
     return res
 
 
-def leg_3d(bn, I, which: str, steps: int, peak_fp32: float):
+def leg_3d(bn, I, which: str, steps: int, peak_fp32: float, **solver_opts):
     """A 3-D configuration in mixed precision with FP64 moments and the conservation projection:
     'config2' = hard spheres N=32, eps=-1, two Gaussians (variance 0.8, centres +-(1.5,0,0), max 0.9),
     RK4 dt=0.01; 'config4' = hard spheres N=48, eps=+1, Gaussian of mass 8 and temperature 0.4, RK4
     dt=0.002 (one evaluation only: 4e14 terms).  The kernel-mode slices are recomputed from the
     quadrature factors at every evaluation.  Times RK4 steps (config2) or evaluations (config4) with
-    CUDA events on the solver's stream, the phases of every evaluation with the library's events."""
+    CUDA events on the solver's stream, the phases of every evaluation with the library's events.
+    `solver_opts` (e.g. beta_budget_mb, pair_weights) go to the solver: profiling runs use them to
+    keep the device memory of a capture small."""
     import torch
     N, eps, dt, f0 = (32, -1.0, 0.01, I.config2_f0(32, R_TRUNC)) if which == "config2" else \
         (48, 1.0, 0.002, I.config4_f0(48, R_TRUNC))
     T = I.box_half_width(R_TRUNC)
     stream = torch.cuda.Stream()
     t_create = time.perf_counter()
-    s = bn.Solver(3, N, T, R_TRUNC, bn.HARD_SPHERE, eps, stream=stream, precision=bn.MIXED, conserve=1)
+    s = bn.Solver(3, N, T, R_TRUNC, bn.HARD_SPHERE, eps, stream=stream, precision=bn.MIXED, conserve=1,
+                  **solver_opts)
     t_create = time.perf_counter() - t_create
     s.set_state(f0)
     s.profile_enable(True)
@@ -253,6 +256,26 @@ def leg_3d(bn, I, which: str, steps: int, peak_fp32: float):
                        "peak_basis": "measured paired-FP32 FMA rate (bn_measure_fma_peak)"}
     out["moments_after"] = {"rho": m[0], "e": m[4], "max_f": m[7], "t": m[8]}
     return out
+
+
+def run_leg_only(args):
+    """One 3-D leg alone (`--only config2|config4`), printed as one JSON line: the profiling runs'
+    command, with the solver's slice budget and pair-weight mode set from the command line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2110_13735_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2110_13735_gb300 import bn
+    from paper_2110_13735_gb300 import inputs as I
+    bn.load()
+    opts = {}
+    if args.beta_budget_mb > 0:
+        opts["beta_budget_mb"] = args.beta_budget_mb
+    if args.pair_weights:
+        opts["pair_weights"] = 1
+    peak = bn.measure_fma_peak(1, None)[0]
+    leg = leg_3d(bn, I, args.only, max(1, args.leg3d_steps), peak, **opts)
+    print(json.dumps({"leg": args.only, "solver_options": opts, **leg}))
 
 
 def run_ours(args):
@@ -399,14 +422,18 @@ def run_ours(args):
         solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
 
     serving = None
-    if args.serving > 0:
-        serving = serving_sample(bn, I, args.serving, 200.0, args.serving_fp64,
-                                 Ns=(16, 32, 64) if args.serving_n64 else (16, 32))
+    if args.serving > 0 and ws == 1:   # extra legs at N=1 only (replicas would repeat them)
+        Ns = tuple(int(x) for x in args.serving_ns.split(","))
+        per_n = {int(a): int(b) for a, b in (x.split(":") for x in args.serving_fp64.split(","))}
+        policy = {"beta_split_N": sorted(int(x) for x in args.serving_beta_split.split(",") if x),
+                  "escalate_at_by_N": {int(a): float(b) for a, b in (x.split(":") for x in args.serving_escalate.split(",")
+                                                                     if x)}}
+        serving = serving_sample(bn, I, args.serving, 200.0, {N: per_n.get(N, 0) for N in Ns}, Ns=Ns, policy=policy)
 
     legs = {}
-    if args.leg3d_steps > 0:
+    if args.leg3d_steps > 0 and ws == 1:
         legs["config2_3d_n32"] = leg_3d(bn, I, "config2", args.leg3d_steps, peaks["fp32x2"])
-    if args.leg48:
+    if args.leg48 and ws == 1:
         legs["config4_3d_n48"] = leg_3d(bn, I, "config4", 1, peaks["fp32x2"])
 
     cpu = None
@@ -437,15 +464,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_run(bn, I, reqs, escalate_at: float):
+def serving_run(bn, I, reqs, policy: dict):
     """Continuous-batching server on a seeded stream of 2-D requests fed in real time from a host
-    thread (mixed precision; with escalate_at > 0 a request switches to FP64 once |eps| max f
-    reaches it).  Returns (latencies, final states, wall seconds, server stats)."""
+    thread (mixed precision with the per-request options of `policy`).  Returns (latencies, final
+    states, wall seconds, server stats); the stats also list the requests that switched to FP64."""
     import threading
     T = I.box_half_width(6.0)
     f0s = [I.request_f0(r) for r in reqs]
     ids = [None] * len(reqs)
-    with bn.Server(max_active=256) as srv:
+    # 64 slots, least estimated work first: the cheap requests pass while the N=64 ones queue (all
+    # admitted at once, every request would finish in the last steps of one shared batch)
+    with bn.Server(max_active=64) as srv:
         def feeder():
             t_start = time.perf_counter()
             for k, r in enumerate(reqs):
@@ -453,35 +482,71 @@ def serving_run(bn, I, reqs, escalate_at: float):
                 if delay > 0:
                     time.sleep(delay)
                 ids[k] = srv.submit(2, r["N"], T, r["R"], r["kernel"], r["eps"], f0s[k], r["dt"], r["t_end"],
-                                    precision=bn.MIXED, escalate_at=escalate_at)
+                                    precision=bn.MIXED, **request_options(r, policy))
         t0 = time.perf_counter()
         th = threading.Thread(target=feeder)
         th.start()
         th.join()
         srv.wait_idle(1800)
         wall = time.perf_counter() - t0
-        lat, results = [], []
+        lat, results, escalated = [], [], []
         for k, r in enumerate(reqs):
             st, res, times = srv.poll(ids[k], r["N"] ** 2)
             if st != 2:
                 raise RuntimeError(f"serving request {k} ended in state {st}")
             lat.append(times[2] - times[0])
             results.append(res)
+            if times[3] >= 0:
+                escalated.append(k)
         stats = srv.stats()
+        stats["escalated"] = escalated
     return np.array(lat), results, wall, stats
 
 
-def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16, 32), escalations=(0.0, 0.5)):
+def serving_fp64_sample(reqs, per_n: dict) -> list:
+    """A stratified sample of the serving mix for the FP64 batch-of-one reference: for each N,
+    `per_n[N]` requests: one classical (eps = 0) request when per_n[N] >= 3, the others spread evenly
+    from the least to the most saturated quantum request of that N (ordered by |eps| max f0, the
+    quantity that sets the mixed-precision error)."""
+    out = []
+    for N, k in sorted(per_n.items()):
+        if k <= 0:
+            continue
+        classical = [r for r in reqs if r["N"] == N and r["eps"] == 0.0]
+        quantum = sorted((r for r in reqs if r["N"] == N and r["eps"] != 0.0), key=lambda r: (abs(r["eps"]) * r["fmax"], r["id"]))
+        if k >= 3 and classical:
+            out.append(classical[len(classical) // 2]["id"])
+            k -= 1
+        if quantum:
+            idx = np.unique(np.linspace(0, len(quantum) - 1, k).round().astype(int))
+            out += [quantum[i]["id"] for i in idx]
+    return out
+
+
+def request_options(r, policy: dict) -> dict:
+    """Solver options of one serving request under `policy`: the kernel-mode rounding correction for
+    the N in policy['beta_split_N'], and the switch to FP64 at |eps| max f >= policy['escalate_at_by_N'][N]."""
+    o = {}
+    if r["N"] in policy.get("beta_split_N", ()):
+        o["beta_split"] = 1
+    x = policy.get("escalate_at_by_N", {}).get(r["N"], 0.0)
+    if x > 0:
+        o["escalate_at"] = x
+    return o
+
+
+def serving_sample(bn, I, n_requests: int, rate: float, per_n: dict, Ns=(16, 32, 64), policy=None):
     """The serving mix (N in `Ns`, eps in {-1, 0, +1}, Maxwell molecules or hard spheres, two-Gaussian
-    data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2) through the continuous-batching server,
-    once per escalation threshold, against a stratified sample of the same requests solved one at a
-    time in FP64 (solves/s and the relative L2 difference of the final states)."""
+    data, Poisson arrivals at `rate`/s, RK4 dt=0.01 to t=2) through the continuous-batching server
+    in mixed precision with the per-request options of `policy` (request_options), against a
+    stratified sample of the same requests solved one at a time in FP64: p50/p99 time to solution,
+    solves/s, and the relative L2 difference of the final states.  The FP64 batch-of-one rate of the
+    whole mix is the measured per-N solve times weighted by the mix's N counts."""
+    policy = policy or {}
     reqs = I.serving_requests(n=n_requests, rate=rate, Ns=Ns, kernels=(0, 1))
     T = I.box_half_width(6.0)
-    step = max(1, len(reqs) // max(1, fp64_sample))
-    sample = list(range(0, len(reqs), step))[:fp64_sample]
-    t_fp = 0.0
-    refs = {}
+    sample = serving_fp64_sample(reqs, per_n)
+    t_by_n, refs = {}, {}
     for k in sample:
         r = reqs[k]
         with bn.Solver(2, r["N"], T, r["R"], r["kernel"], r["eps"], precision=bn.FP64) as s:
@@ -489,24 +554,61 @@ def serving_sample(bn, I, n_requests: int, rate: float, fp64_sample: int, Ns=(16
             a = time.perf_counter()
             s.step_rk(r["dt"], int(round(r["t_end"] / r["dt"])))
             refs[k] = s.get_state().reshape(-1)
-            t_fp += time.perf_counter() - a
-    out = {"requests": len(reqs), "arrival_rate_per_s": rate, "N": list(Ns), "kernels": ["maxwell", "hard_sphere"],
-           "eps": [-1, 0, 1], "fp64_batch_of_one": {"requests": len(sample), "solves_per_s": len(sample) / t_fp}}
-    for esc in escalations:
-        lat, results, wall, stats = serving_run(bn, I, reqs, esc)
-        rel = [float(np.linalg.norm(results[k] - refs[k]) / np.linalg.norm(refs[k])) for k in sample]
-        out["mixed" if esc == 0.0 else f"mixed_escalate_at_{esc:g}"] = {
-            "precision": "mixed" if esc == 0.0 else f"mixed, FP64 once |eps| max f >= {esc:g}",
+            t_by_n.setdefault(r["N"], []).append(time.perf_counter() - a)
+    counts = {N: sum(1 for r in reqs if r["N"] == N) for N in Ns}
+    fp64_mix_s = sum(counts[N] * float(np.mean(t_by_n[N])) for N in Ns if N in t_by_n)
+    lat, results, wall, stats = serving_run(bn, I, reqs, policy)
+    rel = {k: float(np.linalg.norm(results[k] - refs[k]) / np.linalg.norm(refs[k])) for k in sample}
+    lat = np.asarray(lat)
+    by_n = {}
+    for N in Ns:
+        sel = [i for i, r in enumerate(reqs) if r["N"] == N]
+        e = [rel[k] for k in sample if reqs[k]["N"] == N]
+        by_n[str(N)] = {"requests": len(sel), "escalated_to_fp64": sum(1 for k in stats["escalated"] if reqs[k]["N"] == N),
+                        "p50_s": float(np.percentile(lat[sel], 50)),
+                        "p99_s": float(np.percentile(lat[sel], 99)),
+                        "fp64_batch_of_one_s": float(np.mean(t_by_n[N])) if N in t_by_n else None,
+                        "fp64_sample": len(e), "max_rel_l2_vs_fp64": max(e) if e else None,
+                        "within_1e-6": int(sum(x <= 1e-6 for x in e))}
+    worst = max(sample, key=lambda k: rel[k]) if sample else None
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "N": list(Ns), "kernels": ["maxwell", "hard_sphere"],
+            "eps": [-1, 0, 1], "t_end": reqs[0]["t_end"], "dt": reqs[0]["dt"],
+            "precision": "mixed",
+            "policy": {"beta_split_N": list(policy.get("beta_split_N", ())),
+                       "escalate_at_by_N": {str(k): v for k, v in policy.get("escalate_at_by_N", {}).items()}},
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "solves_per_s": len(reqs) / wall, "wall_s": wall, "max_running": stats["max_active"],
-            "ticks": stats["ticks"], "max_rel_l2_vs_fp64": max(rel), "median_rel_l2_vs_fp64": float(np.median(rel)),
-            "within_1e-6": int(sum(x <= 1e-6 for x in rel))}
-    return out
+            "ticks": stats["ticks"], "escalated_to_fp64": len(stats["escalated"]),
+            "fp64_batch_of_one": {"solves_per_s_mix": len(reqs) / fp64_mix_s if fp64_mix_s > 0 else None,
+                                  "basis": "measured FP64 solve time per N (one request at a time) x the mix's "
+                                           "N counts"},
+            "fp64_sample": {"requests": len(sample), "within_1e-6": int(sum(x <= 1e-6 for x in rel.values())),
+                            "max_rel_l2_vs_fp64": rel[worst] if worst is not None else None,
+                            "median_rel_l2_vs_fp64": float(np.median(list(rel.values()))) if rel else None,
+                            "worst": {k: reqs[worst][k] for k in ("id", "N", "eps", "kernel", "fmax", "sigma")}
+                            if worst is not None else None},
+            "by_N": by_n}
+
+
+def host_cpu() -> dict:
+    """The host CPU as lscpu names it (model, sockets x cores, threads per core)."""
+    info = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": info.get("Model name") or info.get("Vendor ID"), "architecture": info.get("Architecture"),
+            "cpus": info.get("CPU(s)"), "sockets": info.get("Socket(s)"), "cores_per_socket": info.get("Core(s) per socket"),
+            "threads_per_core": info.get("Thread(s) per core")}
 
 
 def cpu_baseline_sample(seconds: float):
     """The oracle as it stands on this host: full Lemma evaluations of the two requests at
-    N=32, repeated until `seconds` of CPU time have passed."""
+    N=32, repeated until `seconds` of CPU time have passed, on all host threads and then, for
+    a third of that time, on one thread."""
     import oracle as O
     from paper_2110_13735_gb300 import inputs as I
     T = I.box_half_width(R_TRUNC)
@@ -514,17 +616,29 @@ def cpu_baseline_sample(seconds: float):
            (O.Operator(2, N_MODES, T, R_TRUNC, 0, 1.0), I.config1_boson_f0(N_MODES, R_TRUNC), True)]
     for op, _, _ in ops:
         op.beta()
-    terms, evals, t0 = 0.0, 0, time.perf_counter()
-    while True:
-        for op, f, cubic in ops:
-            op.eval_collision(f)
-            terms += lemma_terms(2, N_MODES, cubic)
-            evals += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    el = time.perf_counter() - t0
-    return {"value": terms / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{evals} full FP64 evaluations of Q_eps (N=32 BKW eps=0 and Gaussian eps=+1), {el:.1f} s"}
+
+    def run(limit):
+        terms, evals, t0 = 0.0, 0, time.perf_counter()
+        while True:
+            for op, f, cubic in ops:
+                op.eval_collision(f)
+                terms += lemma_terms(2, N_MODES, cubic)
+                evals += 1
+            if time.perf_counter() - t0 >= limit:
+                break
+        return terms / (time.perf_counter() - t0), evals, time.perf_counter() - t0
+
+    threads = O.num_threads()
+    value, evals, el = run(seconds)
+    O.set_threads(1)
+    try:
+        v1, e1, el1 = run(seconds / 3.0)
+    finally:
+        O.set_threads(threads)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{evals} full FP64 evaluations of Q_eps (N=32 BKW eps=0 and Gaussian eps=+1), {el:.1f} s",
+            "one_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": f"{e1} evaluations, {el1:.1f} s"},
+            "host": host_cpu()}
 
 
 def run_reference(args):
@@ -561,7 +675,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(ws),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -574,13 +689,24 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving", type=int, default=64, help="requests of the serving sample (0 = skip)")
-    ap.add_argument("--serving-fp64", type=int, default=12, help="requests re-solved one at a time in FP64")
-    ap.add_argument("--serving-n64", action="store_true", help="include N=64 requests in the serving mix")
+    ap.add_argument("--serving", type=int, default=512, help="requests of the serving mix (0 = skip)")
+    ap.add_argument("--serving-ns", default="16,32,64", help="mode counts N of the serving mix")
+    ap.add_argument("--serving-fp64", default="16:6,32:5,64:2",
+                    help="FP64 batch-of-one reference requests per N (stratified by |eps| max f0)")
+    ap.add_argument("--serving-beta-split", default="16",
+                    help="mode counts N whose serving requests use the kernel-mode rounding correction (beta_split)")
+    ap.add_argument("--serving-escalate", default="32:0.5",
+                    help="N:x pairs: requests of that N switch to FP64 once |eps| max f >= x (others never)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 leg (profiling runs)")
     ap.add_argument("--leg3d-steps", type=int, default=1,
                     help="timed RK4 steps of the 3-D N=32 configuration (0 = skip)")
     ap.add_argument("--leg48", action="store_true", help="also time one evaluation of the 3-D N=48 configuration")
+    ap.add_argument("--only", choices=["config2", "config4"],
+                    help="run one 3-D leg alone and print it (profiling runs)")
+    ap.add_argument("--beta-budget-mb", type=int, default=0,
+                    help="with --only: device memory (MiB) for the kernel-mode slices of one round (0 = default)")
+    ap.add_argument("--pair-weights", action="store_true",
+                    help="with --only: recompute the pair weights per evaluation instead of storing them")
     ap.add_argument("--mixed-rw", type=int, default=0, choices=[0, 8, 16],
                     help="outputs per thread of the mixed kernel (0 = autotuner; profiling runs fix it)")
     args = ap.parse_args()
@@ -588,6 +714,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_leg_only(args)
     else:
         run_ours(args)
 

@@ -112,10 +112,26 @@ typedef struct {
                          operator kernels gives up at once, so that the call reports BN_ERR_TIMEOUT
                          (the kernel records it and still waits, bounded, for its copy before going
                          on or returning; the next call starts clean); 0 = normal waits */
+    int beta_split;   /* mixed precision, d = 2, LINEAR: 1 = kernel-mode rounding correction.  The
+                         FP32 tables hold beta (and the weights formed from it) rounded to FP32; a
+                         second pass of the same FP32 kernels over tables of the residuals
+                         x - fl32(x) gives the part of Q^ that the rounding leaves out (Q^ is
+                         linear in beta), so that the two passes carry the weights to about 48
+                         bits.  The rounding of beta is one fixed perturbation of the operator:
+                         its error does not average out over time steps and, without the
+                         correction, it dominates the drift of a mixed run from the FP64 one.  In
+                         the stepping calls the correction is formed at the first stage of each
+                         step and reused by the later stages of that step; a standalone
+                         evaluation forms it every call.  0 = off (ignored in FP64) */
 } bn_options;
 
 /* Fill *opt with the defaults (all zero: FP64, RK4, no correction). */
 bn_status bn_default_options(bn_options* opt);
+
+/* sizeof(bn_options) and sizeof(bn_request) as this library was compiled, for bindings that
+ * declare the structures themselves to check their layout against.  No error case. */
+size_t bn_options_bytes(void);
+size_t bn_request_bytes(void);
 
 /*
  * Create a solver for the operator (d, N, T, R, kernel, eps).  d in {2,3};
@@ -344,7 +360,9 @@ bn_status bn_server_submit(bn_server* srv, const bn_request* req, const double* 
 /* State of a request: *state = 0 queued, 1 running, 2 done, 3 failed.  When
  * done and f_out != NULL, the final state (count = N^d) is copied to f_out.
  * times (ntimes >= 3, may be NULL) receives [submit, admit, done] in seconds
- * since the server was created.  Returns BN_ERR_STATE for a failed request. */
+ * since the server was created, and with ntimes >= 4 also the solve time t at which
+ * a done request switched to FP64 (escalate_at; -1 if it never did).  Returns
+ * BN_ERR_STATE for a failed request. */
 bn_status bn_server_poll(bn_server* srv, long long id, int* state, double* f_out, size_t count, double* times,
                          size_t ntimes);
 

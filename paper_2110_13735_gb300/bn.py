@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("quad3d", ctypes.c_int), ("escalate_at", ctypes.c_double),
                 ("mixed_rw", ctypes.c_int), ("mixed_variant", ctypes.c_int), ("wrap", ctypes.c_int),
                 ("beta_resident", ctypes.c_int), ("beta_budget_mb", ctypes.c_longlong), ("pair_weights", ctypes.c_int),
-                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int), ("debug_wait_giveup", ctypes.c_int)]
+                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int), ("debug_wait_giveup", ctypes.c_int),
+                ("beta_split", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -58,6 +59,8 @@ def load(path: str | None = None):
     lib = ctypes.CDLL(path)
     vp, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
     lib.bn_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.bn_options_bytes.restype = ctypes.c_size_t
+    lib.bn_request_bytes.restype = ctypes.c_size_t
     lib.bn_create_solver.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
     lib.bn_destroy_solver.argtypes = [vp]
@@ -134,13 +137,14 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,
             escalate_at=0.0, mixed_rw=0, mixed_variant=0, wrap=0, beta_resident=0, beta_budget_mb=0,
-            pair_weights=0, shard_index=0, shard_count=0, debug_wait_giveup=0) -> Options:
+            pair_weights=0, shard_index=0, shard_count=0, debug_wait_giveup=0, beta_split=0) -> Options:
     o = Options()
     o.M, o.M1, o.M2, o.precision, o.conserve = M, M1, M2, precision, conserve
     o.c_phi, o.integrator, o.quad3d, o.escalate_at = c_phi, integrator, quad3d, escalate_at
     o.mixed_rw, o.mixed_variant = mixed_rw, mixed_variant
     o.wrap, o.beta_resident, o.beta_budget_mb, o.pair_weights = wrap, beta_resident, beta_budget_mb, pair_weights
     o.shard_index, o.shard_count, o.debug_wait_giveup = shard_index, shard_count, debug_wait_giveup
+    o.beta_split = beta_split
     return o
 
 
@@ -341,12 +345,13 @@ class Server:
         return int(rid.value)
 
     def poll(self, rid: int, n_modes: int | None = None):
-        """(state, result or None, (t_submit, t_admit, t_done)); state 0 queued, 1 running, 2 done, 3 failed."""
+        """(state, result or None, (t_submit, t_admit, t_done, t_escalated)); state 0 queued, 1 running,
+        2 done, 3 failed; t_escalated is the solve time of the switch to FP64, -1 if none."""
         state = ctypes.c_int()
-        times = np.zeros(3)
+        times = np.full(4, -1.0)
         out = np.empty(n_modes) if n_modes else None
         st = _lib.bn_server_poll(self._h, int(rid), ctypes.byref(state), _dptr(out) if out is not None else None,
-                                 out.size if out is not None else 0, _dptr(times), 3)
+                                 out.size if out is not None else 0, _dptr(times), 4)
         if st != BN_OK and state.value != 3:
             self._chk(st)
         return state.value, (out if state.value == 2 else None), tuple(times)

@@ -44,7 +44,8 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 
 void free_buffers(bn_solver* s) {
     void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->twiddle, s->S2, s->quad,
-                    s->red, s->q1q, s->partials, s->Qhat, s->moments, s->flags, s->work.items, s->work_quad.items,
+                    s->red, s->q1q, s->partials, s->Qhat, s->partials_lo, s->S2lo, s->Qlo, s->moments, s->flags,
+                    s->work.items, s->work_quad.items,
                     s->work.meta[0], s->work.meta[1], s->work.meta[2], s->work.meta[3]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -82,10 +83,14 @@ void eval_device(bn_solver* s, const double* f_in, double* Q_out) {
 }
 
 // One time step of the chosen integrator on s->f (state committed only if finite).
+// The kernel-mode rounding correction (opt.beta_split) is formed at the first stage and reused by
+// the later stages of the step.
 void record_step(bn_solver* s, double dt) {
+    s->lo_refresh = true;
     if (s->opt.integrator == 0) {
         // classical RK4: K1..K4, f += dt/6 (K1 + 2 K2 + 2 K3 + K4)
         eval_device(s, s->f, s->Qv);
+        s->lo_refresh = false;
         bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 1.0, 0.5, dt, 1);
         eval_device(s, s->y, s->Qv);
         bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 2.0, 0.5, dt, 0);
@@ -96,10 +101,12 @@ void record_step(bn_solver* s, double dt) {
     } else {
         // SSP-RK2 (Heun): y = f + dt K(f); f = (f + y + dt K(y)) / 2
         eval_device(s, s->f, s->Qv);
+        s->lo_refresh = false;
         bn::launch_rk_stage(s, s->f, s->Qv, s->kacc, s->y, 0.0, 1.0, dt, 1);
         eval_device(s, s->y, s->Qv);
         bn::launch_heun_final(s, s->f, s->y, s->Qv, dt, s->f_prev, s->flags);
     }
+    s->lo_refresh = true;
 }
 
 bn_status ensure_graph(bn_solver* s, double dt) {
@@ -207,6 +214,9 @@ bn_status bn_default_options(bn_options* opt) {
     return BN_OK;
 }
 
+size_t bn_options_bytes(void) { return sizeof(bn_options); }
+size_t bn_request_bytes(void) { return sizeof(bn_request); }
+
 const char* bn_last_error(void) { return g_err.c_str(); }
 
 bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double eps, const bn_options* opt,
@@ -271,6 +281,10 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     if (s->opt.debug_wait_giveup != 0 && s->opt.debug_wait_giveup != 1) {
         delete s;
         return fail(BN_ERR_ARG, "debug_wait_giveup must be 0 or 1");
+    }
+    if (s->opt.beta_split != 0 && s->opt.beta_split != 1) {
+        delete s;
+        return fail(BN_ERR_ARG, "beta_split must be 0 or 1");
     }
     if (s->opt.beta_budget_mb < 0 || (s->opt.beta_resident != 0 && s->opt.beta_resident != 1) ||
         (s->opt.pair_weights != 0 && s->opt.pair_weights != 1)) {
@@ -345,6 +359,11 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     alloc((void**)&s->q1q, n * sizeof(double2));
     if (!nd) alloc((void**)&s->partials, (size_t)s->n_partials * n * sizeof(double2));
     alloc((void**)&s->Qhat, n * sizeof(double2));
+    if (!nd && d == 2 && s->opt.beta_split && s->opt.precision == BN_MIXED) {
+        alloc((void**)&s->partials_lo, (size_t)s->n_partials * n * sizeof(double2));
+        alloc((void**)&s->S2lo, (size_t)s->g.nExt * sizeof(double2));
+        alloc((void**)&s->Qlo, n * sizeof(double2));
+    }
     alloc((void**)&s->moments, 16 * sizeof(double));
     alloc((void**)&s->flags, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s->flags_host, 8 * sizeof(int));
@@ -358,6 +377,10 @@ bn_status bn_create_solver(int d, int N, double T, double R, int kernel, double 
     }
     cudaMemsetAsync(s->flags, 0, 8 * sizeof(int), s->stream);
     cudaMemsetAsync(s->Qhat, 0, n * sizeof(double2), s->stream);
+    if (s->Qlo) {
+        cudaMemsetAsync(s->Qlo, 0, n * sizeof(double2), s->stream);
+        cudaMemsetAsync(s->S2lo, 0, (size_t)s->g.nExt * sizeof(double2), s->stream);
+    }
     st = nd ? bn::prepare_nd(s) : bn::tune_mixed2d(s, &err);
     if (st != BN_OK) {
         if (nd) err = "kernel-mode slice production failed";

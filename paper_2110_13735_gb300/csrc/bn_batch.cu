@@ -38,6 +38,7 @@ struct ElemJob {
     double dt, scale;
     const float2* Sb;   // mixed N <= 32 with eps != 0: S(b) from the operator kernel (else null)
     float eps;
+    const double2* Qlo; // kernel-mode rounding correction: its modes, added to Q^ (else null)
 };
 
 __device__ __forceinline__ double2 warp_sum2(double sr, double si) {
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __res
         tm[1] = 0;
     }
     const ElemJob J = jobs[blockIdx.y];
+    if (!J.Qhat) return;   // a job without a residual-table pass (uniform per block)
     if (J.part32) {
         if (blockIdx.x * kPartModes >= J.nm) return;   // uniform per block
         sum_partials_f32_block(J.nm, J.nPart, reinterpret_cast<const float4*>(J.partials), J.Qhat, blockIdx.x, J.N,
@@ -216,6 +218,19 @@ __global__ void __launch_bounds__(256) k_sum_partials_batch(const ElemJob* __res
         double sx = 0, sy = 0;
         for (int k = 0; k < 32; ++k) { sx += sh[k][m].x; sy += sh[k][m].y; }
         J.Qhat[i] = make_double2(sx, sy);
+    }
+}
+
+// Q^ += the modes of the kernel-mode rounding correction, for the jobs that have it.
+__global__ void k_add_lo_batch(const ElemJob* __restrict__ jobs) {
+    const ElemJob J = jobs[blockIdx.y];
+    if (!J.Qlo) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.nm; i += gridDim.x * blockDim.x) {
+        const double2 a = J.Qlo[i];
+        double2 q = J.Qhat[i];
+        q.x += a.x;
+        q.y += a.y;
+        J.Qhat[i] = q;
     }
 }
 
@@ -282,6 +297,10 @@ struct BatchPlan {
         int* d_cta = nullptr;
     };
     std::vector<Group> groups;
+    // kernel-mode rounding correction: the residual-table pass of the jobs that have it (its own
+    // groups, and job records whose Q^, partials and S(b) are that pass's buffers)
+    std::vector<Group> lo_groups;
+    ElemJob* d_elem_lo = nullptr;
     int maxN = 0, maxNm = 0;
     bool timed = false;
     unsigned long long* d_time = nullptr;   // [min start, max end, total ns, count] (timed plans)
@@ -293,11 +312,13 @@ void destroy_plan(BatchPlan* p) {
     if (!p) return;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->d_elem);
+    cudaFree(p->d_elem_lo);
     cudaFree(p->d_time);
-    for (auto& g : p->groups) {
-        cudaFree(g.d_jobs);
-        cudaFree(g.d_cta);
-    }
+    for (auto* gs : {&p->groups, &p->lo_groups})
+        for (auto& g : *gs) {
+            cudaFree(g.d_jobs);
+            cudaFree(g.d_cta);
+        }
     delete p;
 }
 
@@ -305,21 +326,34 @@ void destroy_plan(BatchPlan* p) {
 // that follows is fused into the last transform pass (arguments as for k_dft_batch): per row, the
 // last inverse pass, the RK update and, for an RK stage, the first forward pass of the next
 // evaluation run as one launch (fwd0_done: this evaluation's first pass was done that way).
+// With lo_pass (the first evaluation of a step) the residual-table pass of the kernel-mode rounding
+// correction runs first; every evaluation then adds its modes to Q^.
 static void record_batched_eval(BatchPlan* p, cudaStream_t st, int stage_in, int rk = 0, double w_acc = 0.0,
-                                double c_next = 0.0, int first = 0, bool fwd0_done = false) {
+                                double c_next = 0.0, int first = 0, bool fwd0_done = false, bool lo_pass = false) {
     const int nj = (int)p->solvers.size();
     const dim3 gw((p->maxNm * 32 + kThreads - 1) / kThreads, nj);
+    const dim3 gp((p->maxNm + kPartModes - 1) / kPartModes, nj);
     if (!fwd0_done) {
         k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 0, stage_in);
         p->launches++;
     }
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 1, stage_in);
     p->launches++;
+    if (lo_pass && !p->lo_groups.empty()) {
+        for (auto& g : p->lo_groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
+        k_sum_partials_batch<<<gp, 256, 0, st>>>(p->d_elem_lo, nullptr);
+        p->launches += (long long)p->lo_groups.size() + 1;
+    }
     for (auto& g : p->groups) launch_fused2d_group(st, g.variant, g.d_jobs, g.d_cta, g.njobs, g.total, g.maxN);
     p->launches += (long long)p->groups.size();
-    k_sum_partials_batch<<<dim3((p->maxNm + kPartModes - 1) / kPartModes, nj), 256, 0, st>>>(p->d_elem, p->d_time);
+    k_sum_partials_batch<<<gp, 256, 0, st>>>(p->d_elem, p->d_time);
+    p->launches++;
+    if (!p->lo_groups.empty()) {
+        k_add_lo_batch<<<dim3((p->maxNm + kThreads - 1) / kThreads, nj), kThreads, 0, st>>>(p->d_elem);
+        p->launches++;
+    }
     k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 2, stage_in);
-    p->launches += 2;
+    p->launches++;
     if (rk == 0) {   // requests project Q: the last pass, the projection, then the RK kernels
         k_dft_batch<<<gw, kThreads, 0, st>>>(p->d_elem, 3, stage_in);
         p->launches++;
@@ -368,6 +402,7 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         J.eps = (float)s->eps;
         J.dt = dts[i];
         J.scale = s->scale;
+        J.Qlo = beta_split_on(s) ? s->Qlo : nullptr;
         elem.push_back(J);
         p->maxN = std::max(p->maxN, s->g.N);
         p->maxNm = std::max(p->maxNm, s->g.nModes);
@@ -414,6 +449,48 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         if (e == cudaSuccess) e = cudaMemcpy(g.d_jobs, args.data(), args.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(g.d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice);
         p->groups.push_back(g);
+        // the residual-table pass of the same jobs that have the kernel-mode rounding correction (same
+        // order, same CTAs per job), untimed
+        if (!mixed || e != cudaSuccess) continue;
+        std::vector<int> lo_jobs;
+        for (int j : kv.second)
+            if (beta_split_on(solvers[j])) lo_jobs.push_back(j);
+        if (lo_jobs.empty()) continue;
+        BatchPlan::Group gl;
+        gl.variant = kv.first;
+        std::vector<unsigned char> largs(sizeof(FusedArgs<float>) * lo_jobs.size());
+        std::vector<int> lcta(1, 0);
+        for (size_t k = 0; k < lo_jobs.size(); ++k) {
+            bn_solver* s = solvers[lo_jobs[k]];
+            fill_fused_args_lo(s, largs.data() + sizeof(FusedArgs<float>) * k);
+            reinterpret_cast<FusedArgs<float>*>(largs.data() + sizeof(FusedArgs<float>) * k)->stamps = nullptr;
+            lcta.push_back(lcta.back() + elem[lo_jobs[k]].nPart);
+            gl.maxN = std::max(gl.maxN, s->g.N);
+        }
+        gl.njobs = (int)lo_jobs.size();
+        gl.total = lcta.back();
+        e = cudaMalloc(&gl.d_jobs, largs.size());
+        if (e == cudaSuccess) e = cudaMalloc((void**)&gl.d_cta, sizeof(int) * lcta.size());
+        if (e == cudaSuccess) e = cudaMemcpy(gl.d_jobs, largs.data(), largs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(gl.d_cta, lcta.data(), sizeof(int) * lcta.size(), cudaMemcpyHostToDevice);
+        p->lo_groups.push_back(gl);
+    }
+    if (e == cudaSuccess && !p->lo_groups.empty()) {
+        std::vector<ElemJob> lo = elem;
+        for (int i = 0; i < n; ++i) {
+            bn_solver* s = solvers[i];
+            ElemJob& J = lo[i];
+            J.Qlo = nullptr;
+            if (!beta_split_on(s)) {
+                J.Qhat = nullptr;   // no residual-table pass for this job
+                continue;
+            }
+            J.Qhat = s->Qlo;
+            J.partials = s->partials_lo;
+            if (J.Sb) J.Sb = reinterpret_cast<const float2*>(s->S2lo);
+        }
+        e = cudaMalloc(&p->d_elem_lo, sizeof(ElemJob) * lo.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_elem_lo, lo.data(), sizeof(ElemJob) * lo.size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         *err = std::string("batch plan: ") + cudaGetErrorString(e);
@@ -439,10 +516,10 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
         for (int stage = 0; stage < 4; ++stage) {
             if (fuse_rk) {
                 record_batched_eval(p, st, stage == 0 ? 0 : 1, stage < 3 ? 1 : 2, stage < 3 ? wacc[stage] : 0.0,
-                                    stage < 3 ? cnext[stage] : 0.0, stage == 0, stage > 0);
+                                    stage < 3 ? cnext[stage] : 0.0, stage == 0, stage > 0, stage == 0);
                 continue;
             }
-            record_batched_eval(p, st, stage == 0 ? 0 : 1);
+            record_batched_eval(p, st, stage == 0 ? 0 : 1, 0, 0.0, 0.0, 0, false, stage == 0);
             if (stage < 3) {
                 k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, wacc[stage], cnext[stage], stage == 0);
                 p->launches++;
@@ -453,10 +530,10 @@ bn_status build_plan(bn_solver** solvers, int n, const double* dts, bool timed, 
             p->launches++;
         }
     } else if (fuse_rk) {
-        record_batched_eval(p, st, 0, 1, 0.0, 1.0, 1);
+        record_batched_eval(p, st, 0, 1, 0.0, 1.0, 1, false, true);
         record_batched_eval(p, st, 1, 3, 0.0, 0.0, 0, true);
     } else {
-        record_batched_eval(p, st, 0);
+        record_batched_eval(p, st, 0, 0, 0.0, 0.0, 0, false, true);
         k_rk_stage_batch<<<ge, kThreads, 0, st>>>(p->d_elem, 0.0, 1.0, 1);
         record_batched_eval(p, st, 1);
         k_heun_final_batch<<<ge, kThreads, 0, st>>>(p->d_elem);

@@ -594,9 +594,36 @@ void fill_args_t(const bn_solver* s, FusedArgs<Real>& A) {
     A.betaT = s->tabs->beta32T;
 }
 
+// The residual-table pass of the kernel-mode rounding correction: the same kernel over the
+// rounding residuals of the FP32 tables, into its own partials and S(b) sums.
+void fill_args_lo(const bn_solver* s, FusedArgs<float>& A) {
+    fill_args_t<float>(s, A);
+    A.beta = s->tabs->beta32lo;
+    A.sw = s->tabs->sw32lo;
+    A.dq = s->tabs->dq32lo;
+    A.betaT = s->tabs->beta32Tlo;
+    A.partials = s->partials_lo;
+    A.Sb = s->S2lo;
+}
+
+__global__ void k_add_modes(int nm, double2* __restrict__ Q, const double2* __restrict__ add) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+        const double2 a = add[i];
+        double2 q = Q[i];
+        q.x += a.x;
+        q.y += a.y;
+        Q[i] = q;
+    }
+}
+
 // Mixed precision N <= 32 (variant 0): k_mixed2d (which also forms S(b)) and the FP32-compensated
 // partial sum with the S(b) convolution (bn_fused2d_mixed.cu).
 void launch_mixed(bn_solver* s) {
+    if (beta_split_on(s) && s->lo_refresh) {
+        FusedArgs<float> L;
+        fill_args_lo(s, L);
+        s->launches += launch_mixed2d(L, std::max(1, std::min(L.count, s->n_partials)), s->mixed_rw, s->Qlo, s->stream);
+    }
     FusedArgs<float> A;
     fill_args_t<float>(s, A);
     if (s->prof && s->prof_slot < 8 && s->prof_stamps) {
@@ -610,6 +637,18 @@ void launch_mixed(bn_solver* s) {
 
 template <typename Real, int RW, int NT, bool STAGE, bool DB>
 void launch_t(bn_solver* s, const cplx<Real>* G, const Real* beta) {
+    if constexpr (sizeof(Real) == 4) {
+        if (beta_split_on(s) && s->lo_refresh) {
+            FusedArgs<float> L;
+            fill_args_lo(s, L);
+            L.G = G;
+            const size_t smem = Layout2D<Real, RW, STAGE, DB>::bytes(s->g.N, NT);
+            const int grid = std::max(1, std::min(L.count, s->n_partials));
+            k_fused2d<Real, RW, NT, STAGE, DB><<<grid, NT, smem, s->stream>>>(L);
+            k_sum_partials<<<(s->g.nModes + 7) / 8, 256, 0, s->stream>>>(s->g.nModes, grid, s->partials_lo, s->Qlo);
+            s->launches += 2;
+        }
+    }
     FusedArgs<Real> A;
     fill_args_t<Real>(s, A);
     A.G = G;
@@ -660,9 +699,15 @@ size_t fused2d_smem(int N, int precision) {
 // The fused operator into caller-chosen scratch on a given stream (used by the no-allocation
 // entry point): G = the solver's precision copy of the modes, partials/Qhat/err in scratch.
 template <typename Real, int RW, int NT, bool STAGE, bool DB>
-void into_t(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err) {
+void into_t(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err,
+            bool lo = false) {
     FusedArgs<Real> A;
-    fill_args_t<Real>(s, A);
+    if constexpr (sizeof(Real) == 4) {
+        if (lo) fill_args_lo(s, A);
+        else fill_args_t<Real>(s, A);
+    } else {
+        fill_args_t<Real>(s, A);
+    }
     A.G = (const cplx<Real>*)G;
     A.partials = partials;
     A.err = err;
@@ -673,12 +718,13 @@ void into_t(const bn_solver* s, cudaStream_t st, const void* G, double2* partial
 }
 
 void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err,
-                  void* sb) {
+                  void* sb, bool lo) {
     switch (fused2d_variant(s)) {
         case 0:
         case 4: {
             FusedArgs<float> A;
-            fill_args_t<float>(s, A);
+            if (lo) fill_args_lo(s, A);
+            else fill_args_t<float>(s, A);
             A.G = (const float2*)G;
             A.partials = partials;
             A.err = err;
@@ -686,7 +732,7 @@ void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* p
             launch_mixed2d(A, std::max(1, std::min(A.count, s->n_partials)), s->mixed_rw, Qhat, st);
             break;
         }
-        case 1: into_t<float, 8, kBigNT, true, false>(s, st, G, partials, Qhat, err); break;
+        case 1: into_t<float, 8, kBigNT, true, false>(s, st, G, partials, Qhat, err, lo); break;
         case 2: into_t<double, 2, 128, true, false>(s, st, G, partials, Qhat, err); break;
         default: into_t<double, 2, 256, false, false>(s, st, G, partials, Qhat, err); break;
     }
@@ -806,6 +852,17 @@ void fill_fused_args(const bn_solver* s, void* out) {
     else fill_args_t<double>(s, *(FusedArgs<double>*)out);
 }
 
+void fill_fused_args_lo(const bn_solver* s, void* out) { fill_args_lo(s, *(FusedArgs<float>*)out); }
+
+bool beta_split_on(const bn_solver* s) {
+    return s->opt.beta_split && s->opt.precision == BN_MIXED && s->g.d == 2 && !s->nd && s->Qlo && s->tabs &&
+           s->tabs->beta32lo;
+}
+
+void launch_add_modes(int nm, double2* Q, const double2* add, cudaStream_t st) {
+    k_add_modes<<<(nm + 255) / 256, 256, 0, st>>>(nm, Q, add);
+}
+
 size_t fused2d_variant_smem(int variant, int N) {
     switch (variant) {
         case 0: return mixed2d_smem(N, 8);
@@ -828,13 +885,19 @@ void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, cons
     }
 }
 
-// The 2-D operator: Q^ (s->Qhat) from the modes of the stage argument.
+// The 2-D operator: Q^ (s->Qhat) from the modes of the stage argument.  With the kernel-mode
+// rounding correction the residual-table pass runs first when s->lo_refresh is set (its modes
+// kept in s->Qlo) and Qlo is added to Q^.
 void launch_fused2d(bn_solver* s) {
     const bool mixed = s->opt.precision == BN_MIXED;
     const bool big = s->g.N > 32;
     if (mixed) {
         if (big) launch_t<float, 8, kBigNT, true, false>(s, s->Ghat32, s->tabs->beta32);
         else launch_mixed(s);
+        if (beta_split_on(s)) {
+            launch_add_modes(s->g.nModes, s->Qhat, s->Qlo, s->stream);
+            s->launches++;
+        }
     } else {
         if (big) launch_t<double, 2, 256, false, false>(s, s->Ghat, s->tabs->beta64);
         else launch_t<double, 2, 128, true, false>(s, s->Ghat, s->tabs->beta64);

@@ -53,6 +53,12 @@ struct KernelTables {
     double* sw64 = nullptr;       // 2-D: [b (ext)][s in I_N] = beta(s,b-s) - beta(b,s) - beta(s,b) (0 off box_s(b))
     float* sw32 = nullptr;
     float* dq32 = nullptr;        // 2-D: [b in I_N][a (ext)] = beta(a, b) - beta(b, b), formed in FP64, rounded once
+    // 2-D: the rounding residuals of the four FP32 tables, x - fl32(x) rounded to FP32 (x the FP64
+    // value), laid out as their FP32 tables: the second pass of the kernel-mode rounding correction
+    float* beta32lo = nullptr;
+    float* beta32Tlo = nullptr;
+    float* sw32lo = nullptr;
+    float* dq32lo = nullptr;
     float* alpha32 = nullptr;     // FP32 copies of alpha64 / alphap64 ([P][nExt])
     float* alphap32 = nullptr;
     double* alphaI64 = nullptr;   // alpha, alpha' restricted to a in I_N ([P][N^d]), FP64 and FP32
@@ -300,6 +306,12 @@ struct bn_solver {
     double2* q1q = nullptr;      // Q_{1,q} modes, N^d
     double2* partials = nullptr; // [n_partials][N^d]
     double2* Qhat = nullptr;     // combined modes
+    // kernel-mode rounding correction (opt.beta_split, mixed 2-D): the residual-table pass's own
+    // partials and S(b) sums, and its modes, added to Q^ by every evaluation
+    double2* partials_lo = nullptr;
+    double2* S2lo = nullptr;
+    double2* Qlo = nullptr;
+    bool lo_refresh = true;      // recompute Qlo in the next evaluation (cleared for RK stages 2..4)
     double* moments = nullptr;   // d+6
     int* flags = nullptr;        // [0] non-finite, [1] committed steps, [2] wait timeout, [4..5] max f (u64 bits)
     int* flags_host = nullptr;   // pinned copy of the 8 flag words
@@ -408,6 +420,10 @@ void set_last_error(const std::string& msg);
 void configure_fused2d();
 size_t fused2d_smem(int N, int precision);
 void launch_fused2d(bn_solver* s);   // s->Qhat from s->Ghat / s->Ghat32
+bool beta_split_on(const bn_solver* s);   // the kernel-mode rounding correction applies to this solver
+// the fused-kernel arguments of the residual-table pass (tables, partials and S(b) buffers swapped)
+void fill_fused_args_lo(const bn_solver* s, void* out);
+void launch_add_modes(int nm, double2* Q, const double2* add, cudaStream_t st);   // Q += add
 
 // batched launches (bn_fused2d.cu): variant 0 = mixed N <= 32, 1 = mixed N = 64,
 // 2 = FP64 N <= 32, 3 = FP64 N = 64
@@ -415,7 +431,7 @@ int fused2d_variant(const bn_solver* s);
 int fused2d_partials(const bn_solver* s);   // CTAs (partial sums) of the solver's fused launch
 // sb: scratch of nExt float2 for S(b) (mixed N <= 32; may alias nothing else)
 void fused2d_into(const bn_solver* s, cudaStream_t st, const void* G, double2* partials, double2* Qhat, int* err,
-                  void* sb);
+                  void* sb, bool lo = false);   // lo: the residual-table pass
 void fill_fused_args(const bn_solver* s, void* out);   // FusedArgs<float> or <double> by precision
 size_t fused2d_variant_smem(int variant, int N);
 void launch_fused2d_group(cudaStream_t st, int variant, const void* d_jobs, const int* d_cta, int njobs, int total,

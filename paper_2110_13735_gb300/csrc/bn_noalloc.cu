@@ -2,7 +2,8 @@
 //
 // bn_eval_collision_device works in buffers that bn_create_solver allocated for the solver.
 // This variant takes its working memory (transform buffer, modes, FP32 modes, per-CTA
-// partial sums, combined modes, S(b) sums, error flag) from one file-scope device array instead, so
+// partial sums, combined modes, S(b) sums, the modes of the kernel-mode rounding correction, error
+// flag) from one file-scope device array instead, so
 // the call itself allocates nothing.  It is meant for callers that must not allocate at
 // evaluation time -- code running where cudaMalloc/cudaFree are not allowed or not wanted
 // (they synchronise the whole device, and fail when another allocator in the process has
@@ -91,7 +92,8 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
     const size_t o_g32 = align256(o_ghat + nm * sizeof(double2));
     const size_t o_qhat = align256(o_g32 + nm * sizeof(float2));
     const size_t o_sb = align256(o_qhat + nm * sizeof(double2));
-    const size_t o_part = align256(o_sb + (size_t)s->g.nExt * sizeof(float2));
+    const size_t o_qlo = align256(o_sb + (size_t)s->g.nExt * sizeof(float2));
+    const size_t o_part = align256(o_qlo + nm * sizeof(double2));
     const size_t need = o_part + (size_t)nPart * nm * sizeof(double2);
     if (need > kNoAllocScratchBytes) {
         char buf[200];
@@ -110,6 +112,7 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
     float2* g32 = reinterpret_cast<float2*>(b + o_g32);
     double2* qhat = reinterpret_cast<double2*>(b + o_qhat);
     double2* part = reinterpret_cast<double2*>(b + o_part);
+    double2* qlo = reinterpret_cast<double2*>(b + o_qlo);
     void* sb = b + o_sb;
     const bool mixed = s->opt.precision == BN_MIXED;
     cudaStream_t strm = (cudaStream_t)cuda_stream;
@@ -117,7 +120,13 @@ bn_status bn_eval_collision_noalloc(const bn_solver* s, const double* f_dev, dou
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), strm);   // the only state that must start at zero
     if (e == cudaSuccess) {
         bn::dft2_forward_into(s, strm, f_dev, work, ghat, mixed ? g32 : nullptr);
-        bn::fused2d_into(s, strm, mixed ? (const void*)g32 : (const void*)ghat, part, qhat, err, sb);
+        const void* gin = mixed ? (const void*)g32 : (const void*)ghat;
+        const bool lo = bn::beta_split_on(s);
+        // the kernel-mode rounding correction: the residual-table pass first (into qlo), then the
+        // main pass reuses the partials and S(b) scratch (stream order) and qlo is added to Q^
+        if (lo) bn::fused2d_into(s, strm, gin, part, qlo, err, sb, true);
+        bn::fused2d_into(s, strm, gin, part, qhat, err, sb);
+        if (lo) bn::launch_add_modes((int)nm, qhat, qlo, strm);
         bn::dft2_inverse_real_into(s, strm, qhat, work, Q_dev);
         if (s->opt.conserve) bn::launch_conserve_on(s, Q_dev, strm);
         e = cudaGetLastError();

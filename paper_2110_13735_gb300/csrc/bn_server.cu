@@ -34,6 +34,7 @@ struct ServerReq {
     std::vector<double> f0, result;
     int state = 0;   // 0 queued, 1 running, 2 done, 3 failed
     double t_submit = 0, t_admit = 0, t_done = 0;
+    double t_escalated = -1;   // solve time of the switch to FP64 (escalate_at), -1 if none
     long long steps_total = 0, steps_done = 0;
     double work = 0;   // estimated work: steps x terms of one evaluation
     bn_solver* s = nullptr;
@@ -52,8 +53,13 @@ bn_status sfail(bn_status st, const std::string& m) {
 size_t solver_bytes(const bn_request& r) {
     const size_t N = (size_t)r.N, nm = r.d == 2 ? N * N : N * N * N, nExt = r.d == 2 ? 4 * N * N : 8 * N * N * N;
     const size_t parts = 152 * 4;   // upper bound of the CTA partials
-    return nm * (6 * sizeof(double) + 7 * sizeof(double2) + sizeof(float2)) + nExt * sizeof(double2) +
-           parts * nm * sizeof(double2) + (1 << 16);
+    size_t b = nm * (6 * sizeof(double) + 7 * sizeof(double2) + sizeof(float2)) + nExt * sizeof(double2) +
+               parts * nm * sizeof(double2) + (1 << 16);
+    if (r.d == 2 && r.opt.beta_split && r.opt.precision == BN_MIXED)   // the residual-table pass's buffers
+        b += parts * nm * sizeof(double2) + nExt * sizeof(double2) + nm * sizeof(double2);
+    if (r.d == 3)   // the kernel-mode slices of one round: the slice budget (default at most 40 GiB)
+        b += r.opt.beta_budget_mb > 0 ? (size_t)r.opt.beta_budget_mb << 20 : (size_t)40 << 30;
+    return b;
 }
 
 // Bytes of the kernel-mode tables of an operator (mirrors acquire_tables).
@@ -62,9 +68,14 @@ size_t table_bytes(const bn_request& r) {
     const size_t M2d = (size_t)(r.opt.M > 0 ? r.opt.M : 2 * r.N);
     const size_t P = r.d == 2 ? (r.kernel == BN_HARD_SPHERE ? M2d * (size_t)(r.opt.M1 > 0 ? r.opt.M1 : r.N + 8) : M2d)
                               : (size_t)(r.opt.M1 > 0 ? r.opt.M1 : r.N / 2) * (r.opt.M2 > 0 ? r.opt.M2 : r.N / 2);
-    size_t b = 2 * P * nExt * sizeof(double) + nExt * nExt * (sizeof(double) + sizeof(float));
-    if (r.d == 2) b += nExt * nm * (sizeof(double) + 2 * sizeof(float));   // reducible and quadratic weights
-    if (r.d == 2 && r.N <= 32) b += nExt * nExt * sizeof(float);          // transposed FP32 table
+    size_t b = 2 * P * nExt * sizeof(double);
+    if (r.d == 2) {
+        // beta in FP64 and FP32, the reducible and quadratic weights, and the rounding residuals of the
+        // FP32 tables (kernel-mode rounding correction)
+        b += nExt * nExt * (sizeof(double) + 2 * sizeof(float));
+        b += nExt * nm * (sizeof(double) + 4 * sizeof(float));
+        if (r.N <= 32) b += 2 * nExt * nExt * sizeof(float);   // transposed FP32 table and its residuals
+    }
     return b;
 }
 
@@ -107,16 +118,19 @@ struct bn_server {
 
 void bn_server::retire(ServerReq* q, bool ok, const std::string& err) {
     // called without the lock; q is no longer in `active`
+    double t_esc = -1;
     if (ok && q->s) {
         q->result.resize(q->f0.size());
         if (bn_get_state(q->s, q->result.data(), q->result.size()) != BN_OK) {
             ok = false;
         }
+        bn_precision_state(q->s, nullptr, &t_esc, nullptr);
     }
     if (q->s) bn_destroy_solver(q->s);
     std::lock_guard<std::mutex> lock(mu);
     q->s = nullptr;
     q->t_done = now();
+    q->t_escalated = t_esc;
     q->state = ok ? 2 : 3;
     q->err = ok ? "" : (err.empty() ? std::string(bn_last_error()) : err);
     q->f0.clear();
@@ -296,6 +310,7 @@ bn_status bn_server_poll(bn_server* S, long long id, int* state, double* f_out, 
         times[0] = q->t_submit;
         times[1] = q->t_admit;
         times[2] = q->t_done;
+        if (ntimes >= 4) times[3] = q->t_escalated;
     }
     if (q->state == 2 && f_out) {
         if (count != q->result.size()) return sfail(BN_ERR_ARG, "count must be N^d");

@@ -165,7 +165,8 @@ __global__ void k_sw_table(int N, const double* __restrict__ beta, double* __res
 // Quadratic weights dq(b, a) = beta(a, b) - beta(b, b) for b in I_N (2-D), the difference taken in
 // FP64 and rounded to FP32 once (the FP32 difference of two rounded weights would carry the
 // rounding of beta itself, which is far larger than the difference for a near b).
-__global__ void k_dq_table(int N, const double* __restrict__ beta, float* __restrict__ dq32) {
+// dq32lo (the rounding residual of each weight) is written beside it.
+__global__ void k_dq_table(int N, const double* __restrict__ beta, float* __restrict__ dq32, float* __restrict__ dq32lo) {
     const int E = 2 * N, nExt = E * E, h = N / 2;
     const long long total = (long long)N * N * nExt;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -173,8 +174,18 @@ __global__ void k_dq_table(int N, const double* __restrict__ beta, float* __rest
         const int q = (int)(idx / nExt), ia = (int)(idx % nExt);
         const int b1 = q / N - h, b2 = q % N - h;
         const int ib = (b1 + N) * E + (b2 + N);
-        dq32[idx] = (float)(beta[(size_t)ib * nExt + ia] - beta[(size_t)ib * nExt + ib]);
+        const double v = beta[(size_t)ib * nExt + ia] - beta[(size_t)ib * nExt + ib];
+        const float hi = (float)v;
+        dq32[idx] = hi;
+        dq32lo[idx] = (float)(v - (double)hi);
     }
+}
+
+// Rounding residuals lo = fl32(x - hi) of an FP64 table x and its FP32 rounding hi (2-D).
+__global__ void k_residual_table(long long n, const double* __restrict__ x64, const float* __restrict__ hi,
+                                 float* __restrict__ lo) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        lo[i] = (float)(x64[i] - (double)hi[i]);
 }
 
 // FP32 table with the a axes swapped: betaT[b][a2][a1] = beta[b][a1][a2] (2-D).
@@ -296,17 +307,24 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     if (e == cudaSuccess && nDq) e = cudaMalloc(&t->dq32, sizeof(float) * nDq);
     const size_t nBT = d == 2 && s->g.N <= 32 ? nBeta : 0;
     if (e == cudaSuccess && nBT) e = cudaMalloc(&t->beta32T, sizeof(float) * nBT);
+    // the rounding residuals of the four FP32 tables (kernel-mode rounding correction)
+    if (e == cudaSuccess && nBeta) e = cudaMalloc(&t->beta32lo, sizeof(float) * nBeta);
+    if (e == cudaSuccess && nSw) e = cudaMalloc(&t->sw32lo, sizeof(float) * nSw);
+    if (e == cudaSuccess && nDq) e = cudaMalloc(&t->dq32lo, sizeof(float) * nDq);
+    if (e == cudaSuccess && nBT) e = cudaMalloc(&t->beta32Tlo, sizeof(float) * nBT);
     if (e != cudaSuccess) {
         *err = std::string("kernel-mode table allocation failed: ") + cudaGetErrorString(e);
         cudaFree(d_nodes);
         cudaFree(d_rad);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
         cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
+        cudaFree(t->beta32lo); cudaFree(t->sw32lo); cudaFree(t->dq32lo); cudaFree(t->beta32Tlo);
         delete t;
         cudaGetLastError();
         return BN_ERR_NOMEM;
     }
-    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + sizeof(float)) * (nBeta + nSw) + sizeof(float) * (nDq + nBT);
+    t->bytes = sizeof(double) * 2 * nAl + (sizeof(double) + 2 * sizeof(float)) * (nBeta + nSw) +
+               2 * sizeof(float) * (nDq + nBT);
     cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice, s->stream);
     if (d_rad) cudaMemcpyAsync(d_rad, rad.data(), sizeof(double2) * rad.size(), cudaMemcpyHostToDevice, s->stream);
     k_alpha_tables<<<1024, 256, 0, s->stream>>>(d, s->g.N, t->P, s->Rxi, s->opt.c_phi, s->kernel, (int)rad.size(),
@@ -326,6 +344,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
             cudaFree(d_rad);
             cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
             cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
+        cudaFree(t->beta32lo); cudaFree(t->sw32lo); cudaFree(t->dq32lo); cudaFree(t->beta32Tlo);
             cudaFree(t->alpha32); cudaFree(t->alphap32); cudaFree(t->alphaI64); cudaFree(t->alphapI64);
             cudaFree(t->alphaI32); cudaFree(t->alphapI32);
             delete t;
@@ -334,11 +353,14 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
     }
     if (nSw) {
         k_sw_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->sw64, t->sw32);
-        k_dq_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->dq32);
-        s->launches++;
+        k_dq_table<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta64, t->dq32, t->dq32lo);
+        k_residual_table<<<4096, 256, 0, s->stream>>>((long long)nBeta, t->beta64, t->beta32, t->beta32lo);
+        k_residual_table<<<4096, 256, 0, s->stream>>>((long long)nSw, t->sw64, t->sw32, t->sw32lo);
+        s->launches += 3;
         if (nBT) {
             k_beta_transpose<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta32, t->beta32T);
-            s->launches++;
+            k_beta_transpose<<<4096, 256, 0, s->stream>>>(s->g.N, t->beta32lo, t->beta32Tlo);
+            s->launches += 2;
         }
         s->launches++;
     }
@@ -350,6 +372,7 @@ bn_status acquire_tables(bn_solver* s, std::string* err) {
         *err = std::string("kernel-mode table build failed: ") + cudaGetErrorString(e);
         cudaFree(t->alpha64); cudaFree(t->alphap64); cudaFree(t->beta64); cudaFree(t->beta32);
         cudaFree(t->sw64); cudaFree(t->sw32); cudaFree(t->dq32); cudaFree(t->beta32T);
+        cudaFree(t->beta32lo); cudaFree(t->sw32lo); cudaFree(t->dq32lo); cudaFree(t->beta32Tlo);
         cudaFree(t->alpha32); cudaFree(t->alphap32); cudaFree(t->alphaI64); cudaFree(t->alphapI64);
         cudaFree(t->alphaI32); cudaFree(t->alphapI32);
         delete t;
@@ -374,6 +397,10 @@ void release_tables(KernelTables* t) {
     cudaFree(t->sw32);
     cudaFree(t->dq32);
     cudaFree(t->beta32T);
+    cudaFree(t->beta32lo);
+    cudaFree(t->sw32lo);
+    cudaFree(t->dq32lo);
+    cudaFree(t->beta32Tlo);
     cudaFree(t->alpha32);
     cudaFree(t->alphap32);
     cudaFree(t->alphaI64);

@@ -23,6 +23,12 @@ def test_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_struct_layouts_match_the_binding(lib):
+    """The binding declares bn_options and bn_request itself: their sizes must be the library's."""
+    assert lib.bn_options_bytes() == ctypes.sizeof(B.Options)
+    assert lib.bn_request_bytes() == ctypes.sizeof(B.Request)
+
+
 def test_default_options_and_last_error(lib):
     o = B.Options()
     assert lib.bn_default_options(ctypes.byref(o)) == 0

@@ -96,7 +96,9 @@ def test_server_admission_by_memory(B):
     and every request still completes."""
     N = 16
     nExt, nm, P = 4 * N * N, N * N, 2 * N
-    tables = 2 * P * nExt * 8 + nExt * nExt * 12 + nExt * nm * 12
+    # alpha tables; beta in FP64, FP32 and its FP32 residuals; the reducible (FP64, FP32, residual) and
+    # quadratic (FP32, residual) weights; the transposed FP32 table and its residuals (N <= 32)
+    tables = 2 * P * nExt * 8 + nExt * nExt * 16 + nExt * nm * 24 + 2 * nExt * nExt * 4
     solver = nm * (6 * 8 + 7 * 16 + 8) + nExt * 16 + 152 * 4 * nm * 16 + (1 << 16)
     with B.Server(device_bytes=tables + 2 * solver + 1024, max_active=16) as srv:
         ids = [srv.submit(2, N, T6, R6, B.MAXWELL, 1.0, _f0(N, k), 0.01, 0.02) for k in range(5)]
