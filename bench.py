@@ -258,9 +258,39 @@ def leg_3d(bn, I, which: str, steps: int, peak_fp32: float, **solver_opts):
     return out
 
 
+def leg_2d64(bn, I, evals: int, peak_fp32: float):
+    """The largest serving size alone: 2-D Maxwell molecules N=64, R=6, the Gaussian of mass 5 and
+    temperature 0.5 with eps=+1, mixed precision; `evals` evaluations after two warm-up ones, timed
+    with CUDA events on the solver's stream."""
+    import torch
+    N = 64
+    T = I.box_half_width(R_TRUNC)
+    stream = torch.cuda.Stream()
+    with bn.Solver(2, N, T, R_TRUNC, bn.MAXWELL, 1.0, stream=stream, precision=bn.MIXED) as s:
+        s.set_state(I.config1_boson_f0(N, R_TRUNC))
+        for _ in range(2):
+            s.eval_collision()
+        ms = []
+        for _ in range(evals):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.eval_collision_modes()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    terms = (2.0 * (N ** 3 - N) / 3.0) ** 2
+    t = float(np.median(ms))
+    return {"workload": "2-D Maxwell molecules N=64, Gaussian (mass 5, temperature 0.5), eps=+1, mixed precision",
+            "evaluations": evals, "ms_per_eval_median": t,
+            "achieved_tflops": 4.0 * terms / (t * 1e-3) / 1e12,
+            "frac": 4.0 * terms / (t * 1e-3) / 1e12 / peak_fp32,
+            "basis": "4 flop per Q_{1,q} term / whole-evaluation event time (transforms and partial sums included)"}
+
+
 def run_leg_only(args):
-    """One 3-D leg alone (`--only config2|config4`), printed as one JSON line: the profiling runs'
-    command, with the solver's slice budget and pair-weight mode set from the command line."""
+    """One leg alone (`--only config2|config4|2d64`), printed as one JSON line: the profiling runs'
+    command, with the 3-D solver's slice budget and pair-weight mode set from the command line."""
     import torch
     torch.cuda.set_device(0)
     from paper_2110_13735_gb300 import build as BUILD
@@ -268,6 +298,10 @@ def run_leg_only(args):
     from paper_2110_13735_gb300 import bn
     from paper_2110_13735_gb300 import inputs as I
     bn.load()
+    if args.only == "2d64":
+        peak = bn.measure_fma_peak(1, None)[0]
+        print(json.dumps({"leg": args.only, **leg_2d64(bn, I, max(3, args.steps), peak)}))
+        return
     opts = {}
     if args.beta_budget_mb > 0:
         opts["beta_budget_mb"] = args.beta_budget_mb
@@ -701,8 +735,9 @@ def main():
     ap.add_argument("--leg3d-steps", type=int, default=1,
                     help="timed RK4 steps of the 3-D N=32 configuration (0 = skip)")
     ap.add_argument("--leg48", action="store_true", help="also time one evaluation of the 3-D N=48 configuration")
-    ap.add_argument("--only", choices=["config2", "config4"],
-                    help="run one 3-D leg alone and print it (profiling runs)")
+    ap.add_argument("--only", choices=["config2", "config4", "2d64"],
+                    help="run one leg alone and print it (profiling runs): a 3-D configuration, or the 2-D "
+                         "N=64 mixed operator (--steps evaluations)")
     ap.add_argument("--beta-budget-mb", type=int, default=0,
                     help="with --only: device memory (MiB) for the kernel-mode slices of one round (0 = default)")
     ap.add_argument("--pair-weights", action="store_true",
