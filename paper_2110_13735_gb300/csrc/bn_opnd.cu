@@ -373,6 +373,9 @@ struct TripleNdArgs {
     int PP;                   // complex entries per P plane buffer
     int GP;                   // complex entries per staged mode plane (n1 n2; 0 when axis 0 is trivial)
     int T0max;
+    int gstage;               // 1: the two mode planes of each P plane are staged in shared memory by
+                              // bulk copies one step ahead; 0: P planes are built from global memory
+                              // (the planes stay L2-resident), leaving that shared memory to more CTAs
     int giveup_first;             // testing: 1 = each tile's first bounded wait gives up at once
     unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
 };
@@ -521,7 +524,7 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
         stage_plane(aHi, 0);
         // the first step needs P planes s0 = n0 - aHi for n0 in [t0, t0 + T0): only slo0 exists
         for (int s0 = max(B.slo[0], t0 - aHi); s0 <= min(shi0, t0 + T0 - 1 - aHi); ++s0) build_P(s0, -1);
-        {
+        if (A.gstage) {
             const int sN = t0 + T0 - aHi;
             if (aHi > aLo && sN <= shi0) fetch_modes(sN, 0);
         }
@@ -533,7 +536,9 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
             if (a0 > aLo) {
                 stage_plane(a0 - 1, slot ^ 1);
                 const int sNew = t0 + T0 - a0;   // first needed at step a0 - 1; its modes are in slot k
-                if (sNew <= shi0) {
+                if (sNew <= shi0 && !A.gstage) {
+                    build_P(sNew, -1);
+                } else if (sNew <= shi0) {
                     const int sNext = sNew + 1;
                     if (a0 - 1 > aLo && sNext <= shi0) fetch_modes(sNext, k ^ 1);
                     const bool giveup = a0 == aHi && A.giveup_first;
@@ -634,12 +639,12 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) k_triple_nd(TripleNdArgs A) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 1) k_triple_nd(TripleNdArgs A) {
     using C = typename CT<Real>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     NdShared sm;
     C* bufG = reinterpret_cast<C*>(smem_raw);
-    C* bufP = bufG + 4 * (size_t)A.GP;
+    C* bufP = bufG + (A.gstage ? 4 * (size_t)A.GP : 0);
     Real* bufB = reinterpret_cast<Real*>(bufP + (size_t)(A.T0max + 1) * A.PP);
     sm.G = bufG;
     sm.P = bufP;
@@ -1101,7 +1106,7 @@ struct NdRound {
 struct NdPlan {
     NdGeo g{};
     int RW = 8, threads = 256, T0 = 1, nCTA = 0;
-    int WS = 0, PB = 0, PS = 0, PP = 0, GP = 0;
+    int WS = 0, PB = 0, PS = 0, PP = 0, GP = 0, gstage = 1;
     size_t smem = 0, smem_pair = 0;
     int TXp = 4;
     int pair_threads = 256;
@@ -1313,25 +1318,40 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     p->PP = maxS1 * p->PS;
     p->GP = g.n[0] > 1 ? g.n[1] * g.n[2] : 0;
     const size_t Csz = 2 * (size_t)elem;
-    p->smem = 4 * (size_t)p->GP * Csz + (size_t)(p->T0 + 1) * p->PP * Csz + 2 * (size_t)p->PB * elem;
-    p->smem = (p->smem + 15) / 16 * 16 + 16;
-    if (p->smem > 227 * 1024) {
+    // shared memory with and without the staged mode planes (two slots of two planes).  The staging
+    // is dropped only when it leaves a single CTA per SM and dropping it admits a second: the P
+    // planes are then built from the L2-resident modes, on the critical path of each plane step
+    // (measured on the FP32 sweep: N=48, 1 -> 2 CTAs per SM, 68.5 -> 64.6 s per evaluation; N=32,
+    // 2 -> 3 CTAs per SM, 1554 -> 1678 ms, so N=32 keeps it)
+    const size_t base = (size_t)(p->T0 + 1) * p->PP * Csz + 2 * (size_t)p->PB * elem;
+    auto round16 = [](size_t b) { return (b + 15) / 16 * 16 + 16; };
+    const size_t with_g = round16(4 * (size_t)p->GP * Csz + base), without_g = round16(base);
+    if (without_g > 227 * 1024) {
         *err = "the 3-D kernel's staging does not fit in shared memory";
         return BN_ERR_UNSUPPORTED;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     if (sms <= 0) sms = 152;
-    int per_sm = 0;
-    if (fp32) {
-        configure_triple_nd<float>(p->smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<float>, p->threads, p->smem);
-    } else {
-        configure_triple_nd<double>(p->smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triple_nd<double>, p->threads, p->smem);
-    }
-    cudaGetLastError();
-    per_sm = std::max(1, per_sm);
+    auto occupancy = [&](size_t smem) {
+        if (smem > 227 * 1024) return 0;
+        int n = 0;
+        if (fp32) {
+            configure_triple_nd<float>(smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<float>, p->threads, smem);
+        } else {
+            configure_triple_nd<double>(smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<double>, p->threads, smem);
+        }
+        cudaGetLastError();
+        return n;
+    };
+    const int occ_g = p->GP > 0 ? occupancy(with_g) : 0, occ_ng = occupancy(without_g);
+    p->gstage = p->GP > 0 && (occ_g >= occ_ng || occ_g >= 2) ? 1 : 0;
+    p->smem = p->gstage ? with_g : without_g;
+    if (fp32) configure_triple_nd<float>(p->smem);
+    else configure_triple_nd<double>(p->smem);
+    int per_sm = std::max(1, p->gstage ? occ_g : occ_ng);
     p->nCTA = per_sm * sms;
 
     // b list and groups
@@ -1675,6 +1695,7 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
             TA.PP = p->PP;
             TA.GP = p->GP;
             TA.T0max = p->T0;
+            TA.gstage = p->gstage;
             TA.stamps = stamps;
             k_triple_nd<Real><<<p->nCTA, p->threads, p->smem, st>>>(TA);
             s->launches++;
