@@ -78,6 +78,9 @@ def load(path: str | None = None):
     lib.bn_work_counts.argtypes = [vp, dp, sz]
     lib.bn_precision_state.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp]
     lib.bn_kernel_config.argtypes = [vp, dp, sz]
+    lib.bn_rescale_set.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, sz, ctypes.c_double, ctypes.c_double]
+    lib.bn_step_rescaled.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.bn_rescale_get.argtypes = [vp, dp, sz]
     ip = ctypes.POINTER(ctypes.c_int)
     lib.bn_plan_mixed2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, sz, ip]
     lib.bn_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp, sz]
@@ -257,6 +260,20 @@ class Solver:
         out = np.zeros(7)
         _check(_lib.bn_kernel_config(self._h, _dptr(out), 7))
         return int(out[0]), int(out[1]), int(out[2]), tuple(float(x) for x in out[3:])
+
+    def rescale_set(self, L: float, omega: float, u, rho: float, e: float):
+        """Velocity rescaling (include/bn.h: bn_rescale_set): the state is G on the xi grid of a T = pi solver."""
+        uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        _check(_lib.bn_rescale_set(self._h, float(L), float(omega), _dptr(uu), uu.size, float(rho), float(e)))
+
+    def step_rescaled(self, dt: float, nsteps: int):
+        _check(_lib.bn_step_rescaled(self._h, float(dt), int(nsteps)))
+
+    def rescale_state(self) -> dict:
+        """{w, u, rho, e, T, z, t} of the rescaled solve (include/bn.h: bn_rescale_get)."""
+        out = np.zeros(8)
+        _check(_lib.bn_rescale_get(self._h, _dptr(out), 8))
+        return {"w": out[0], "u": out[1:3].copy(), "rho": out[3], "e": out[4], "T": out[5], "z": out[6], "t": out[7]}
 
     def precision_state(self):
         """(precision in use, time of the switch to FP64 or -1, max f after the last step)."""

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbn.so")
-SOURCES = ["bn_api.cu", "bn_tables.cu", "bn_transform.cu", "bn_sums.cu", "bn_fused2d.cu", "bn_fused2d_mixed.cu", "bn_batch.cu", "bn_server.cu", "bn_noalloc.cu", "bn_peak.cu", "bn_opnd.cu"]
+SOURCES = ["bn_api.cu", "bn_tables.cu", "bn_transform.cu", "bn_sums.cu", "bn_fused2d.cu", "bn_fused2d_mixed.cu", "bn_batch.cu", "bn_server.cu", "bn_noalloc.cu", "bn_peak.cu", "bn_opnd.cu", "bn_rescale.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

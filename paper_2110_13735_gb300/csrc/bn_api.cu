@@ -44,12 +44,14 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 
 void free_buffers(bn_solver* s) {
     void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->twiddle, s->S2, s->quad,
-                    s->red, s->q1q, s->partials, s->Qhat, s->partials_lo, s->S2lo, s->Qlo, s->moments, s->flags,
+                    s->red, s->q1q, s->partials, s->Qhat, s->partials_lo, s->S2lo, s->Qlo, s->resc_H, s->resc_M,
+                    s->resc_acc, s->resc_div, s->resc_mom, s->moments, s->flags,
                     s->work.items, s->work_quad.items,
                     s->work.meta[0], s->work.meta[1], s->work.meta[2], s->work.meta[3]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->flags_host) cudaFreeHost(s->flags_host);
+    if (s->resc_mom_host) cudaFreeHost(s->resc_mom_host);
     bn::free_nd(s);
 }
 
@@ -747,5 +749,111 @@ extern "C" bn_status bn_plan_shards(int d, int N, int wrap, int count, int* boun
         return fail(BN_ERR_ARG, "bn_plan_shards: d = 3, N even in [4, 48], wrap 0/1, 1 <= count <= N, nbounds >= count + 1");
     const std::vector<int> b = bn::shard_bounds_for(d, N, wrap, count);
     for (int i = 0; i <= count; ++i) bounds[i] = b[i];
+    return BN_OK;
+}
+
+// ------------------------------------------------------------------ velocity rescaling (Sec. 3)
+extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, size_t du, double rho, double e) {
+    if (!valid_solver(s) || !u) return fail(BN_ERR_ARG, "null solver or u");
+    if (s->g.d != 2 || s->nd)
+        return fail(BN_ERR_UNSUPPORTED, "velocity rescaling: 2-D solvers with the LINEAR truncation only");
+    if (std::fabs(s->T - M_PI) > 1e-12 * M_PI)
+        return fail(BN_ERR_ARG, "velocity rescaling: the solver's box must be T = pi (the rescaled variable xi)");
+    if (du != (size_t)s->g.d) return fail(BN_ERR_ARG, "velocity rescaling: u needs d components");
+    if (!(L > 0) || !(omega > 0) || !(rho > 0) || !(e > 0) || !std::isfinite(L) || !std::isfinite(omega) ||
+        !std::isfinite(rho) || !std::isfinite(e) || !std::isfinite(u[0]) || !std::isfinite(u[1]))
+        return fail(BN_ERR_ARG, "velocity rescaling: L, omega, rho, e must be finite and > 0, u finite");
+    const size_t n = s->g.nModes;
+    if (!s->resc_H) {
+        cudaError_t e2 = cudaMalloc((void**)&s->resc_H, n * sizeof(double));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_M, n * sizeof(double2));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_acc, n * sizeof(double2));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_div, n * sizeof(double));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_mom, 4 * sizeof(double));
+        if (e2 == cudaSuccess) e2 = cudaMallocHost((void**)&s->resc_mom_host, 4 * sizeof(double));
+        if (e2 != cudaSuccess) return cuda_fail(e2, "velocity rescaling buffers");
+    }
+    double T = 0, z = 0;
+    std::string err;
+    const bn_status st = bn::rescale_temperature(s->g.d, s->eps, rho, e, &T, &z, &err);
+    if (st != BN_OK) return fail(st, err);
+    s->resc = true;
+    s->resc_L = L;
+    s->resc_w = omega;
+    s->resc_u[0] = u[0];
+    s->resc_u[1] = u[1];
+    s->resc_rho = rho;
+    s->resc_e = e;
+    s->resc_T = T;
+    s->resc_z = z;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_rescale_get(const bn_solver* s, double* out, size_t count) {
+    if (!valid_solver(s) || !out || count < 8) return fail(BN_ERR_ARG, "null solver/out or count < 8");
+    if (!s->resc) return fail(BN_ERR_STATE, "velocity rescaling not set (bn_rescale_set)");
+    const double v[8] = {s->resc_w, s->resc_u[0], s->resc_u[1], s->resc_rho, s->resc_e, s->resc_T, s->resc_z, s->t};
+    std::copy(v, v + 8, out);
+    return BN_OK;
+}
+
+extern "C" bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps) {
+    if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
+    if (!s->resc) return fail(BN_ERR_STATE, "velocity rescaling not set (bn_rescale_set)");
+    if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
+    if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(BN_ERR_ARG, "dt must be > 0 and nsteps >= 0");
+    const int d = s->g.d, N = s->g.N;
+    const double eps0 = s->eps, gamma = s->kernel == BN_HARD_SPHERE ? 1.0 : 0.0;
+    const double dxi = std::pow(2.0 * M_PI / N, d);
+    cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
+    for (int step = 0; step < nsteps; ++step) {
+        const double sc = M_PI * s->resc_w / s->resc_L;
+        // step 2: Q^n of G^n with the rescaled quantum parameter
+        s->eps = eps0 * std::pow(sc, d);
+        s->lo_refresh = true;
+        eval_device(s, s->f, s->Qv);
+        s->eps = eps0;
+        bn::launch_resc_moments(s, s->Qv, s->resc_mom);
+        cudaMemcpyAsync(s->resc_mom_host, s->resc_mom, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        cudaMemcpyAsync(s->flags_host, s->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
+        if (s->flags_host[2]) {
+            cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
+            return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during the rescaled step");
+        }
+        const double* S = s->resc_mom_host;
+        if (!std::isfinite(S[0]) || !std::isfinite(S[1]) || !std::isfinite(S[2]) || !std::isfinite(S[3]))
+            return fail(BN_ERR_NONFINITE, "rescaled step: non-finite collision moments (state kept)");
+        // step 3(a): rho, u, e from the moments of Q^n
+        const double coef = dxi * std::pow(sc, -gamma);
+        const double rho1 = s->resc_rho + dt * coef * S[0];
+        double u1[2];
+        for (int c = 0; c < 2; ++c)
+            u1[c] = (s->resc_rho * s->resc_u[c] + dt * coef * (S[1 + c] / sc + s->resc_u[c] * S[0])) / rho1;
+        const double e1 = (s->resc_rho * s->resc_e + dt * 0.5 * coef * S[3] / (sc * sc)) / rho1;
+        // step 3(b), (c): temperature, fugacity, scale
+        double T1 = 0, z1 = 0;
+        std::string err;
+        const bn_status st = bn::rescale_temperature(d, eps0, rho1, e1, &T1, &z1, &err);
+        if (st != BN_OK) return fail(st, err + " (state kept)");
+        const double w1 = eps0 != 0.0 ? std::sqrt(T1) : std::sqrt(T1 + (u1[0] * u1[0] + u1[1] * u1[1]) / d);
+        // steps 4, 5: the divergence term and G^{n+1}
+        const double a = (w1 - s->resc_w) / (dt * s->resc_w);
+        const double b[2] = {sc * (u1[0] - s->resc_u[0]) / dt, sc * (u1[1] - s->resc_u[1]) / dt};
+        bn::launch_resc_advance(s, s->f, s->Qv, a, b, dt, std::pow(sc, -gamma), s->resc_H, s->resc_M, s->resc_acc,
+                                s->resc_div);
+        s->resc_rho = rho1;
+        s->resc_u[0] = u1[0];
+        s->resc_u[1] = u1[1];
+        s->resc_e = e1;
+        s->resc_T = T1;
+        s->resc_z = z1;
+        s->resc_w = w1;
+        s->t += dt;
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
     return BN_OK;
 }

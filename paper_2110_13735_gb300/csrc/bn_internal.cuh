@@ -312,6 +312,17 @@ struct bn_solver {
     double2* S2lo = nullptr;
     double2* Qlo = nullptr;
     bool lo_refresh = true;      // recompute Qlo in the next evaluation (cleared for RK stages 2..4)
+    // velocity rescaling (bn_rescale_set, bn_step_rescaled): the state is G on the grid of [-pi, pi]^d;
+    // L the velocity box of scale 1, w the velocity scale, u the mean velocity, rho, e, T, z the
+    // moments, temperature and fugacity; scratch for the divergence term and the moments of Q
+    bool resc = false;
+    double resc_L = 0, resc_w = 1, resc_u[3] = {0, 0, 0}, resc_rho = 0, resc_e = 0, resc_T = 0, resc_z = 0;
+    double* resc_H = nullptr;
+    double2* resc_M = nullptr;
+    double2* resc_acc = nullptr;
+    double* resc_div = nullptr;
+    double* resc_mom = nullptr;       // device [4]
+    double* resc_mom_host = nullptr;  // pinned [4]
     double* moments = nullptr;   // d+6
     int* flags = nullptr;        // [0] non-finite, [1] committed steps, [2] wait timeout, [4..5] max f (u64 bits)
     int* flags_host = nullptr;   // pinned copy of the 8 flag words
@@ -424,6 +435,11 @@ bool beta_split_on(const bn_solver* s);   // the kernel-mode rounding correction
 // the fused-kernel arguments of the residual-table pass (tables, partials and S(b) buffers swapped)
 void fill_fused_args_lo(const bn_solver* s, void* out);
 void launch_add_modes(int nm, double2* Q, const double2* add, cudaStream_t st);   // Q += add
+// velocity rescaling (bn_rescale.cu)
+bn_status rescale_temperature(int d, double eps, double rho, double e, double* T, double* z, std::string* err);
+void launch_resc_moments(bn_solver* s, const double* Q, double* out_dev);
+void launch_resc_advance(bn_solver* s, double* G, const double* Q, double a, const double* b, double dt, double qc,
+                         double* H, double2* M, double2* acc, double* div);
 
 // batched launches (bn_fused2d.cu): variant 0 = mixed N <= 32, 1 = mixed N = 64,
 // 2 = FP64 N <= 32, 3 = FP64 N = 64

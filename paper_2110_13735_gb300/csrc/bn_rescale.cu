@@ -1,0 +1,253 @@
+// bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D: the kernels of one
+// forward Euler step of Sec. 3.3 around the operator evaluation, and the host-side temperature solve.
+//
+// The state is G on the grid xi_j = 2 pi j / N of [-pi, pi]^2 (the solver's box T = pi), with
+// f(v) = (pi w / L)^2 G((pi w / L)(v - u)).  Per step (bn_step_rescaled in bn_api.cu):
+//   Q^n = Q_{eps (pi w / L)^2}(G^n)                         (the solver's operator, eps rescaled)
+//   S0, S1, S2 = sum_j Q^n_j (1, xi_j, |xi_j|^2)           (k_resc_moments, fixed order, FP64)
+//   rho, u, e advanced with them; T, z solved; w = sqrt(T) (quantum) or sqrt(T + |u|^2/2)
+//   div = sum_c d/dxi_c ((a xi_c - b_c) G^n): per component the flux (k_resc_flux), its modes, times
+//         i k_c (k_resc_deriv; the k_c = -N/2 mode gets 0), summed, transformed back
+//   G^{n+1} = G^n + dt (-div + (pi w / L)^{-gamma} Q^n)   (k_resc_update)
+// The temperature solve (step 3(b) of Sec. 3.3; Sec. 1.2): T = 2e/d classically; for eps != 0,
+// x = |eps| rho (d / (4 pi e))^{d/2} must lie in I_eq, then z solves x = K_1(z)^2 / K_2(z) by Brent's
+// method (on mu = ln z for Fermi-Dirac particles) and T = |eps| rho / (2 pi K_1(z)); K_1 and K_2 are
+// the Fermi-Dirac (eps < 0) or Bose-Einstein (eps > 0) integrals of orders 1 and 2: ln(1 + z) or
+// -ln(1 - z), and -Li_2(-z) or Li_2(z).
+#include <cmath>
+#include <string>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+namespace {
+
+constexpr int kResThreads = 256;
+
+// sums over the grid of Q, xi_0 Q, xi_1 Q, |xi|^2 Q (one block, fixed order: deterministic)
+__global__ void __launch_bounds__(kResThreads) k_resc_moments(int N, const double* __restrict__ Q, double* __restrict__ out) {
+    __shared__ double sh[4][kResThreads];
+    const int n = N * N, tid = threadIdx.x;
+    const double h = 2.0 * M_PI / N;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int j = tid; j < n; j += kResThreads) {
+        const double x0 = h * (j / N - N / 2), x1 = h * (j % N - N / 2), q = Q[j];
+        s0 += q;
+        s1 = fma(x0, q, s1);
+        s2 = fma(x1, q, s2);
+        s3 = fma(x0 * x0 + x1 * x1, q, s3);
+    }
+    sh[0][tid] = s0;
+    sh[1][tid] = s1;
+    sh[2][tid] = s2;
+    sh[3][tid] = s3;
+    __syncthreads();
+    for (int st = kResThreads / 2; st >= 1; st >>= 1) {
+        if (tid < st)
+            for (int c = 0; c < 4; ++c) sh[c][tid] += sh[c][tid + st];
+        __syncthreads();
+    }
+    if (tid < 4) out[tid] = sh[tid][0];
+}
+
+// H = (a xi_c - b) G, component c of the rescaling flux
+__global__ void k_resc_flux(int N, const double* __restrict__ G, double a, double b, int c, double* __restrict__ H) {
+    const int n = N * N;
+    const double h = 2.0 * M_PI / N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double x = h * ((c == 0 ? j / N : j % N) - N / 2);
+        H[j] = (a * x - b) * G[j];
+    }
+}
+
+// acc (+)= i k_c M: the modes of the derivative along axis c (k in I_N; the k_c = -N/2 mode gets 0)
+__global__ void k_resc_deriv(int N, const double2* __restrict__ M, double2* __restrict__ acc, int c, int first) {
+    const int n = N * N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int k = (c == 0 ? j / N : j % N) - N / 2;
+        const double kk = k == -N / 2 ? 0.0 : (double)k;
+        const double2 m = M[j];
+        const double2 v = make_double2(-kk * m.y, kk * m.x);
+        if (first) {
+            acc[j] = v;
+        } else {
+            double2 t = acc[j];
+            t.x += v.x;
+            t.y += v.y;
+            acc[j] = t;
+        }
+    }
+}
+
+// G += dt (-div + qc Q)
+__global__ void k_resc_update(int n, double* __restrict__ G, const double* __restrict__ div, const double* __restrict__ Q,
+                              double dt, double qc) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        G[j] = fma(dt, fma(qc, Q[j], -div[j]), G[j]);
+}
+
+inline int blocks_for(int n) { return (n + kResThreads - 1) / kResThreads; }
+
+// ------------------------------------------------------------------ host: dilogarithm, K, Brent
+// Li_2(x) for x <= 1: the series sum x^k / k^2 for |x| <= 1/2; Euler's reflection
+// Li_2(x) = pi^2/6 - ln(x) ln(1 - x) - Li_2(1 - x) on (1/2, 1]; Landen's identity
+// Li_2(x) = -Li_2(x / (x - 1)) - ln(1 - x)^2 / 2 on [-1, -1/2); the inversion
+// Li_2(x) = -pi^2/6 - ln(-x)^2 / 2 - Li_2(1 / x) below -1.
+double li2_series(double x) {
+    double total = 0.0, term = x;
+    for (int k = 1; k < 200; ++k) {
+        const double add = term / ((double)k * k);
+        total += add;
+        if (std::fabs(add) <= 1e-18 * std::fabs(total)) break;
+        term *= x;
+    }
+    return total;
+}
+
+double li2(double x) {
+    const double pi2_6 = M_PI * M_PI / 6.0;
+    if (x == 1.0) return pi2_6;
+    if (std::fabs(x) <= 0.5) return li2_series(x);
+    if (x > 0.5) return pi2_6 - std::log(x) * std::log1p(-x) - li2_series(1.0 - x);
+    if (x >= -1.0) {
+        const double l = std::log1p(-x);
+        return -li2_series(x / (x - 1.0)) - 0.5 * l * l;
+    }
+    const double l = std::log(-x);
+    return -pi2_6 - 0.5 * l * l - li2(1.0 / x);
+}
+
+// K_nu(z), nu = 1, 2: Fermi-Dirac (eps < 0) or Bose-Einstein (eps > 0, 0 < z < 1)
+double k_nu(int nu, double z, double eps) {
+    if (eps < 0) return nu == 1 ? std::log1p(z) : -li2(-z);
+    return nu == 1 ? -std::log1p(-z) : li2(z);
+}
+
+// Brent's root finder on [a, b] with f(a) f(b) < 0: inverse quadratic interpolation or the secant
+// step when it stays inside the bracket and shrinks it fast enough, bisection otherwise.
+template <typename F>
+bool brent(F f, double a, double b, double tol, double* root) {
+    double fa = f(a), fb = f(b);
+    if (!(fa * fb <= 0.0) || !std::isfinite(fa) || !std::isfinite(fb)) return false;
+    if (std::fabs(fa) < std::fabs(fb)) {
+        std::swap(a, b);
+        std::swap(fa, fb);
+    }
+    double c = a, fc = fa, d = b - a, e = d;
+    for (int it = 0; it < 300; ++it) {
+        if (fb == 0.0) break;
+        if ((fb > 0) == (fc > 0)) {   // keep the root between b and c
+            c = a;
+            fc = fa;
+            d = e = b - a;
+        }
+        if (std::fabs(fc) < std::fabs(fb)) {
+            a = b; b = c; c = a;
+            fa = fb; fb = fc; fc = fa;
+        }
+        const double m = 0.5 * (c - b);
+        const double t = 2.0 * 2.2e-16 * std::fabs(b) + 0.5 * tol;
+        if (std::fabs(m) <= t) break;
+        if (std::fabs(e) >= t && std::fabs(fa) > std::fabs(fb)) {
+            double p, q;
+            const double s = fb / fa;
+            if (a == c) {   // secant
+                p = 2.0 * m * s;
+                q = 1.0 - s;
+            } else {        // inverse quadratic interpolation through a, b, c
+                const double qa = fa / fc, r = fb / fc;
+                p = s * (2.0 * m * qa * (qa - r) - (b - a) * (r - 1.0));
+                q = (qa - 1.0) * (r - 1.0) * (s - 1.0);
+            }
+            if (p > 0) q = -q;
+            else p = -p;
+            if (2.0 * p < std::min(3.0 * m * q - std::fabs(t * q), std::fabs(e * q))) {
+                e = d;
+                d = p / q;
+            } else {
+                d = m;
+                e = m;
+            }
+        } else {
+            d = m;
+            e = m;
+        }
+        a = b;
+        fa = fb;
+        b += std::fabs(d) > t ? d : (m > 0 ? t : -t);
+        fb = f(b);
+    }
+    *root = b;
+    return std::isfinite(b);
+}
+
+}  // namespace
+
+bn_status rescale_temperature(int d, double eps, double rho, double e, double* T, double* z, std::string* err) {
+    if (!(rho > 0) || !(e > 0) || !std::isfinite(rho) || !std::isfinite(e)) {
+        *err = "rescaling: non-positive or non-finite mass or internal energy";
+        return BN_ERR_STATE;
+    }
+    if (eps == 0.0) {
+        *T = 2.0 * e / d;
+        *z = 0.0;
+        return BN_OK;
+    }
+    if (d != 2) {
+        *err = "rescaling: the quantum temperature solve is 2-D";
+        return BN_ERR_UNSUPPORTED;
+    }
+    const double x = std::fabs(eps) * rho * (d / (4.0 * M_PI * e));
+    double zz = 0.0;
+    bool ok;
+    if (eps < 0) {
+        if (!(x > 0.0 && x < 2.0)) {
+            *err = "rescaling: Fermi-Dirac moments outside I_eq (degenerate state)";
+            return BN_ERR_STATE;
+        }
+        auto g = [&](double mu) {
+            const double zz1 = std::exp(mu);
+            const double k1 = k_nu(1, zz1, eps);
+            return k1 * k1 / k_nu(2, zz1, eps) - x;
+        };
+        double mu = 0.0;
+        ok = brent(g, -60.0, 60.0, 1e-15, &mu);
+        zz = std::exp(mu);
+    } else {
+        auto g = [&](double zz1) {
+            const double k1 = k_nu(1, zz1, eps);
+            return k1 * k1 / k_nu(2, zz1, eps) - x;
+        };
+        ok = brent(g, 1e-300, 1.0 - 1e-16, 1e-300, &zz);
+    }
+    if (!ok || !(zz > 0)) {
+        *err = "rescaling: the fugacity equation has no root in its bracket";
+        return BN_ERR_STATE;
+    }
+    *z = zz;
+    *T = std::fabs(eps) * rho / k_nu(1, zz, eps) / (2.0 * M_PI);
+    return BN_OK;
+}
+
+void launch_resc_moments(bn_solver* s, const double* Q, double* out_dev) {
+    k_resc_moments<<<1, kResThreads, 0, s->stream>>>(s->g.N, Q, out_dev);
+    s->launches++;
+}
+
+// div = sum_c d/dxi_c ((a xi_c - b_c) G) into `div`, then G += dt (-div + qc Q).
+void launch_resc_advance(bn_solver* s, double* G, const double* Q, double a, const double* b, double dt, double qc,
+                         double* H, double2* M, double2* acc, double* div) {
+    const int N = s->g.N, n = s->g.nModes;
+    for (int c = 0; c < 2; ++c) {
+        k_resc_flux<<<blocks_for(n), kResThreads, 0, s->stream>>>(N, G, a, b[c], c, H);
+        launch_dft_forward(s, H, M);
+        k_resc_deriv<<<blocks_for(n), kResThreads, 0, s->stream>>>(N, M, acc, c, c == 0);
+        s->launches += 2;
+    }
+    launch_dft_inverse_real(s, acc, div, 1.0);
+    k_resc_update<<<blocks_for(n), kResThreads, 0, s->stream>>>(n, G, div, Q, dt, qc);
+    s->launches++;
+}
+
+}  // namespace bn

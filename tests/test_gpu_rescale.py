@@ -1,0 +1,110 @@
+"""The velocity-rescaling method on the GPU (include/bn.h: bn_rescale_set, bn_step_rescaled) against
+the FP64 oracle of the same procedure (oracle/rescaling.py; Mouton & Rey, Sec. 3.3, forward Euler).
+
+Setup as in Sec. 4.1: the initial datum discretised on the velocity grid of scale 1 centred on its
+mean gives the discrete mass, mean velocity and internal energy, hence the temperature (and fugacity)
+and the scale w0 = sqrt(T0) (quantum) or sqrt(T0 + |u0|^2 / 2) (classical); G0 = (L / (pi w0))^2
+f0(L xi / (pi w0) + u0) on the grid of [-pi, pi]^2, R = S = 2 pi / (3 + sqrt 2).  Several steps on both
+sides; FP64: the state G and (w, u, rho, e) within 1e-12, mixed precision within 1e-6.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import rescaling as RS
+
+pytestmark = pytest.mark.gpu
+
+S_TRUNC = 2.0 * math.pi / (3.0 + math.sqrt(2.0))
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_13735_gb300 import build as BUILD
+    BUILD.build()
+    from paper_2110_13735_gb300 import bn
+    bn.load()
+    return bn
+
+
+def f0(v, amp):
+    """Two Gaussian bumps (not an equilibrium), max below 1/|eps| for the quantum cases."""
+    r1 = np.sum((v - [0.8, 0.3]) ** 2, -1)
+    r2 = np.sum((v + [0.6, 0.5]) ** 2, -1)
+    return amp * (np.exp(-r1 / 0.8) + 0.7 * np.exp(-r2 / 0.5))
+
+
+def initial(N, L, eps, amp):
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, indexing="ij"), -1)
+    f = f0(v, amp)
+    dv = (2.0 * L / N) ** 2
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1)) * dv / rho
+    # the grid of scale 1 centred on the discrete mean (Sec. 4.1, steps 2-3)
+    vc = v + u
+    fc = f0(vc, amp)
+    rho = fc.sum() * dv
+    e = 0.5 * (np.sum((vc - u) ** 2, -1) * fc).sum() * dv / rho
+    T, _ = RS.temperature(2, eps, rho, e)
+    w = RS.omega_of(2, eps, T, u)
+    s = math.pi * w / L
+    G = f0(u + RS.xi_grid(2, N) / s, amp) / s ** 2
+    return G, rho, u, e, w
+
+
+CASES = [  # (N, L, kernel, eps, amp, precision, tolerance, start off the scale)
+    (16, 4.0, 0, -9.0, 0.06, "fp64", 1e-12, False),
+    (16, 4.0, 0, -9.0, 0.06, "fp64", 1e-12, True),
+    (16, 5.0, 0, 9.0, 0.01, "fp64", 1e-12, False),
+    (16, 5.0, 0, 0.0, 0.3, "fp64", 1e-12, True),
+    (12, 4.0, 1, -9.0, 0.06, "fp64", 1e-12, False),
+    (16, 4.0, 0, -9.0, 0.06, "mixed", 1e-6, True),
+]
+
+
+@pytest.mark.parametrize("N,L,kernel,eps,amp,precision,tol,off", CASES)
+def test_rescaled_steps_match_the_oracle(B, N, L, kernel, eps, amp, precision, tol, off):
+    """`off`: the solve starts with w 25 % above sqrt(T) and u shifted, so that the first step moves
+    the scale and the mean velocity by a lot and the divergence term carries real weight."""
+    dt, steps = 0.01, 4
+    G, rho, u, e, w = initial(N, L, eps, amp)
+    if off:
+        w, u = 1.25 * w, u + np.array([0.1, -0.05])
+    run = RS.RescaledRun(N, L, S_TRUNC, kernel, eps, G, rho, u, e, w)
+    for _ in range(steps):
+        run.step(dt)
+    prec = B.FP64 if precision == "fp64" else B.MIXED
+    with B.Solver(2, N, math.pi, S_TRUNC, kernel, eps, precision=prec) as s:
+        s.set_state(G)
+        s.rescale_set(L, w, u, rho, e)
+        s.step_rescaled(dt, steps)
+        Gg = s.get_state().reshape(N, N)
+        st = s.rescale_state()
+    assert np.linalg.norm(Gg - run.G) <= tol * np.linalg.norm(run.G)
+    assert st["w"] == pytest.approx(run.w, rel=tol)
+    assert np.allclose(st["u"], run.u, rtol=tol, atol=tol * (abs(run.u).max() + w))
+    assert st["rho"] == pytest.approx(run.rho, rel=tol) and st["e"] == pytest.approx(run.e, rel=tol)
+    assert st["t"] == pytest.approx(steps * dt)
+    assert w != run.w   # the scale moved: the divergence term was exercised
+
+
+def test_rescaling_arguments_and_degenerate_state(B):
+    with B.Solver(2, 16, 4.0, 1.0, 0, -9.0) as s:
+        with pytest.raises(B.BNError) as ei:          # the box must be T = pi
+            s.rescale_set(4.0, 1.0, [0.0, 0.0], 1.0, 1.0)
+        assert ei.value.status == -1
+    with B.Solver(2, 16, math.pi, S_TRUNC, 0, -9.0) as s:
+        s.set_state(np.full((16, 16), 0.01))
+        with pytest.raises(B.BNError) as ei:
+            s.step_rescaled(0.01, 1)                  # before bn_rescale_set
+        assert ei.value.status == -7
+        with pytest.raises(B.BNError) as ei:          # 2-D Fermi-Dirac: |eps| rho / (2 pi e) >= 2
+            s.rescale_set(4.0, 1.0, [0.0, 0.0], 1.0, 9.0 / (2 * math.pi * 2.5))
+        assert ei.value.status == -7
