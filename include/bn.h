@@ -254,21 +254,23 @@ bn_status bn_profile_nd(bn_solver* s, double* out, size_t count);
 bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f);
 
 /* Velocity rescaling (Sec. 3 of the paper; the velocity rescaling method of Sec. 3.2 with
- * lambda = mu = 1), 2-D LINEAR solvers.  The solver must have been created with T = pi: its state
- * (bn_set_state / bn_get_state) is then G on the grid xi_j = 2 pi j / N of [-pi, pi]^2 (row-major,
- * j in I_N), with f(t, v) = (pi w / L)^2 G(t, (pi w / L)(v - u)), i.e. f_j = (pi w / L)^2 G_j at the
- * velocities v_j = u + 2 L j / (N w); R is the kernel truncation in xi.
+ * lambda = mu = 1), LINEAR solvers: 2-D, and 3-D with eps = 0 (the quantum temperature solve is
+ * 2-D).  The solver must have been created with T = pi: its state (bn_set_state / bn_get_state) is
+ * then G on the grid xi_j = 2 pi j / N of [-pi, pi]^d (row-major, j in I_N), with
+ * f(t, v) = (pi w / L)^d G(t, (pi w / L)(v - u)), i.e. f_j = (pi w / L)^d G_j at the velocities
+ * v_j = u + 2 L j / (N w); R is the kernel truncation in xi.
  * bn_rescale_set: L > 0 the half-width of the velocity box at w = 1, omega > 0 the scale w, u the mean
- * velocity (du = 2 values), rho, e > 0 the mass and internal energy of the state; also solves the
- * temperature (and the fugacity).  Allocates the step's scratch (5 arrays of N^2) once.
- * BN_ERR_ARG for bad values or T != pi, BN_ERR_UNSUPPORTED for 3-D or CIRCULAR solvers, BN_ERR_STATE
- * when the moments admit no temperature (2-D Fermi-Dirac: |eps| rho / (2 pi e) >= 2). */
+ * velocity (du = d values), rho, e > 0 the mass and internal energy of the state; also solves the
+ * temperature (and the fugacity).  Allocates the step's scratch (4 arrays of N^d) once.
+ * BN_ERR_ARG for bad values or T != pi, BN_ERR_UNSUPPORTED for CIRCULAR or sharded solvers and
+ * 3-D with eps != 0, BN_ERR_STATE when the moments admit no temperature (2-D Fermi-Dirac:
+ * |eps| rho / (2 pi e) >= 2). */
 bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, size_t du, double rho, double e);
 
 /* nsteps forward Euler steps of the procedure of Sec. 3.3: Q of G with the quantum parameter
- * eps (pi w / L)^2; rho, u, e advanced with the moments of Q (Delta xi = (2 pi / N)^2, the
+ * eps (pi w / L)^d; rho, u, e advanced with the moments of Q (Delta xi = (2 pi / N)^d, the
  * collision frequency of d_t f = Q(f)); T (and z: Brent's method on the equilibrium relations,
- * mu = ln z for fermions) and w = sqrt(T) (quantum) or sqrt(T + |u|^2 / 2) (classical); the
+ * mu = ln z for fermions) and w = sqrt(T) (quantum) or sqrt(T + |u|^2 / d) (classical); the
  * divergence term div(((w' - w) / (dt w) xi - (pi w / L)(u' - u) / dt) G) by spectral
  * differentiation (the k_c = -N/2 mode of each derivative set to 0); G += dt (-div +
  * (pi w / L)^{-gamma} Q).  One host synchronisation per step (the moments of Q).  BN_ERR_STATE when
@@ -276,8 +278,8 @@ bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, 
  * state of the start of that step), BN_ERR_TIMEOUT as for bn_eval_collision. */
 bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps);
 
-/* out[0..7] = [w, u_0, u_1, rho, e, T, z, t] of the rescaled solve (z = 0 classically); count >= 8.
- * BN_ERR_STATE before bn_rescale_set. */
+/* out[0..8] = [w, u_0, u_1, u_2, rho, e, T, z, t] of the rescaled solve (u_2 = 0 in 2-D, z = 0
+ * classically); count >= 9.  BN_ERR_STATE before bn_rescale_set. */
 bn_status bn_rescale_get(const bn_solver* s, double* out, size_t count);
 
 /* Kernel configuration of the operator: out[0] = outputs per thread of the fused

@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D.
+"""FP64 CPU oracle of the velocity-rescaling method (Mouton & Rey, Sec. 3): 2-D, and 3-D classical.
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package: the product library never imports it.
 
@@ -116,17 +116,19 @@ def spectral_divergence(H: np.ndarray) -> np.ndarray:
 
 
 class RescaledRun:
-    """The state of one rescaled solve (2-D): G on the xi grid, rho, u, e, w, and the operator
-    (box pi, truncation R) whose eps is set to eps (pi w / L)^d before every evaluation."""
+    """The state of one rescaled solve (d = 2, or d = 3 classically): G on the xi grid, rho, u, e, w,
+    and the operator (box pi, truncation R) whose eps is set to eps (pi w / L)^d before every
+    evaluation; `op_kw` goes to the operator (3-D: M1, M2)."""
 
-    def __init__(self, N: int, L: float, R: float, kernel: int, eps: float, G, rho: float, u, e: float, w: float):
-        self.d, self.N, self.L, self.eps = 2, int(N), float(L), float(eps)
+    def __init__(self, N: int, L: float, R: float, kernel: int, eps: float, G, rho: float, u, e: float, w: float,
+                 d: int = 2, **op_kw):
+        self.d, self.N, self.L, self.eps = int(d), int(N), float(L), float(eps)
         self.gamma = 1 if kernel == 1 else 0
-        self.op = Operator(2, self.N, math.pi, R, kernel, 0.0)
-        self.G = np.array(G, dtype=np.float64).reshape((self.N,) * 2)
+        self.op = Operator(self.d, self.N, math.pi, R, kernel, 0.0, **op_kw)
+        self.G = np.array(G, dtype=np.float64).reshape((self.N,) * self.d)
         self.rho, self.u, self.e, self.w = float(rho), np.array(u, dtype=np.float64), float(e), float(w)
         self.T, self.z = None, None
-        self.xi = xi_grid(2, self.N)
+        self.xi = xi_grid(self.d, self.N)
 
     def scale(self) -> float:
         return math.pi * self.w / self.L

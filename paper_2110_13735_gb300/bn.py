@@ -271,9 +271,10 @@ class Solver:
 
     def rescale_state(self) -> dict:
         """{w, u, rho, e, T, z, t} of the rescaled solve (include/bn.h: bn_rescale_get)."""
-        out = np.zeros(8)
-        _check(_lib.bn_rescale_get(self._h, _dptr(out), 8))
-        return {"w": out[0], "u": out[1:3].copy(), "rho": out[3], "e": out[4], "T": out[5], "z": out[6], "t": out[7]}
+        out = np.zeros(9)
+        _check(_lib.bn_rescale_get(self._h, _dptr(out), 9))
+        return {"w": out[0], "u": out[1:1 + self.d].copy(), "rho": out[4], "e": out[5], "T": out[6], "z": out[7],
+                "t": out[8]}
 
     def precision_state(self):
         """(precision in use, time of the switch to FP64 or -1, max f after the last step)."""

@@ -755,13 +755,15 @@ extern "C" bn_status bn_plan_shards(int d, int N, int wrap, int count, int* boun
 // ------------------------------------------------------------------ velocity rescaling (Sec. 3)
 extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, size_t du, double rho, double e) {
     if (!valid_solver(s) || !u) return fail(BN_ERR_ARG, "null solver or u");
-    if (s->g.d != 2 || s->nd)
-        return fail(BN_ERR_UNSUPPORTED, "velocity rescaling: 2-D solvers with the LINEAR truncation only");
+    if (s->opt.wrap || s->opt.shard_count > 1)
+        return fail(BN_ERR_UNSUPPORTED, "velocity rescaling: LINEAR truncation, unsharded solvers only");
     if (std::fabs(s->T - M_PI) > 1e-12 * M_PI)
         return fail(BN_ERR_ARG, "velocity rescaling: the solver's box must be T = pi (the rescaled variable xi)");
     if (du != (size_t)s->g.d) return fail(BN_ERR_ARG, "velocity rescaling: u needs d components");
+    bool ufin = true;
+    for (int c = 0; c < s->g.d; ++c) ufin = ufin && std::isfinite(u[c]);
     if (!(L > 0) || !(omega > 0) || !(rho > 0) || !(e > 0) || !std::isfinite(L) || !std::isfinite(omega) ||
-        !std::isfinite(rho) || !std::isfinite(e) || !std::isfinite(u[0]) || !std::isfinite(u[1]))
+        !std::isfinite(rho) || !std::isfinite(e) || !ufin)
         return fail(BN_ERR_ARG, "velocity rescaling: L, omega, rho, e must be finite and > 0, u finite");
     const size_t n = s->g.nModes;
     if (!s->resc_H) {
@@ -769,8 +771,8 @@ extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const 
         if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_M, n * sizeof(double2));
         if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_acc, n * sizeof(double2));
         if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_div, n * sizeof(double));
-        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_mom, 4 * sizeof(double));
-        if (e2 == cudaSuccess) e2 = cudaMallocHost((void**)&s->resc_mom_host, 4 * sizeof(double));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&s->resc_mom, 5 * sizeof(double));
+        if (e2 == cudaSuccess) e2 = cudaMallocHost((void**)&s->resc_mom_host, 5 * sizeof(double));
         if (e2 != cudaSuccess) return cuda_fail(e2, "velocity rescaling buffers");
     }
     double T = 0, z = 0;
@@ -780,8 +782,7 @@ extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const 
     s->resc = true;
     s->resc_L = L;
     s->resc_w = omega;
-    s->resc_u[0] = u[0];
-    s->resc_u[1] = u[1];
+    for (int c = 0; c < 3; ++c) s->resc_u[c] = c < s->g.d ? u[c] : 0.0;
     s->resc_rho = rho;
     s->resc_e = e;
     s->resc_T = T;
@@ -790,10 +791,11 @@ extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const 
 }
 
 extern "C" bn_status bn_rescale_get(const bn_solver* s, double* out, size_t count) {
-    if (!valid_solver(s) || !out || count < 8) return fail(BN_ERR_ARG, "null solver/out or count < 8");
+    if (!valid_solver(s) || !out || count < 9) return fail(BN_ERR_ARG, "null solver/out or count < 9");
     if (!s->resc) return fail(BN_ERR_STATE, "velocity rescaling not set (bn_rescale_set)");
-    const double v[8] = {s->resc_w, s->resc_u[0], s->resc_u[1], s->resc_rho, s->resc_e, s->resc_T, s->resc_z, s->t};
-    std::copy(v, v + 8, out);
+    const double v[9] = {s->resc_w, s->resc_u[0], s->resc_u[1], s->resc_u[2], s->resc_rho, s->resc_e, s->resc_T,
+                         s->resc_z, s->t};
+    std::copy(v, v + 9, out);
     return BN_OK;
 }
 
@@ -814,7 +816,7 @@ extern "C" bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps) {
         eval_device(s, s->f, s->Qv);
         s->eps = eps0;
         bn::launch_resc_moments(s, s->Qv, s->resc_mom);
-        cudaMemcpyAsync(s->resc_mom_host, s->resc_mom, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        cudaMemcpyAsync(s->resc_mom_host, s->resc_mom, (d + 2) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
         cudaMemcpyAsync(s->flags_host, s->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
         cudaError_t e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
@@ -822,30 +824,33 @@ extern "C" bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps) {
             cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
             return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during the rescaled step");
         }
-        const double* S = s->resc_mom_host;
-        if (!std::isfinite(S[0]) || !std::isfinite(S[1]) || !std::isfinite(S[2]) || !std::isfinite(S[3]))
-            return fail(BN_ERR_NONFINITE, "rescaled step: non-finite collision moments (state kept)");
+        const double* S = s->resc_mom_host;   // [sum Q, sum xi_c Q (c < d), sum |xi|^2 Q]
+        bool fin = true;
+        for (int c = 0; c < d + 2; ++c) fin = fin && std::isfinite(S[c]);
+        if (!fin) return fail(BN_ERR_NONFINITE, "rescaled step: non-finite collision moments (state kept)");
         // step 3(a): rho, u, e from the moments of Q^n
         const double coef = dxi * std::pow(sc, -gamma);
         const double rho1 = s->resc_rho + dt * coef * S[0];
-        double u1[2];
-        for (int c = 0; c < 2; ++c)
+        double u1[3] = {0, 0, 0}, u2 = 0;
+        for (int c = 0; c < d; ++c) {
             u1[c] = (s->resc_rho * s->resc_u[c] + dt * coef * (S[1 + c] / sc + s->resc_u[c] * S[0])) / rho1;
-        const double e1 = (s->resc_rho * s->resc_e + dt * 0.5 * coef * S[3] / (sc * sc)) / rho1;
+            u2 += u1[c] * u1[c];
+        }
+        const double e1 = (s->resc_rho * s->resc_e + dt * 0.5 * coef * S[1 + d] / (sc * sc)) / rho1;
         // step 3(b), (c): temperature, fugacity, scale
         double T1 = 0, z1 = 0;
         std::string err;
         const bn_status st = bn::rescale_temperature(d, eps0, rho1, e1, &T1, &z1, &err);
         if (st != BN_OK) return fail(st, err + " (state kept)");
-        const double w1 = eps0 != 0.0 ? std::sqrt(T1) : std::sqrt(T1 + (u1[0] * u1[0] + u1[1] * u1[1]) / d);
+        const double w1 = eps0 != 0.0 ? std::sqrt(T1) : std::sqrt(T1 + u2 / d);
         // steps 4, 5: the divergence term and G^{n+1}
         const double a = (w1 - s->resc_w) / (dt * s->resc_w);
-        const double b[2] = {sc * (u1[0] - s->resc_u[0]) / dt, sc * (u1[1] - s->resc_u[1]) / dt};
+        double b[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) b[c] = sc * (u1[c] - s->resc_u[c]) / dt;
         bn::launch_resc_advance(s, s->f, s->Qv, a, b, dt, std::pow(sc, -gamma), s->resc_H, s->resc_M, s->resc_acc,
                                 s->resc_div);
         s->resc_rho = rho1;
-        s->resc_u[0] = u1[0];
-        s->resc_u[1] = u1[1];
+        for (int c = 0; c < 3; ++c) s->resc_u[c] = u1[c];
         s->resc_e = e1;
         s->resc_T = T1;
         s->resc_z = z1;

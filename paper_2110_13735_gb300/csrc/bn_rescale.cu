@@ -1,11 +1,11 @@
-// bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D: the kernels of one
+// bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D and 3-D classical: the kernels of one
 // forward Euler step of Sec. 3.3 around the operator evaluation, and the host-side temperature solve.
 //
-// The state is G on the grid xi_j = 2 pi j / N of [-pi, pi]^2 (the solver's box T = pi), with
-// f(v) = (pi w / L)^2 G((pi w / L)(v - u)).  Per step (bn_step_rescaled in bn_api.cu):
-//   Q^n = Q_{eps (pi w / L)^2}(G^n)                         (the solver's operator, eps rescaled)
+// The state is G on the grid xi_j = 2 pi j / N of [-pi, pi]^d (the solver's box T = pi), with
+// f(v) = (pi w / L)^d G((pi w / L)(v - u)).  Per step (bn_step_rescaled in bn_api.cu):
+//   Q^n = Q_{eps (pi w / L)^d}(G^n)                         (the solver's operator, eps rescaled)
 //   S0, S1, S2 = sum_j Q^n_j (1, xi_j, |xi_j|^2)           (k_resc_moments, fixed order, FP64)
-//   rho, u, e advanced with them; T, z solved; w = sqrt(T) (quantum) or sqrt(T + |u|^2/2)
+//   rho, u, e advanced with them; T, z solved; w = sqrt(T) (quantum) or sqrt(T + |u|^2/d)
 //   div = sum_c d/dxi_c ((a xi_c - b_c) G^n): per component the flux (k_resc_flux), its modes, times
 //         i k_c (k_resc_deriv; the k_c = -N/2 mode gets 0), summed, transformed back
 //   G^{n+1} = G^n + dt (-div + (pi w / L)^{-gamma} Q^n)   (k_resc_update)
@@ -25,47 +25,54 @@ namespace {
 
 constexpr int kResThreads = 256;
 
-// sums over the grid of Q, xi_0 Q, xi_1 Q, |xi|^2 Q (one block, fixed order: deterministic)
-__global__ void __launch_bounds__(kResThreads) k_resc_moments(int N, const double* __restrict__ Q, double* __restrict__ out) {
-    __shared__ double sh[4][kResThreads];
-    const int n = N * N, tid = threadIdx.x;
+// coordinate c of grid index j in d dimensions (axis 0 slowest), shifted to I_N
+__device__ __forceinline__ int coord(int j, int c, int d, int N) {
+    for (int a = d - 1; a > c; --a) j /= N;
+    return j % N - N / 2;
+}
+
+// sums over the grid of Q, xi_c Q (c < d), |xi|^2 Q into out[0], out[1..d], out[d+1] (one block,
+// fixed order: deterministic)
+__global__ void __launch_bounds__(kResThreads) k_resc_moments(int d, int N, const double* __restrict__ Q,
+                                                              double* __restrict__ out) {
+    __shared__ double sh[5][kResThreads];
+    const int n = d == 2 ? N * N : N * N * N, tid = threadIdx.x;
     const double h = 2.0 * M_PI / N;
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    double acc[5] = {0, 0, 0, 0, 0};
     for (int j = tid; j < n; j += kResThreads) {
-        const double x0 = h * (j / N - N / 2), x1 = h * (j % N - N / 2), q = Q[j];
-        s0 += q;
-        s1 = fma(x0, q, s1);
-        s2 = fma(x1, q, s2);
-        s3 = fma(x0 * x0 + x1 * x1, q, s3);
+        const double q = Q[j];
+        double r2 = 0.0;
+        acc[0] += q;
+        for (int c = 0; c < d; ++c) {
+            const double x = h * coord(j, c, d, N);
+            acc[1 + c] = fma(x, q, acc[1 + c]);
+            r2 = fma(x, x, r2);
+        }
+        acc[1 + d] = fma(r2, q, acc[1 + d]);
     }
-    sh[0][tid] = s0;
-    sh[1][tid] = s1;
-    sh[2][tid] = s2;
-    sh[3][tid] = s3;
+    for (int c = 0; c < 5; ++c) sh[c][tid] = acc[c];
     __syncthreads();
     for (int st = kResThreads / 2; st >= 1; st >>= 1) {
         if (tid < st)
-            for (int c = 0; c < 4; ++c) sh[c][tid] += sh[c][tid + st];
+            for (int c = 0; c < 5; ++c) sh[c][tid] += sh[c][tid + st];
         __syncthreads();
     }
-    if (tid < 4) out[tid] = sh[tid][0];
+    if (tid < d + 2) out[tid] = sh[tid][0];
 }
 
 // H = (a xi_c - b) G, component c of the rescaling flux
-__global__ void k_resc_flux(int N, const double* __restrict__ G, double a, double b, int c, double* __restrict__ H) {
-    const int n = N * N;
+__global__ void k_resc_flux(int d, int N, int n, const double* __restrict__ G, double a, double b, int c,
+                            double* __restrict__ H) {
     const double h = 2.0 * M_PI / N;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const double x = h * ((c == 0 ? j / N : j % N) - N / 2);
-        H[j] = (a * x - b) * G[j];
-    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        H[j] = (a * (h * coord(j, c, d, N)) - b) * G[j];
 }
 
 // acc (+)= i k_c M: the modes of the derivative along axis c (k in I_N; the k_c = -N/2 mode gets 0)
-__global__ void k_resc_deriv(int N, const double2* __restrict__ M, double2* __restrict__ acc, int c, int first) {
-    const int n = N * N;
+__global__ void k_resc_deriv(int d, int N, int n, const double2* __restrict__ M, double2* __restrict__ acc, int c,
+                             int first) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int k = (c == 0 ? j / N : j % N) - N / 2;
+        const int k = coord(j, c, d, N);
         const double kk = k == -N / 2 ? 0.0 : (double)k;
         const double2 m = M[j];
         const double2 v = make_double2(-kk * m.y, kk * m.x);
@@ -231,18 +238,18 @@ bn_status rescale_temperature(int d, double eps, double rho, double e, double* T
 }
 
 void launch_resc_moments(bn_solver* s, const double* Q, double* out_dev) {
-    k_resc_moments<<<1, kResThreads, 0, s->stream>>>(s->g.N, Q, out_dev);
+    k_resc_moments<<<1, kResThreads, 0, s->stream>>>(s->g.d, s->g.N, Q, out_dev);
     s->launches++;
 }
 
 // div = sum_c d/dxi_c ((a xi_c - b_c) G) into `div`, then G += dt (-div + qc Q).
 void launch_resc_advance(bn_solver* s, double* G, const double* Q, double a, const double* b, double dt, double qc,
                          double* H, double2* M, double2* acc, double* div) {
-    const int N = s->g.N, n = s->g.nModes;
-    for (int c = 0; c < 2; ++c) {
-        k_resc_flux<<<blocks_for(n), kResThreads, 0, s->stream>>>(N, G, a, b[c], c, H);
+    const int d = s->g.d, N = s->g.N, n = s->g.nModes;
+    for (int c = 0; c < d; ++c) {
+        k_resc_flux<<<blocks_for(n), kResThreads, 0, s->stream>>>(d, N, n, G, a, b[c], c, H);
         launch_dft_forward(s, H, M);
-        k_resc_deriv<<<blocks_for(n), kResThreads, 0, s->stream>>>(N, M, acc, c, c == 0);
+        k_resc_deriv<<<blocks_for(n), kResThreads, 0, s->stream>>>(d, N, n, M, acc, c, c == 0);
         s->launches += 2;
     }
     launch_dft_inverse_real(s, acc, div, 1.0);

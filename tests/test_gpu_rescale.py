@@ -95,6 +95,42 @@ def test_rescaled_steps_match_the_oracle(B, N, L, kernel, eps, amp, precision, t
     assert w != run.w   # the scale moved: the divergence term was exercised
 
 
+def test_rescaled_steps_3d_classical(B):
+    """3-D hard spheres, eps = 0 (the classical temperature T = 2e/3), N = 8, started off the scale."""
+    N, L, dt, steps = 8, 4.0, 0.01, 3
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, j, indexing="ij"), -1)
+
+    def g0(x):
+        return 0.3 * np.exp(-np.sum((x - [0.5, 0.2, -0.1]) ** 2, -1) / 0.9) + \
+            0.2 * np.exp(-np.sum((x + [0.4, 0.3, 0.0]) ** 2, -1) / 0.6)
+
+    dv = (2.0 * L / N) ** 3
+    f = g0(v)
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1, 2)) * dv / rho
+    e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
+    T, _ = RS.temperature(3, 0.0, rho, e)
+    w = 1.2 * RS.omega_of(3, 0.0, T, u)
+    s = math.pi * w / L
+    G = g0(u + RS.xi_grid(3, N) / s) / s ** 3
+    run = RS.RescaledRun(N, L, S_TRUNC, 1, 0.0, G, rho, u, e, w, d=3, M1=4, M2=4)
+    for _ in range(steps):
+        run.step(dt)
+    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, 0.0, precision=B.FP64, M1=4, M2=4) as sol:
+        sol.set_state(G)
+        sol.rescale_set(L, w, u, rho, e)
+        sol.step_rescaled(dt, steps)
+        Gg = sol.get_state().reshape((N,) * 3)
+        st = sol.rescale_state()
+    assert np.linalg.norm(Gg - run.G) <= 1e-12 * np.linalg.norm(run.G)
+    assert st["w"] == pytest.approx(run.w, rel=1e-12) and np.allclose(st["u"], run.u, rtol=1e-12, atol=1e-13)
+    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, 1.0, M1=4, M2=4) as sol:
+        with pytest.raises(B.BNError) as ei:          # the quantum temperature solve is 2-D
+            sol.rescale_set(L, 1.0, [0.0, 0.0, 0.0], 1.0, 1.0)
+        assert ei.value.status == -8
+
+
 def test_rescaling_arguments_and_degenerate_state(B):
     with B.Solver(2, 16, 4.0, 1.0, 0, -9.0) as s:
         with pytest.raises(B.BNError) as ei:          # the box must be T = pi

@@ -64,20 +64,22 @@ def test_spectral_divergence_closed_form():
     assert np.abs(div - exact).max() <= 1e-9 * np.abs(exact).max()
 
 
-@pytest.mark.parametrize("kernel,eps", [(0, 0.0), (0, -9.0), (1, 9.0)])
-def test_operator_scaling_identity(kernel, eps):
+@pytest.mark.parametrize("d,kernel,eps", [(2, 0, 0.0), (2, 0, -9.0), (2, 1, 9.0), (3, 1, 0.0), (3, 1, -2.0)])
+def test_operator_scaling_identity(d, kernel, eps):
     """Q_eps(f)(v) = (pi w/L)^{d - gamma} Q_{eps (pi w/L)^d}(G)(xi) for f = (pi w/L)^d G on the grid
     v = u + L xi / (pi w): the velocity-box operator (T = L/w, R = S L / (pi w)) against the xi-box
     operator (T = pi, R = S)."""
-    N, L, w = 12, 5.0, 0.8
+    N, L, w = (12, 5.0, 0.8) if d == 2 else (6, 5.0, 0.8)
+    kw = {} if d == 2 else dict(M1=4, M2=4)
     s = math.pi * w / L
-    xi = RS.xi_grid(2, N)
-    G = 0.05 * np.exp(-np.sum((xi - [0.3, -0.1]) ** 2, -1) / 0.6) * (1 + 0.3 * np.cos(xi[..., 0]))
+    xi = RS.xi_grid(d, N)
+    c = np.array([0.3, -0.1, 0.2][:d])
+    G = 0.05 * np.exp(-np.sum((xi - c) ** 2, -1) / 0.6) * (1 + 0.3 * np.cos(xi[..., 0]))
     gamma = 1 if kernel == 1 else 0
-    op_xi = O.Operator(2, N, math.pi, S_TRUNC, kernel, eps * s ** 2)
-    op_v = O.Operator(2, N, L / w, S_TRUNC / s, kernel, eps)
-    rhs = s ** (2 - gamma) * op_xi.eval_collision(G)
-    lhs = op_v.eval_collision(s ** 2 * G)
+    op_xi = O.Operator(d, N, math.pi, S_TRUNC, kernel, eps * s ** d, **kw)
+    op_v = O.Operator(d, N, L / w, S_TRUNC / s, kernel, eps, **kw)
+    rhs = s ** (d - gamma) * op_xi.eval_collision(G)
+    lhs = op_v.eval_collision(s ** d * G)
     assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
 
 
