@@ -374,8 +374,9 @@ struct TripleNdArgs {
     int GP;                   // complex entries per staged mode plane (n1 n2; 0 when axis 0 is trivial)
     int T0max;
     int gstage;               // 1: the two mode planes of each P plane are staged in shared memory by
-                              // bulk copies one step ahead; 0: P planes are built from global memory
-                              // (the planes stay L2-resident), leaving that shared memory to more CTAs
+                              // bulk copies one step ahead (kernel instance GS = true); 0: P planes are
+                              // built from global memory (L2-resident), leaving that shared memory to
+                              // more CTAs
     int giveup_first;             // testing: 1 = each tile's first bounded wait gives up at once
     unsigned long long* stamps;   // optional [2]: first CTA start / last CTA end (%globaltimer)
 };
@@ -416,8 +417,8 @@ struct NdShared {
 // n_1; RW outputs per thread along axis 2 and the s_1 range split over J lanes.  For each tile the
 // CTA walks the planes a_0 of the slice: the rows of plane a_0 the tile needs are copied into
 // shared memory while the previous plane is swept, and the P plane first needed at the next step
-// is built from mode planes fetched (bulk copy) one step earlier.
-template <typename Real, int RW>
+// is built from mode planes fetched (bulk copy) one step earlier (GS), or from global memory.
+template <typename Real, int RW, bool GS>
 __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem& item, const NdShared& sm,
                                             uint32_t& phases) {
     using C = typename CT<Real>::C;
@@ -524,7 +525,7 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
         stage_plane(aHi, 0);
         // the first step needs P planes s0 = n0 - aHi for n0 in [t0, t0 + T0): only slo0 exists
         for (int s0 = max(B.slo[0], t0 - aHi); s0 <= min(shi0, t0 + T0 - 1 - aHi); ++s0) build_P(s0, -1);
-        if (A.gstage) {
+        if constexpr (GS) {
             const int sN = t0 + T0 - aHi;
             if (aHi > aLo && sN <= shi0) fetch_modes(sN, 0);
         }
@@ -536,8 +537,8 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
             if (a0 > aLo) {
                 stage_plane(a0 - 1, slot ^ 1);
                 const int sNew = t0 + T0 - a0;   // first needed at step a0 - 1; its modes are in slot k
-                if (sNew <= shi0 && !A.gstage) {
-                    build_P(sNew, -1);
+                if (!GS) {
+                    if (sNew <= shi0) build_P(sNew, -1);
                 } else if (sNew <= shi0) {
                     const int sNext = sNew + 1;
                     if (a0 - 1 > aLo && sNext <= shi0) fetch_modes(sNext, k ^ 1);
@@ -638,13 +639,16 @@ __device__ __forceinline__ void triple_item(const TripleNdArgs& A, const NdItem&
     }
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 1) k_triple_nd(TripleNdArgs A) {
+// GS: mode planes staged in shared memory (else the P planes are built from global memory).  FP32:
+// up to 128 registers, 2 CTAs per SM (the staging instance is held there by its shared memory at
+// N = 32 anyway; capped at 80 registers for a third CTA it ran 25 % slower).
+template <typename Real, bool GS>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) k_triple_nd(TripleNdArgs A) {
     using C = typename CT<Real>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     NdShared sm;
     C* bufG = reinterpret_cast<C*>(smem_raw);
-    C* bufP = bufG + (A.gstage ? 4 * (size_t)A.GP : 0);
+    C* bufP = bufG + (GS ? 4 * (size_t)A.GP : 0);
     Real* bufB = reinterpret_cast<Real*>(bufP + (size_t)(A.T0max + 1) * A.PP);
     sm.G = bufG;
     sm.P = bufP;
@@ -662,10 +666,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 1) k_triple_nd(Tr
     for (int it = it0; it < it1; ++it) {
         const NdItem item = A.items[it];
         if constexpr (sizeof(Real) == 4) {
-            if (item.RW == 8) triple_item<Real, 8>(A, item, sm, phases);
-            else triple_item<Real, 4>(A, item, sm, phases);
+            if (item.RW == 8) triple_item<Real, 8, GS>(A, item, sm, phases);
+            else triple_item<Real, 4, GS>(A, item, sm, phases);
         } else {
-            triple_item<Real, 4>(A, item, sm, phases);
+            triple_item<Real, 4, GS>(A, item, sm, phases);
         }
     }
     // every bulk copy issued was waited for (each fetch is consumed one step later) and every
@@ -1205,7 +1209,8 @@ void free_nd(bn_solver* s) {
 
 template <typename Real>
 static void configure_triple_nd(size_t smem) {
-    cudaFuncSetAttribute(k_triple_nd<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_triple_nd<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_triple_nd<Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 template <typename Real, int TX>
 static void configure_pair_nd(size_t smem) {
@@ -1321,8 +1326,8 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     // shared memory with and without the staged mode planes (two slots of two planes).  The staging
     // is dropped only when it leaves a single CTA per SM and dropping it admits a second: the P
     // planes are then built from the L2-resident modes, on the critical path of each plane step
-    // (measured on the FP32 sweep: N=48, 1 -> 2 CTAs per SM, 68.5 -> 64.6 s per evaluation; N=32,
-    // 2 -> 3 CTAs per SM, 1554 -> 1678 ms, so N=32 keeps it)
+    // (measured on the FP32 sweep: N=48, 1 -> 2 CTAs per SM, 68.5 -> 54.7 s per evaluation; N=32,
+    // where both forms hold 2 CTAs per SM, 1488 ms with the staging against 1533 ms without)
     const size_t base = (size_t)(p->T0 + 1) * p->PP * Csz + 2 * (size_t)p->PB * elem;
     auto round16 = [](size_t b) { return (b + 15) / 16 * 16 + 16; };
     const size_t with_g = round16(4 * (size_t)p->GP * Csz + base), without_g = round16(base);
@@ -1333,20 +1338,22 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     if (sms <= 0) sms = 152;
-    auto occupancy = [&](size_t smem) {
+    auto occupancy = [&](size_t smem, bool gs) {
         if (smem > 227 * 1024) return 0;
         int n = 0;
         if (fp32) {
             configure_triple_nd<float>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<float>, p->threads, smem);
+            if (gs) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<float, true>, p->threads, smem);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<float, false>, p->threads, smem);
         } else {
             configure_triple_nd<double>(smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<double>, p->threads, smem);
+            if (gs) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<double, true>, p->threads, smem);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_triple_nd<double, false>, p->threads, smem);
         }
         cudaGetLastError();
         return n;
     };
-    const int occ_g = p->GP > 0 ? occupancy(with_g) : 0, occ_ng = occupancy(without_g);
+    const int occ_g = p->GP > 0 ? occupancy(with_g, true) : 0, occ_ng = occupancy(without_g, false);
     p->gstage = p->GP > 0 && (occ_g >= occ_ng || occ_g >= 2) ? 1 : 0;
     p->smem = p->gstage ? with_g : without_g;
     if (fp32) configure_triple_nd<float>(p->smem);
@@ -1697,7 +1704,8 @@ static void launch_nd_t(bn_solver* s, cudaStream_t st, int slot) {
             TA.T0max = p->T0;
             TA.gstage = p->gstage;
             TA.stamps = stamps;
-            k_triple_nd<Real><<<p->nCTA, p->threads, p->smem, st>>>(TA);
+            if (p->gstage) k_triple_nd<Real, true><<<p->nCTA, p->threads, p->smem, st>>>(TA);
+            else k_triple_nd<Real, false><<<p->nCTA, p->threads, p->smem, st>>>(TA);
             s->launches++;
             mark(7 + 4 * (int)r);
         }
