@@ -1306,7 +1306,10 @@ bn_status plan_nd(bn_solver* s, std::string* err) {
     // FP64), planes per item (T0 <= T0max) and s_1 split (J) are chosen on the host below
     p->RW = fp32 ? 8 : 4;                    // the widest RW (sizes the staged row slack)
     const int RW = p->RW;
-    p->T0 = N > 32 ? 1 : 3;                  // T0max: the P-plane ring holds T0max + 1 planes
+    // T0max: the P-plane ring holds T0max + 1 planes; at N <= 32 four output planes share a staged
+    // slice plane (sweep per N=32 evaluation: T0max 3, 4, 6 -> 1488, 1450, 1469 ms); at N = 48 a
+    // second P plane would leave one CTA per SM
+    p->T0 = N > 32 ? 1 : 4;
     p->threads = 256;
     // largest slice plane and P plane; staged rows at odd strides (distinct banks for the rows a
     // warp sweeps)
