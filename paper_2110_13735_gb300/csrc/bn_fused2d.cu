@@ -74,9 +74,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-// threads per CTA of the mixed-precision kernel for N > 32 (one CTA per SM, limited by shared memory:
-// 32 warps hide the shared-load latency of the sweep better than 8)
-constexpr int kBigNT = 1024;
+// threads per CTA of the mixed-precision kernel for N > 32 (one CTA per SM, limited by shared memory):
+// 24 warps of up to 85 registers (N = 64 evaluation: 4.12, 3.61, 3.95, 4.08 ms at 640, 768, 896,
+// 1024 threads; 1024 threads leave 64 registers, 512 hide the shared-load latency worse)
+constexpr int kBigNT = 768;
 
 
 
