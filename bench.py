@@ -258,6 +258,63 @@ def leg_3d(bn, I, which: str, steps: int, peak_fp32: float, **solver_opts):
     return out
 
 
+def leg_rescale(bn, I, steps: int, peak_fp32: float):
+    """The velocity-rescaling method (Sec. 3.3, forward Euler) on a 2-D Fermi-Dirac solve: N=32,
+    hbar = 3 (eps = -9), Maxwell molecules, L = 4, R = S = 2 pi / (3 + sqrt 2) on the xi box, mixed
+    precision, two Gaussian bumps (not an equilibrium) started off the scale (w 25 % above sqrt(T)).
+    Times `steps` rescaled steps (each: one operator evaluation, the moments of Q brought to the host,
+    the temperature solve, the spectral divergence and the update) against plain evaluations of the
+    same operator, both by CUDA events around the calls."""
+    import torch
+    N, L, eps = 32, 4.0, -9.0
+    S = 2.0 * math.pi / (3.0 + math.sqrt(2.0))
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, indexing="ij"), -1)
+
+    def f0(x):
+        return 0.06 * (np.exp(-np.sum((x - [0.8, 0.3]) ** 2, -1) / 0.8) +
+                       0.7 * np.exp(-np.sum((x + [0.6, 0.5]) ** 2, -1) / 0.5))
+
+    dv = (2.0 * L / N) ** 2
+    f = f0(v)
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1)) * dv / rho
+    e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
+    stream = torch.cuda.Stream()
+    with bn.Solver(2, N, math.pi, S, bn.MAXWELL, eps, stream=stream, precision=bn.MIXED) as s:
+        s.set_state(f)   # any state: sized for the first evaluation
+        w = 1.0
+        s.rescale_set(L, w, u, rho, e)
+        T = s.rescale_state()["T"]
+        w = 1.25 * math.sqrt(T)
+        sc = math.pi * w / L
+        xi = np.stack(np.meshgrid(*(2 * [np.arange(-N // 2, N // 2) * (2 * math.pi / N)]), indexing="ij"), -1)
+        s.set_state(f0(u + xi / sc) / sc ** 2)
+        s.rescale_set(L, w, u, rho, e)
+        s.step_rescaled(0.01, 2)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_rescaled(0.01, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / steps
+        st = s.rescale_state()
+        e0.record(stream)
+        for _ in range(steps):
+            s.eval_collision_modes()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eval_ms = e0.elapsed_time(e1) / steps
+    terms = lemma_terms(2, N, True)
+    return {"workload": "2-D Fermi-Dirac (hbar = 3) N=32, velocity rescaling (forward Euler), L = 4, mixed precision",
+            "steps": steps, "ms_per_step": step_ms, "ms_per_plain_evaluation": eval_ms,
+            "rescaling_overhead": step_ms / eval_ms - 1.0,
+            "value": terms / (step_ms * 1e-3), "unit": UNIT,
+            "sweep_fraction_of_peak_bound": 4.0 * (2.0 * (N ** 3 - N) / 3.0) ** 2 / (step_ms * 1e-3) / 1e12 / peak_fp32,
+            "after": {"w": st["w"], "T": st["T"], "z": st["z"], "t": st["t"]}}
+
+
 def leg_2d64(bn, I, evals: int, peak_fp32: float):
     """The largest serving size alone: 2-D Maxwell molecules N=64, R=6, the Gaussian of mass 5 and
     temperature 0.5 with eps=+1, mixed precision; `evals` evaluations after two warm-up ones, timed
@@ -298,9 +355,11 @@ def run_leg_only(args):
     from paper_2110_13735_gb300 import bn
     from paper_2110_13735_gb300 import inputs as I
     bn.load()
-    if args.only == "2d64":
+    if args.only in ("2d64", "rescale"):
         peak = bn.measure_fma_peak(1, None)[0]
-        print(json.dumps({"leg": args.only, **leg_2d64(bn, I, max(3, args.steps), peak)}))
+        leg = leg_2d64(bn, I, max(3, args.steps), peak) if args.only == "2d64" else \
+            leg_rescale(bn, I, max(3, args.leg_rescale), peak)
+        print(json.dumps({"leg": args.only, **leg}))
         return
     opts = {}
     if args.beta_budget_mb > 0:
@@ -469,6 +528,8 @@ def run_ours(args):
         legs["config2_3d_n32"] = leg_3d(bn, I, "config2", args.leg3d_steps, peaks["fp32x2"])
     if args.leg48 and ws == 1:
         legs["config4_3d_n48"] = leg_3d(bn, I, "config4", 1, peaks["fp32x2"])
+    if args.leg_rescale > 0 and ws == 1:
+        legs["rescaling_2d_n32"] = leg_rescale(bn, I, args.leg_rescale, peaks["fp32x2"])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -735,7 +796,9 @@ def main():
     ap.add_argument("--leg3d-steps", type=int, default=1,
                     help="timed RK4 steps of the 3-D N=32 configuration (0 = skip)")
     ap.add_argument("--leg48", action="store_true", help="also time one evaluation of the 3-D N=48 configuration")
-    ap.add_argument("--only", choices=["config2", "config4", "2d64"],
+    ap.add_argument("--leg-rescale", type=int, default=20,
+                    help="timed steps of the 2-D velocity-rescaling leg (0 = skip)")
+    ap.add_argument("--only", choices=["config2", "config4", "2d64", "rescale"],
                     help="run one leg alone and print it (profiling runs): a 3-D configuration, or the 2-D "
                          "N=64 mixed operator (--steps evaluations)")
     ap.add_argument("--beta-budget-mb", type=int, default=0,
