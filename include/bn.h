@@ -190,6 +190,8 @@ bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count);
  * being captured.  The current device must be the solver's device (BN_ERR_ARG
  * otherwise).  The solver's read-only kernel-mode
  * tables, work lists and twiddles are used; the solver itself is not modified.
+ * With opt.beta_split the residual-table pass runs first in the same scratch and its
+ * modes are added, as in bn_eval_collision_device.
  * 2-D solvers only (BN_ERR_UNSUPPORTED otherwise).  Runs on cuda_stream (NULL =
  * legacy default stream) and returns when Q_dev holds the result.
  */
