@@ -280,6 +280,14 @@ bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, 
  * state of the start of that step), BN_ERR_TIMEOUT as for bn_eval_collision. */
 bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps);
 
+/* The temperature (and fugacity) of the equilibrium with mass rho and internal energy e, as the
+ * rescaled step solves it (Sec. 3.3 step 3(b), Sec. 1.2): T = 2e/d for eps = 0 (*z = 0); for
+ * eps != 0 (2-D only) z from |eps| rho / (2 pi e) = K_1(z)^2 / K_2(z) by Brent's method and
+ * T = |eps| rho / (2 pi K_1(z)).  Host only, no GPU needed.  BN_ERR_ARG for null pointers or d not
+ * 2 or 3, BN_ERR_UNSUPPORTED for 3-D with eps != 0, BN_ERR_STATE outside I_eq or for non-positive
+ * rho or e. */
+bn_status bn_equilibrium_temperature(int d, double eps, double rho, double e, double* T, double* z);
+
 /* out[0..8] = [w, u_0, u_1, u_2, rho, e, T, z, t] of the rescaled solve (u_2 = 0 in 2-D, z = 0
  * classically); count >= 9.  BN_ERR_STATE before bn_rescale_set. */
 bn_status bn_rescale_get(const bn_solver* s, double* out, size_t count);

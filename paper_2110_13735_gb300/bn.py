@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.bn_rescale_set.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, sz, ctypes.c_double, ctypes.c_double]
     lib.bn_step_rescaled.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.bn_rescale_get.argtypes = [vp, dp, sz]
+    lib.bn_equilibrium_temperature.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     ip = ctypes.POINTER(ctypes.c_int)
     lib.bn_plan_mixed2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, sz, ip]
     lib.bn_measure_fma_peak.argtypes = [ctypes.c_int, vp, dp, sz]
@@ -136,6 +138,15 @@ def plan_mixed2d(N: int, rw: int = 8, oriented: bool = True, nblk: int = 456) ->
     _check(lib.bn_plan_mixed2d(int(N), int(rw), int(bool(oriented)), int(nblk),
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), out.size, ctypes.byref(n)))
     return out
+
+
+def equilibrium_temperature(d: int, eps: float, rho: float, e: float):
+    """(T, z) of the equilibrium with mass rho and internal energy e (include/bn.h:
+    bn_equilibrium_temperature); host only."""
+    lib = load()
+    T, z = ctypes.c_double(), ctypes.c_double()
+    _check(lib.bn_equilibrium_temperature(int(d), float(eps), float(rho), float(e), ctypes.byref(T), ctypes.byref(z)))
+    return T.value, z.value
 
 
 def options(M=0, M1=0, M2=0, precision=FP64, conserve=0, c_phi=0.0, integrator=0, quad3d=0,

@@ -790,6 +790,14 @@ extern "C" bn_status bn_rescale_set(bn_solver* s, double L, double omega, const 
     return BN_OK;
 }
 
+extern "C" bn_status bn_equilibrium_temperature(int d, double eps, double rho, double e, double* T, double* z) {
+    if (!T || !z || (d != 2 && d != 3)) return fail(BN_ERR_ARG, "T, z must be non-null and d 2 or 3");
+    std::string err;
+    const bn_status st = bn::rescale_temperature(d, eps, rho, e, T, z, &err);
+    if (st != BN_OK) return fail(st, err);
+    return BN_OK;
+}
+
 extern "C" bn_status bn_rescale_get(const bn_solver* s, double* out, size_t count) {
     if (!valid_solver(s) || !out || count < 9) return fail(BN_ERR_ARG, "null solver/out or count < 9");
     if (!s->resc) return fail(BN_ERR_STATE, "velocity rescaling not set (bn_rescale_set)");

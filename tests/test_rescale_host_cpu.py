@@ -1,0 +1,77 @@
+"""The library's own temperature and fugacity solve of the velocity-rescaling step (include/bn.h:
+bn_equilibrium_temperature; its dilogarithm from the series with Euler's reflection, Landen's identity
+and the inversion formula, and its own Brent iteration), on the CPU, against the oracle's solve
+(oracle/rescaling.py: scipy's Spence function and brentq) and against quantum Maxwellian moments
+from quadrature (tests/equilibria.py): from nearly classical to strongly degenerate fermions
+(z = e^30) and bosons close to z = 1."""
+from __future__ import annotations
+
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import rescaling as RS
+from paper_2110_13735_gb300 import bn
+
+sys.path.insert(0, os.path.dirname(__file__))
+import equilibria as EQ  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        return bn.load()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+
+
+def _moments(stat, eps, T, z):
+    rho = EQ.mass(2, stat, z, T, abs(eps))
+    K1 = EQ.fd_integral(1.0, z) if stat == "FD" else EQ.be_integral(1.0, z)
+    K2 = EQ.fd_integral(2.0, z) if stat == "FD" else EQ.be_integral(2.0, z)
+    return rho, T * K2 / K1
+
+
+@pytest.mark.parametrize("stat,eps", [("FD", -9.0), ("FD", -1.0), ("BE", 9.0), ("BE", 1.0)])
+@pytest.mark.parametrize("T,z", [(1.0, 1e-6), (0.5, 0.3), (2.0, 0.95), (0.7, 5.0), (0.2, math.exp(30.0)),
+                                 (1.3, 0.999999)])
+def test_temperature_against_quadrature_and_the_oracle(lib, stat, eps, T, z):
+    if stat == "BE" and z >= 1.0:
+        pytest.skip("Bose-Einstein fugacity < 1")
+    rho, e = _moments(stat, eps, T, z)
+    Tl, zl = bn.equilibrium_temperature(2, eps, rho, e)
+    To, zo = RS.temperature(2, eps, rho, e)
+    assert Tl == pytest.approx(T, rel=1e-10) and zl == pytest.approx(z, rel=1e-9)
+    assert Tl == pytest.approx(To, rel=1e-12) and zl == pytest.approx(zo, rel=1e-11)
+
+
+def test_classical_and_errors(lib):
+    assert bn.equilibrium_temperature(2, 0.0, 1.3, 0.7) == (0.7, 0.0)
+    assert bn.equilibrium_temperature(3, 0.0, 1.3, 0.6)[0] == pytest.approx(0.4)
+    with pytest.raises(bn.BNError) as ei:          # 2-D Fermi-Dirac outside I_eq
+        bn.equilibrium_temperature(2, -9.0, 1.0, 9.0 / (2 * math.pi * 2.5))
+    assert ei.value.status == -7
+    with pytest.raises(bn.BNError) as ei:          # the quantum solve is 2-D
+        bn.equilibrium_temperature(3, 1.0, 1.0, 1.0)
+    assert ei.value.status == -8
+    with pytest.raises(bn.BNError):
+        bn.equilibrium_temperature(2, 1.0, -1.0, 1.0)
+    # the oracle agrees on the degenerate boundary
+    with pytest.raises(ValueError):
+        RS.temperature(2, -9.0, 1.0, 9.0 / (2 * math.pi * 2.5))
+    # 2-D Bose-Einstein: x = K_1^2 / K_2 -> infinity as z -> 1, but with z in FP64 (z <= 1 - 1e-16) x
+    # reaches only ~6 ln(1e16)^2 / pi^2 = 824; beyond that neither solve has a root in its bracket
+    x_ok, x_far = 500.0, 5000.0
+    for x, solvable in ((x_ok, True), (x_far, False)):
+        rho, e = 1.0, 9.0 * 1.0 / (2 * math.pi * x)
+        if solvable:
+            T, z = bn.equilibrium_temperature(2, 9.0, rho, e)
+            assert z == pytest.approx(RS.temperature(2, 9.0, rho, e)[1], rel=1e-12) and 1 - z < 1e-10
+        else:
+            with pytest.raises(bn.BNError):
+                bn.equilibrium_temperature(2, 9.0, rho, e)
+            with pytest.raises(ValueError):
+                RS.temperature(2, 9.0, rho, e)
