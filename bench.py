@@ -514,6 +514,14 @@ def run_ours(args):
         solves["pair_solve_s_fp64"] = ms64_step * max(steps_to_end.values()) / 1e3
         solves["solves_per_s_fp64"] = ws * 2.0 / solves["pair_solve_s_fp64"]
 
+    def guarded(fn, *a, **kw):
+        """An extra leg: its failure is recorded in its field of the JSON line, not raised (the
+        headline numbers above are already measured)."""
+        try:
+            return fn(*a, **kw)
+        except Exception as exc:   # noqa: BLE001 -- any failure of a side leg
+            return {"error": f"{type(exc).__name__}: {exc}"}
+
     serving = None
     if args.serving > 0 and ws == 1:   # extra legs at N=1 only (replicas would repeat them)
         Ns = tuple(int(x) for x in args.serving_ns.split(","))
@@ -521,19 +529,20 @@ def run_ours(args):
         policy = {"beta_split_N": sorted(int(x) for x in args.serving_beta_split.split(",") if x),
                   "escalate_at_by_N": {int(a): float(b) for a, b in (x.split(":") for x in args.serving_escalate.split(",")
                                                                      if x)}}
-        serving = serving_sample(bn, I, args.serving, 200.0, {N: per_n.get(N, 0) for N in Ns}, Ns=Ns, policy=policy)
+        serving = guarded(serving_sample, bn, I, args.serving, 200.0, {N: per_n.get(N, 0) for N in Ns}, Ns=Ns,
+                          policy=policy)
 
     legs = {}
     if args.leg3d_steps > 0 and ws == 1:
-        legs["config2_3d_n32"] = leg_3d(bn, I, "config2", args.leg3d_steps, peaks["fp32x2"])
+        legs["config2_3d_n32"] = guarded(leg_3d, bn, I, "config2", args.leg3d_steps, peaks["fp32x2"])
     if args.leg48 and ws == 1:
-        legs["config4_3d_n48"] = leg_3d(bn, I, "config4", 1, peaks["fp32x2"])
+        legs["config4_3d_n48"] = guarded(leg_3d, bn, I, "config4", 1, peaks["fp32x2"])
     if args.leg_rescale > 0 and ws == 1:
-        legs["rescaling_2d_n32"] = leg_rescale(bn, I, args.leg_rescale, peaks["fp32x2"])
+        legs["rescaling_2d_n32"] = guarded(leg_rescale, bn, I, args.leg_rescale, peaks["fp32x2"])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(args.cpu_seconds)
+        cpu = guarded(cpu_baseline_sample, args.cpu_seconds)
 
     if rank == 0:
         line = {
