@@ -185,7 +185,7 @@ bn_status bn_eval_collision_modes(bn_solver* s, double* Qhat, size_t count);
  * clears what must start at zero.  Calls whose GPU work overlaps in time (other
  * threads, other streams) race on it: serialise them.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress), which is
- * also when the driver loads the array onto that device.  Every call reads an
+ * also when the CUDA driver loads the array onto that device.  Every call reads an
  * error flag back and synchronises cuda_stream, so no call can be made while a stream is
  * being captured.  The current device must be the solver's device (BN_ERR_ARG
  * otherwise).  The solver's read-only kernel-mode

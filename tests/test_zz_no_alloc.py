@@ -8,7 +8,7 @@ test checks, through the C ABI, that it gives the same Q as the ordinary device 
 (bn_eval_collision_device) within the tolerances of the other GPU tests, on two calls in a row with
 different data (the shared array keeps the previous call's contents), and that a call leaves the
 device's free memory unchanged (checked on the second call of each case: the first call in a process
-looks up the array's address, which is when the driver loads the array itself).  The file is collected last so that a failure here comes after every
+looks up the array's address, which is when the CUDA driver loads the array itself).  The file is collected last so that a failure here comes after every
 other test has run.
 """
 from __future__ import annotations
