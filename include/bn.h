@@ -256,17 +256,18 @@ bn_status bn_profile_nd(bn_solver* s, double* out, size_t count);
 bn_status bn_precision_state(const bn_solver* s, int* precision, double* t_escalated, double* max_f);
 
 /* Velocity rescaling (Sec. 3 of the paper; the velocity rescaling method of Sec. 3.2 with
- * lambda = mu = 1), LINEAR solvers: 2-D, and 3-D with eps = 0 (the quantum temperature solve is
- * 2-D).  The solver must have been created with T = pi: its state (bn_set_state / bn_get_state) is
+ * lambda = mu = 1), LINEAR solvers, 2-D and 3-D.  The solver must have been created with T = pi: its state (bn_set_state / bn_get_state) is
  * then G on the grid xi_j = 2 pi j / N of [-pi, pi]^d (row-major, j in I_N), with
  * f(t, v) = (pi w / L)^d G(t, (pi w / L)(v - u)), i.e. f_j = (pi w / L)^d G_j at the velocities
  * v_j = u + 2 L j / (N w); R is the kernel truncation in xi.
  * bn_rescale_set: L > 0 the half-width of the velocity box at w = 1, omega > 0 the scale w, u the mean
  * velocity (du = d values), rho, e > 0 the mass and internal energy of the state; also solves the
  * temperature (and the fugacity).  Allocates the step's scratch (4 arrays of N^d) once.
- * BN_ERR_ARG for bad values or T != pi, BN_ERR_UNSUPPORTED for CIRCULAR or sharded solvers and
- * 3-D with eps != 0, BN_ERR_STATE when the moments admit no temperature (2-D Fermi-Dirac:
- * |eps| rho / (2 pi e) >= 2). */
+ * BN_ERR_ARG for bad values or T != pi, BN_ERR_UNSUPPORTED for CIRCULAR or sharded solvers,
+ * BN_ERR_STATE when the moments admit no temperature (x = |eps| rho (d / (4 pi e))^{d/2} outside
+ * I_eq: x >= 2 for 2-D Fermi-Dirac, x >= (5/3) sqrt(10/pi) for 3-D Fermi-Dirac, x >=
+ * zeta(3/2)^{5/2} / zeta(5/2)^{3/2} for 3-D Bose-Einstein, whose equilibrium then carries a
+ * condensate that the grid cannot hold). */
 bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, size_t du, double rho, double e);
 
 /* nsteps forward Euler steps of the procedure of Sec. 3.3: Q of G with the quantum parameter
@@ -282,10 +283,13 @@ bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps);
 
 /* The temperature (and fugacity) of the equilibrium with mass rho and internal energy e, as the
  * rescaled step solves it (Sec. 3.3 step 3(b), Sec. 1.2): T = 2e/d for eps = 0 (*z = 0); for
- * eps != 0 (2-D only) z from |eps| rho / (2 pi e) = K_1(z)^2 / K_2(z) by Brent's method and
- * T = |eps| rho / (2 pi K_1(z)).  Host only, no GPU needed.  BN_ERR_ARG for null pointers or d not
- * 2 or 3, BN_ERR_UNSUPPORTED for 3-D with eps != 0, BN_ERR_STATE outside I_eq or for non-positive
- * rho or e. */
+ * eps != 0 z from x = |eps| rho (d / (4 pi e))^{d/2} = K_nu(z)^{nu+1} / K_{nu+1}(z)^nu, nu = d/2
+ * (eq_fugacity), by Brent's method (on mu = ln z for Fermi-Dirac, on ln(-ln z) for 3-D
+ * Bose-Einstein), and T = (|eps| rho / K_nu(z))^{1/nu} / (2 pi) (mom0_qmaxwell); K_nu is the complete
+ * Fermi-Dirac (eps < 0) or Bose-Einstein (eps > 0) integral, in closed form for nu = 1, 2 and by
+ * double-exponential quadrature for nu = 3/2, 5/2.  Host only, no GPU needed.  BN_ERR_ARG for null
+ * pointers or d not 2 or 3, BN_ERR_STATE outside I_eq (as for bn_rescale_set), when the root lies
+ * beyond the bracket (3-D Fermi-Dirac: ln z > 700) or for non-positive rho or e. */
 bn_status bn_equilibrium_temperature(int d, double eps, double rho, double e, double* T, double* z);
 
 /* out[0..8] = [w, u_0, u_1, u_2, rho, e, T, z, t] of the rescaled solve (u_2 = 0 in 2-D, z = 0

@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the velocity-rescaling method (Mouton & Rey, Sec. 3): 2-D, and 3-D classical.
+"""FP64 CPU oracle of the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D and 3-D.
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package: the product library never imports it.
 
@@ -23,15 +23,18 @@ One step follows the numbered procedure of Sec. 3.3 for the forward Euler scheme
      component times i k_d (k_d in I_N; the k_d = -N/2 mode, which has no partner, gets 0);
   5. G^{n+1} = G^n + dt (-div + (pi w^n / L)^{-gamma} Q^n).
 
-The Fermi-Dirac and Bose-Einstein integrals of order 1 and 2 are closed forms: K_1 = ln(1 + z) or
--ln(1 - z), K_2 = -Li_2(-z) or Li_2(z), the dilogarithm taken from scipy (spence(1 - x) = Li_2(x)).
+The Fermi-Dirac and Bose-Einstein integrals of order 1 and 2 (2-D) are closed forms: K_1 = ln(1 + z)
+or -ln(1 - z), K_2 = -Li_2(-z) or Li_2(z), the dilogarithm taken from scipy (spence(1 - x) = Li_2(x)).
+Those of order 3/2 and 5/2 (3-D) are their defining integrals (Sec. 1.2) taken by scipy's adaptive
+quadrature.
 """
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
-from scipy import optimize, special
+from scipy import integrate, optimize, special
 
 from . import Operator
 
@@ -59,15 +62,85 @@ def k_nu(nu: int, z: float, eps: float) -> float:
     return -math.log1p(-z) if nu == 1 else li2(z)
 
 
+def k_half(nu: float, mu: float, eps: float) -> float:
+    """K_nu(e^mu) of Sec. 1.2 for nu = 3/2, 5/2: Gamma(nu)^{-1} int_0^inf x^{nu-1} / (e^{x-mu} + s) dx,
+    s = +1 Fermi-Dirac (eps < 0), -1 Bose-Einstein (eps > 0, mu < 0).  Written in t = sqrt(x),
+    2 t^{2nu-1} / (e^{t^2-mu} + s), split at t = sqrt(mu) (the Fermi step) when mu > 0 and cut where
+    e^{t^2-mu} exceeds e^{60}."""
+    fd = eps < 0
+
+    def f(t):
+        a = t * t - mu
+        if a > 700.0:
+            return 0.0
+        return 2.0 * t ** (2.0 * nu - 1.0) / (math.exp(a) + 1.0 if fd else math.expm1(a))
+
+    t0 = math.sqrt(max(mu, 0.0))
+    t1 = math.sqrt(max(mu, 0.0) + 60.0)
+    if t0 > 0.0:
+        pts = [0.0, t0, t1]
+    else:
+        # Bose-Einstein near z = 1: below t ~ sqrt(-mu) the integrand drops from 2 t^{2nu-1} / t^2 to
+        # 0, a layer that carries a relative pi sqrt(-mu) / K; breakpoints at sqrt(-mu) 10^k resolve it
+        pts = [0.0]
+        if not fd:
+            c = max(math.sqrt(-mu), 1e-17)
+            while c < 1.0:
+                pts.append(c)
+                c *= 10.0
+        pts.append(t1)
+    pieces = list(zip(pts[:-1], pts[1:]))
+    total = 0.0
+    with warnings.catch_warnings():
+        # quad reports roundoff at the tolerance it is asked for; the pins bound the result (1e-14)
+        warnings.simplefilter("ignore", integrate.IntegrationWarning)
+        for a, b in pieces:
+            v, _ = integrate.quad(f, a, b, epsabs=0.0, epsrel=1.2e-14, limit=500)
+            total += v
+    return total / special.gamma(nu)
+
+
+# the ends of I_eq in 3-D (def_Ieq)
+IEQ_FD_3D = 5.0 / 3.0 * math.sqrt(10.0 / math.pi)
+IEQ_BE_3D = float(special.zeta(1.5)) ** 2.5 / float(special.zeta(2.5)) ** 1.5
+
+
+def _temperature_3d(eps: float, rho: float, e: float):
+    """3-D: nu = 3/2, x = |eps| rho (3 / (4 pi e))^{3/2} = K_{3/2}^{5/2} / K_{5/2}^{3/2} (eq_fugacity),
+    compared in logarithms; Brent on mu = ln z (Fermi-Dirac) or on ln(-mu) (Bose-Einstein, so that
+    z -> 1 stays resolved); T = (|eps| rho / K_{3/2})^{2/3} / (2 pi) (mom0_qmaxwell)."""
+    x = abs(eps) * rho * (3.0 / (4.0 * math.pi * e)) ** 1.5
+    lx = math.log(x) if x > 0.0 else -math.inf
+
+    def g(mu):
+        return 2.5 * math.log(k_half(1.5, mu, eps)) - 1.5 * math.log(k_half(2.5, mu, eps)) - lx
+
+    if eps < 0:
+        if not 0.0 < x < IEQ_FD_3D:
+            raise ValueError("Fermi-Dirac moments outside I_eq (degenerate state)")
+        if g(700.0) < 0.0:
+            raise ValueError("the fugacity lies beyond ln z = 700")
+        mu = optimize.brentq(g, -600.0, 700.0, xtol=1e-14, rtol=1e-15, maxiter=500)
+    else:
+        if not 0.0 < x < IEQ_BE_3D:
+            raise ValueError("Bose-Einstein moments outside I_eq (condensed state)")
+        lam = optimize.brentq(lambda l: g(-math.exp(l)), -690.0, math.log(600.0), xtol=1e-14, rtol=1e-15,
+                              maxiter=500)
+        mu = -math.exp(lam)
+    T = (abs(eps) * rho / k_half(1.5, mu, eps)) ** (2.0 / 3.0) / (2.0 * math.pi)
+    return T, math.exp(mu)
+
+
 def temperature(d: int, eps: float, rho: float, e: float):
     """(T, z) from the mass and internal energy (Sec. 3.3 step 3(b); Sec. 1.2): classical T = 2e/d
-    (z = None); quantum, 2-D: x = |eps| rho (d / (4 pi e))^{d/2} must lie in I_eq ((0, 2) for
-    Fermi-Dirac, (0, inf) for Bose-Einstein); then z solves x = K_1(z)^2 / K_2(z) (eq_fugacity with
-    nu = 1) and T = (|eps| rho / K_1(z)) / (2 pi) (mom0_qmaxwell).  Raises ValueError outside I_eq."""
+    (z = None); quantum: x = |eps| rho (d / (4 pi e))^{d/2} must lie in I_eq (2-D: (0, 2) for
+    Fermi-Dirac, (0, inf) for Bose-Einstein; 3-D: see _temperature_3d); in 2-D z solves
+    x = K_1(z)^2 / K_2(z) (eq_fugacity with nu = 1) and T = (|eps| rho / K_1(z)) / (2 pi)
+    (mom0_qmaxwell).  Raises ValueError outside I_eq."""
     if eps == 0.0:
         return 2.0 * e / d, None
-    if d != 2:
-        raise ValueError("the quantum temperature solve is written for d = 2")
+    if d == 3:
+        return _temperature_3d(eps, rho, e)
     x = abs(eps) * rho * (d / (4.0 * math.pi * e)) ** (d / 2.0)
     if eps < 0:
         if not 0.0 < x < 2.0:

@@ -1,4 +1,4 @@
-// bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D and 3-D classical: the kernels of one
+// bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D and 3-D: the kernels of one
 // forward Euler step of Sec. 3.3 around the operator evaluation, and the host-side temperature solve.
 //
 // The state is G on the grid xi_j = 2 pi j / N of [-pi, pi]^d (the solver's box T = pi), with
@@ -13,7 +13,9 @@
 // x = |eps| rho (d / (4 pi e))^{d/2} must lie in I_eq, then z solves x = K_1(z)^2 / K_2(z) by Brent's
 // method (on mu = ln z for Fermi-Dirac particles) and T = |eps| rho / (2 pi K_1(z)); K_1 and K_2 are
 // the Fermi-Dirac (eps < 0) or Bose-Einstein (eps > 0) integrals of orders 1 and 2: ln(1 + z) or
-// -ln(1 - z), and -Li_2(-z) or Li_2(z).
+// -ln(1 - z), and -Li_2(-z) or Li_2(z).  In 3-D the orders are 3/2 and 5/2 (nu = d/2 in eq_fugacity),
+// x = |eps| rho (3 / (4 pi e))^{3/2} = K_{3/2}^{5/2} / K_{5/2}^{3/2} and T = (|eps| rho / K_{3/2})^{2/3} / (2 pi);
+// those integrals are taken by double-exponential quadrature of their definition.
 #include <cmath>
 #include <string>
 
@@ -131,6 +133,53 @@ double k_nu(int nu, double z, double eps) {
     return nu == 1 ? -std::log1p(-z) : li2(z);
 }
 
+// int_a^b f(t) dt by the tanh-sinh rule t = a + (b - a) / (1 + e^{-2 phi}), phi = (pi/2) sinh(u),
+// halving the step u from 1/2 until two levels agree to 1e-15 (Takahasi and Mori's double-exponential
+// quadrature).  The nodes crowd both ends, where the integrands below have their only sharp features.
+template <typename F>
+double tanh_sinh(F f, double a, double b) {
+    const double half = 0.5 * (b - a);
+    auto term = [&](double u) {
+        const double phi = 0.5 * M_PI * std::sinh(u);
+        const double c = std::cosh(phi);
+        const double w = half * 0.5 * M_PI * std::cosh(u) / (c * c);
+        if (!(w > 0.0)) return 0.0;
+        // distance to the nearer end without cancellation: (b - a) / (1 + e^{2|phi|})
+        const double near = (b - a) / (1.0 + std::exp(2.0 * std::fabs(phi)));
+        return w * f(phi < 0 ? a + near : b - near);
+    };
+    const double umax = 4.0;   // weights there are below 1e-35 of the central one
+    double h = 0.5;
+    double sum = term(0.0);
+    for (double u = h; u <= umax; u += h) sum += term(u) + term(-u);
+    double prev = h * sum;
+    for (int level = 0; level < 9; ++level) {
+        h *= 0.5;
+        for (double u = h; u <= umax; u += 2.0 * h) sum += term(u) + term(-u);
+        const double cur = h * sum;
+        if (level >= 2 && std::fabs(cur - prev) <= 1e-15 * std::fabs(cur)) return cur;
+        prev = cur;
+    }
+    return prev;
+}
+
+// K_nu(e^mu) for nu = n2 / 2 in {3/2, 5/2}: Gamma(nu)^{-1} int_0^inf x^{nu-1} / (e^{x - mu} + s) dx,
+// s = +1 Fermi-Dirac (eps < 0), s = -1 Bose-Einstein (eps > 0, mu < 0).  In t = sqrt(x) the
+// integrand 2 t^{n2-1} / (e^{t^2 - mu} + s) is smooth; for mu > 0 the range is split at t = sqrt(mu),
+// where the Fermi step sits, and it ends where e^{t^2 - mu} > e^{49}.
+double k_half(int n2, double mu, double eps) {
+    const bool fd = eps < 0;
+    auto f = [&](double t) {
+        const double t2 = t * t, p = n2 == 3 ? t2 : t2 * t2;
+        const double den = fd ? std::exp(t2 - mu) + 1.0 : std::expm1(t2 - mu);
+        return 2.0 * p / den;
+    };
+    const double t0 = std::sqrt(std::max(mu, 0.0));
+    double v = tanh_sinh(f, t0, t0 + 7.0);
+    if (t0 > 0.0) v += tanh_sinh(f, 0.0, t0);
+    return v / std::tgamma(0.5 * n2);
+}
+
 // Brent's root finder on [a, b] with f(a) f(b) < 0: inverse quadratic interpolation or the secant
 // step when it stays inside the bracket and shrinks it fast enough, bisection otherwise.
 template <typename F>
@@ -201,9 +250,43 @@ bn_status rescale_temperature(int d, double eps, double rho, double e, double* T
         *z = 0.0;
         return BN_OK;
     }
-    if (d != 2) {
-        *err = "rescaling: the quantum temperature solve is 2-D";
-        return BN_ERR_UNSUPPORTED;
+    if (d == 3) {
+        // nu = 3/2: x = K_{3/2}(z)^{5/2} / K_{5/2}(z)^{3/2} (eq_fugacity), compared in logarithms so that
+        // integrals of size e^{-600} do not underflow; Fermi-Dirac on mu = ln z in [-600, 700], I_eq =
+        // (0, (5/3) sqrt(10/pi)); Bose-Einstein on lambda = ln(-mu) in [-690, ln 600] (z = e^{-e^lambda},
+        // which resolves z -> 1), I_eq = (0, zeta(3/2)^{5/2} / zeta(5/2)^{3/2})
+        const double x = std::fabs(eps) * rho * std::pow(3.0 / (4.0 * M_PI * e), 1.5);
+        const double lx = std::log(x);
+        auto lF = [&](double mu) {
+            return 2.5 * std::log(k_half(3, mu, eps)) - 1.5 * std::log(k_half(5, mu, eps)) - lx;
+        };
+        double mu = 0.0;
+        bool ok;
+        if (eps < 0) {
+            const double xmax = 5.0 / 3.0 * std::sqrt(10.0 / M_PI);
+            if (!(x > 0.0 && x < xmax)) {
+                *err = "rescaling: Fermi-Dirac moments outside I_eq (degenerate state)";
+                return BN_ERR_STATE;
+            }
+            ok = brent(lF, -600.0, 700.0, 1e-14, &mu);
+        } else {
+            const double zeta32 = 2.612375348685488, zeta52 = 1.341487257250917;
+            const double xmax = std::pow(zeta32, 2.5) / std::pow(zeta52, 1.5);
+            if (!(x > 0.0 && x < xmax)) {
+                *err = "rescaling: Bose-Einstein moments outside I_eq (condensed state)";
+                return BN_ERR_STATE;
+            }
+            double lam = 0.0;
+            ok = brent([&](double l) { return lF(-std::exp(l)); }, -690.0, std::log(600.0), 1e-14, &lam);
+            mu = -std::exp(lam);
+        }
+        if (!ok) {
+            *err = "rescaling: the fugacity equation has no root in its bracket";
+            return BN_ERR_STATE;
+        }
+        *z = std::exp(mu);
+        *T = std::pow(std::fabs(eps) * rho / k_half(3, mu, eps), 2.0 / 3.0) / (2.0 * M_PI);
+        return BN_OK;
     }
     const double x = std::fabs(eps) * rho * (d / (4.0 * M_PI * e));
     double zz = 0.0;

@@ -95,8 +95,11 @@ def test_rescaled_steps_match_the_oracle(B, N, L, kernel, eps, amp, precision, t
     assert w != run.w   # the scale moved: the divergence term was exercised
 
 
-def test_rescaled_steps_3d_classical(B):
-    """3-D hard spheres, eps = 0 (the classical temperature T = 2e/3), N = 8, started off the scale."""
+@pytest.mark.parametrize("eps", [0.0, -1.0, 1.0])
+def test_rescaled_steps_3d(B, eps):
+    """3-D hard spheres, N = 8, started 20 % off the scale: eps = 0 (the classical temperature
+    T = 2e/3), Fermi-Dirac and Bose-Einstein (x = 0.37: T and z from K_{3/2}, K_{5/2} by quadrature on
+    both sides, the library's own double-exponential rule against the oracle's adaptive one)."""
     N, L, dt, steps = 8, 4.0, 0.01, 3
     j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
     v = np.stack(np.meshgrid(j, j, j, indexing="ij"), -1)
@@ -110,14 +113,14 @@ def test_rescaled_steps_3d_classical(B):
     rho = f.sum() * dv
     u = (v * f[..., None]).sum((0, 1, 2)) * dv / rho
     e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
-    T, _ = RS.temperature(3, 0.0, rho, e)
-    w = 1.2 * RS.omega_of(3, 0.0, T, u)
+    T, _ = RS.temperature(3, eps, rho, e)
+    w = 1.2 * RS.omega_of(3, eps, T, u)
     s = math.pi * w / L
     G = g0(u + RS.xi_grid(3, N) / s) / s ** 3
-    run = RS.RescaledRun(N, L, S_TRUNC, 1, 0.0, G, rho, u, e, w, d=3, M1=4, M2=4)
+    run = RS.RescaledRun(N, L, S_TRUNC, 1, eps, G, rho, u, e, w, d=3, M1=4, M2=4)
     for _ in range(steps):
         run.step(dt)
-    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, 0.0, precision=B.FP64, M1=4, M2=4) as sol:
+    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, eps, precision=B.FP64, M1=4, M2=4) as sol:
         sol.set_state(G)
         sol.rescale_set(L, w, u, rho, e)
         sol.step_rescaled(dt, steps)
@@ -125,10 +128,17 @@ def test_rescaled_steps_3d_classical(B):
         st = sol.rescale_state()
     assert np.linalg.norm(Gg - run.G) <= 1e-12 * np.linalg.norm(run.G)
     assert st["w"] == pytest.approx(run.w, rel=1e-12) and np.allclose(st["u"], run.u, rtol=1e-12, atol=1e-13)
-    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, 1.0, M1=4, M2=4) as sol:
-        with pytest.raises(B.BNError) as ei:          # the quantum temperature solve is 2-D
-            sol.rescale_set(L, 1.0, [0.0, 0.0, 0.0], 1.0, 1.0)
-        assert ei.value.status == -8
+    assert st["rho"] == pytest.approx(run.rho, rel=1e-12) and st["e"] == pytest.approx(run.e, rel=1e-12)
+    assert w != run.w
+    if eps != 0.0:
+        assert st["z"] == pytest.approx(run.z, rel=1e-10)
+        with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, eps, M1=4, M2=4) as sol:
+            # moments beyond the end of I_eq (x = 1.001 times it): degenerate / condensed
+            xmax = RS.IEQ_FD_3D if eps < 0 else RS.IEQ_BE_3D
+            e_out = 0.75 * (1.0 / (1.001 * xmax)) ** (2.0 / 3.0) / math.pi
+            with pytest.raises(B.BNError) as ei:
+                sol.rescale_set(L, 1.0, [0.0, 0.0, 0.0], 1.0, e_out)
+            assert ei.value.status == -7
 
 
 def test_rescaling_arguments_and_degenerate_state(B):

@@ -144,3 +144,56 @@ def test_residuals_with_rescaling_against_the_printed_table():
     # at N = 32 the fixed box [-L, L]^2 of the classical method, which cuts the shifted
     # distribution, leaves the larger residual (Sec. 4.1)
     assert ours[(32, 1)] < _residual(32, 4.0, 0.5, ub, False)
+
+
+# ------------------------------------------------------------------ 3-D temperature solve
+@pytest.mark.parametrize("eps", [-1.0, 1.0])
+def test_half_integer_integrals_against_polylog(eps):
+    """K_nu(e^mu) = -Li_nu(-e^mu) (Fermi-Dirac) or Li_nu(e^mu) (Bose-Einstein), nu = 3/2, 5/2: the
+    oracle's quadrature of the defining integral against mpmath's polylogarithm, from nearly
+    classical to degenerate fermions (mu = 700) and to bosons at 1 - z = 1e-14."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    mus = [-600.0, -40.0, -2.0, 0.5, 4.0, 30.0, 700.0] if eps < 0 else [-600.0, -40.0, -2.0, -1e-3, -1e-8, -1e-14]
+    for mu in mus:
+        for nu in (1.5, 2.5):
+            z = mpmath.exp(mu)
+            ref = float(mpmath.re(-mpmath.polylog(nu, -z) if eps < 0 else mpmath.polylog(nu, z)))
+            assert RS.k_half(nu, mu, eps) == pytest.approx(ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("stat,eps", [("FD", -9.0), ("FD", -1.0), ("BE", 9.0), ("BE", 1.0)])
+@pytest.mark.parametrize("T,z", [(1.0, 1e-6), (0.5, 0.3), (2.0, 0.95), (0.7, 5.0), (0.3, 2e4), (1.3, 1 - 1e-6)])
+def test_temperature_round_trip_3d(stat, eps, T, z):
+    """3-D: rho and e of the quantum Maxwellian by quadrature (mom02_qmaxwell, tests/equilibria.py),
+    then the oracle's solve gives back T and z."""
+    if stat == "BE" and z >= 1.0:
+        pytest.skip("Bose-Einstein fugacity < 1")
+    rho = EQ.mass(3, stat, z, T, abs(eps))
+    K32 = EQ.fd_integral(1.5, z) if stat == "FD" else EQ.be_integral(1.5, z)
+    K52 = EQ.fd_integral(2.5, z) if stat == "FD" else EQ.be_integral(2.5, z)
+    e = 1.5 * T * K52 / K32
+    T2, z2 = RS.temperature(3, eps, rho, e)
+    assert T2 == pytest.approx(T, rel=1e-11)
+    assert z2 == pytest.approx(z, rel=1e-9 if z < 1e3 else 1e-8)
+
+
+def test_ieq_ends_3d():
+    """The ends of I_eq in 3-D (def_Ieq) are the limits of the fugacity functions (Sec. 1.2):
+    F_{3/2}(e^mu) -> (5/2)^{3/2} / Gamma(5/2) = (5/3) sqrt(10/pi) from below as mu -> inf, B_{3/2}(z) ->
+    zeta(3/2)^{5/2} / zeta(5/2)^{3/2} from below as z -> 1, and both are z + o(z) as z -> 0."""
+    def ratio(mu, eps):
+        return RS.k_half(1.5, mu, eps) ** 2.5 / RS.k_half(2.5, mu, eps) ** 1.5
+
+    xF = 2.5 ** 1.5 / math.gamma(2.5)
+    assert RS.IEQ_FD_3D == pytest.approx(xF, rel=1e-15)
+    f200, f700 = ratio(200.0, -1.0), ratio(700.0, -1.0)
+    assert f200 < f700 < xF and xF - f700 < 0.3 * (xF - f200)   # O(mu^-2) approach
+    b = [ratio(-10.0 ** -k, 1.0) for k in (4, 8, 12)]
+    assert b[0] < b[1] < b[2] < RS.IEQ_BE_3D and RS.IEQ_BE_3D - b[2] < 1e-4
+    for eps in (-1.0, 1.0):
+        assert ratio(-30.0, eps) == pytest.approx(math.exp(-30.0), rel=1e-12)
+    with pytest.raises(ValueError):                 # Fermi-Dirac beyond the end of I_eq
+        RS.temperature(3, -1.0, 1.0, 0.75 * (1.0 / (1.001 * xF)) ** (2.0 / 3.0) / math.pi)
+    with pytest.raises(ValueError):                 # a condensate: x above the Bose-Einstein end
+        RS.temperature(3, 1.0, 1.0, 0.75 * (1.0 / (1.001 * RS.IEQ_BE_3D)) ** (2.0 / 3.0) / math.pi)

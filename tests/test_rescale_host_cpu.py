@@ -54,9 +54,15 @@ def test_classical_and_errors(lib):
     with pytest.raises(bn.BNError) as ei:          # 2-D Fermi-Dirac outside I_eq
         bn.equilibrium_temperature(2, -9.0, 1.0, 9.0 / (2 * math.pi * 2.5))
     assert ei.value.status == -7
-    with pytest.raises(bn.BNError) as ei:          # the quantum solve is 2-D
-        bn.equilibrium_temperature(3, 1.0, 1.0, 1.0)
-    assert ei.value.status == -8
+    for eps, xmax in ((-1.0, RS.IEQ_FD_3D), (1.0, RS.IEQ_BE_3D)):   # 3-D outside I_eq
+        e = 0.75 * (1.0 / (1.001 * xmax)) ** (2.0 / 3.0) / math.pi       # x = 1.001 xmax
+        with pytest.raises(bn.BNError) as ei:
+            bn.equilibrium_temperature(3, eps, 1.0, e)
+        assert ei.value.status == -7
+        e_in = 0.75 * (1.0 / (0.999 * xmax)) ** (2.0 / 3.0) / math.pi    # x = 0.999 xmax: solvable
+        Tl, zl = bn.equilibrium_temperature(3, eps, 1.0, e_in)
+        To, zo = RS.temperature(3, eps, 1.0, e_in)
+        assert Tl == pytest.approx(To, rel=1e-10) and zl == pytest.approx(zo, rel=1e-8)
     with pytest.raises(bn.BNError):
         bn.equilibrium_temperature(2, 1.0, -1.0, 1.0)
     # the oracle agrees on the degenerate boundary
@@ -75,3 +81,38 @@ def test_classical_and_errors(lib):
                 bn.equilibrium_temperature(2, 9.0, rho, e)
             with pytest.raises(ValueError):
                 RS.temperature(2, 9.0, rho, e)
+
+
+@pytest.mark.parametrize("stat,eps", [("FD", -9.0), ("FD", -1.0), ("BE", 9.0), ("BE", 1.0)])
+@pytest.mark.parametrize("T,z", [(1.0, 1e-6), (0.5, 0.3), (2.0, 0.95), (0.7, 5.0), (0.3, math.exp(12.0)),
+                                 (1.3, 1 - 1e-6)])
+def test_temperature_3d_against_quadrature_and_the_oracle(lib, stat, eps, T, z):
+    if stat == "BE" and z >= 1.0:
+        pytest.skip("Bose-Einstein fugacity < 1")
+    rho = EQ.mass(3, stat, z, T, abs(eps))
+    K32 = EQ.fd_integral(1.5, z) if stat == "FD" else EQ.be_integral(1.5, z)
+    K52 = EQ.fd_integral(2.5, z) if stat == "FD" else EQ.be_integral(2.5, z)
+    e = 1.5 * T * K52 / K32
+    Tl, zl = bn.equilibrium_temperature(3, eps, rho, e)
+    To, zo = RS.temperature(3, eps, rho, e)
+    assert Tl == pytest.approx(T, rel=1e-10) and zl == pytest.approx(z, rel=1e-8)
+    # the degenerate end is ill-conditioned (d ln z / d ln x ~ mu^3): 1e-12 up to mu = 12
+    assert Tl == pytest.approx(To, rel=1e-12) and zl == pytest.approx(zo, rel=1e-11)
+
+
+@pytest.mark.parametrize("eps", [9.0, 1.0])
+@pytest.mark.parametrize("T,one_minus_z", [(0.8, 1e-10), (1.5, 1e-14)])
+def test_temperature_3d_bosons_near_condensation(lib, eps, T, one_minus_z):
+    """3-D bosons with 1 - z down to 1e-14: the moments from mpmath's polylogarithm (the plain
+    quadrature of tests/equilibria.py misses the x^{-1/2} layer of B_{3/2} there); both solves give
+    back T, and z to the resolution of a double next to 1."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    z = 1 - mpmath.mpf(one_minus_z)
+    K32, K52 = mpmath.polylog(1.5, z), mpmath.polylog(2.5, z)
+    rho = float((2 * mpmath.pi * T) ** 1.5 * K32 / abs(eps))
+    e = float(1.5 * T * K52 / K32)
+    Tl, zl = bn.equilibrium_temperature(3, eps, rho, e)
+    To, zo = RS.temperature(3, eps, rho, e)
+    assert Tl == pytest.approx(T, rel=1e-12) and To == pytest.approx(T, rel=1e-12)
+    assert abs(zl - float(z)) <= 4e-16 and abs(zo - float(z)) <= 4e-16
