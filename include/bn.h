@@ -281,6 +281,17 @@ bn_status bn_rescale_set(bn_solver* s, double L, double omega, const double* u, 
  * state of the start of that step), BN_ERR_TIMEOUT as for bn_eval_collision. */
 bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps);
 
+/* nsteps steps of an SSP-RK2 (Heun) form of the same procedure, second order in dt for G, w, u, e:
+ * the predictor is the forward Euler step of bn_step_rescaled (G^(1), rho^(1), u^(1), e^(1), w^(1));
+ * rho, rho u, rho e are the average of their values at the start and after a second Euler moment
+ * update from the predictor with the moments of Q(G^(1)) (at the scale of G^(1)); T, z and w^{n+1}
+ * follow from them; G^{n+1} = G^n + dt/2 [F(G^n) + F(G^(1))], F(G) = -div((a xi - b) G) +
+ * (pi w / L)^{-gamma} Q(G) at each stage's scale w, with the midpoint rates a = ln(w^{n+1} / w^n) / dt
+ * and b = (pi w / L)(u^{n+1} - u^n) / dt.  Two operator evaluations per step.  Allocates one more
+ * array of N^d on its first call.  Errors as for bn_step_rescaled; on an error the state of the start
+ * of the failed step is restored. */
+bn_status bn_step_rescaled_rk2(bn_solver* s, double dt, int nsteps);
+
 /* The temperature (and fugacity) of the equilibrium with mass rho and internal energy e, as the
  * rescaled step solves it (Sec. 3.3 step 3(b), Sec. 1.2): T = 2e/d for eps = 0 (*z = 0); for
  * eps != 0 z from x = |eps| rho (d / (4 pi e))^{d/2} = K_nu(z)^{nu+1} / K_{nu+1}(z)^nu, nu = d/2

@@ -241,6 +241,44 @@ class RescaledRun:
         self.rho, self.u, self.e, self.w, self.T, self.z = rho1, u1, e1, w1, T1, z1
         return self
 
+    def rhs(self, G, Q, s: float, a: float, b) -> np.ndarray:
+        """F(G) = -div((a xi - b) G) + s^{-gamma} Q: the right-hand side of the rescaled equation at
+        scale s with dilation rate a = w'/w and drift b = (pi w / L) u'."""
+        div = spectral_divergence((a * self.xi - np.asarray(b, dtype=np.float64)) * G[..., None])
+        return -div + s ** (-self.gamma) * Q
+
+    def step_rk2(self, dt: float):
+        """One step of the SSP-RK2 (Heun) form of the procedure (reading of the RK2 variant the
+        paper mentions for Sec. 3.3):
+          predictor: the forward Euler step (G1, rho1, u1, e1, w1 from Q0 = Q(G0));
+          moments:   Y^{n+1} = (Y^n + Y^(2)) / 2 for rho, rho u, rho e, Y^(2) the Euler moment update
+                     from (rho1, u1, e1) with the moments of Q1 = Q(G1) at the scale of G1;
+                     T, z, w^{n+1} from the averaged rho, e (steps 3(b), (c));
+          G:         G^{n+1} = G0 + dt/2 [F(G0) + F(G1)], F at each stage's own scale, with the
+                     midpoint rates a = ln(w^{n+1} / w^n) / dt and u' = (u^{n+1} - u^n) / dt."""
+        G0, rho0, u0, e0, w0 = self.G.copy(), self.rho, self.u.copy(), self.e, self.w
+        s0 = self.scale()
+        Q0 = self.collision()
+        rho1, u1, e1 = self.moments_update(Q0, dt)
+        T1, _ = temperature(self.d, self.eps, rho1, e1)
+        w1 = omega_of(self.d, self.eps, T1, u1)
+        G1 = self.advance(Q0, dt, w1, u1)
+        # the second stage, from the predictor
+        self.G, self.rho, self.u, self.e, self.w = G1, rho1, u1, e1, w1
+        s1 = self.scale()
+        Q1 = self.collision()
+        rho2, u2, e2 = self.moments_update(Q1, dt)
+        rhoN = 0.5 * (rho0 + rho2)
+        uN = 0.5 * (rho0 * u0 + rho2 * u2) / rhoN
+        eN = 0.5 * (rho0 * e0 + rho2 * e2) / rhoN
+        TN, zN = temperature(self.d, self.eps, rhoN, eN)
+        wN = omega_of(self.d, self.eps, TN, uN)
+        a = math.log(wN / w0) / dt
+        du = (uN - u0) / dt
+        self.G = G0 + 0.5 * dt * (self.rhs(G0, Q0, s0, a, s0 * du) + self.rhs(G1, Q1, s1, a, s1 * du))
+        self.rho, self.u, self.e, self.w, self.T, self.z = rhoN, uN, eN, wN, TN, zN
+        return self
+
     def f_grid(self):
         """(v, f): the velocities v_j = u + 2 L j / (N w) and f_j = (pi w / L)^d G_j."""
         s = self.scale()

@@ -80,6 +80,7 @@ def load(path: str | None = None):
     lib.bn_kernel_config.argtypes = [vp, dp, sz]
     lib.bn_rescale_set.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, sz, ctypes.c_double, ctypes.c_double]
     lib.bn_step_rescaled.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.bn_step_rescaled_rk2.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.bn_rescale_get.argtypes = [vp, dp, sz]
     lib.bn_equilibrium_temperature.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -277,8 +278,10 @@ class Solver:
         uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
         _check(_lib.bn_rescale_set(self._h, float(L), float(omega), _dptr(uu), uu.size, float(rho), float(e)))
 
-    def step_rescaled(self, dt: float, nsteps: int):
-        _check(_lib.bn_step_rescaled(self._h, float(dt), int(nsteps)))
+    def step_rescaled(self, dt: float, nsteps: int, rk2: bool = False):
+        """nsteps forward Euler (bn_step_rescaled) or SSP-RK2 (bn_step_rescaled_rk2) rescaled steps."""
+        fn = _lib.bn_step_rescaled_rk2 if rk2 else _lib.bn_step_rescaled
+        _check(fn(self._h, float(dt), int(nsteps)))
 
     def rescale_state(self) -> dict:
         """{w, u, rho, e, T, z, t} of the rescaled solve (include/bn.h: bn_rescale_get)."""

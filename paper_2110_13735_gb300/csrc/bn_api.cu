@@ -45,7 +45,7 @@ bn_status cuda_fail(cudaError_t e, const char* what) {
 void free_buffers(bn_solver* s) {
     void* ptrs[] = {s->f, s->f_prev, s->y, s->kacc, s->Qv, s->Ghat, s->Ghat32, s->work_c, s->twiddle, s->S2, s->quad,
                     s->red, s->q1q, s->partials, s->Qhat, s->partials_lo, s->S2lo, s->Qlo, s->resc_H, s->resc_M,
-                    s->resc_acc, s->resc_div, s->resc_mom, s->moments, s->flags,
+                    s->resc_acc, s->resc_div, s->resc_mom, s->resc_G0, s->moments, s->flags,
                     s->work.items, s->work_quad.items,
                     s->work.meta[0], s->work.meta[1], s->work.meta[2], s->work.meta[3]};
     for (void* p : ptrs)
@@ -807,62 +807,186 @@ extern "C" bn_status bn_rescale_get(const bn_solver* s, double* out, size_t coun
     return BN_OK;
 }
 
-extern "C" bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps) {
+namespace {
+
+// Step 2 and 3(a) of Sec. 3.3 for the rescaled solve: Q of s->f (the solver's operator with eps0 times
+// the scale^d) into s->Qv, and rho, u, e advanced by dt with its moments from the stored macroscopic
+// state.  Nothing of the state changes.
+bn_status resc_eval_moments(bn_solver* s, double dt, double eps0, double* rho1, double* u1, double* e1) {
+    const int d = s->g.d, N = s->g.N;
+    const double gamma = s->kernel == BN_HARD_SPHERE ? 1.0 : 0.0;
+    const double dxi = std::pow(2.0 * M_PI / N, d);
+    const double sc = M_PI * s->resc_w / s->resc_L;
+    s->eps = eps0 * std::pow(sc, d);
+    s->lo_refresh = true;
+    eval_device(s, s->f, s->Qv);
+    s->eps = eps0;
+    bn::launch_resc_moments(s, s->Qv, s->resc_mom);
+    cudaMemcpyAsync(s->resc_mom_host, s->resc_mom, (d + 2) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(s->flags_host, s->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
+    if (s->flags_host[2]) {
+        cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
+        return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during the rescaled step");
+    }
+    const double* S = s->resc_mom_host;   // [sum Q, sum xi_c Q (c < d), sum |xi|^2 Q]
+    bool fin = true;
+    for (int c = 0; c < d + 2; ++c) fin = fin && std::isfinite(S[c]);
+    if (!fin) return fail(BN_ERR_NONFINITE, "rescaled step: non-finite collision moments (state kept)");
+    const double coef = dxi * std::pow(sc, -gamma);
+    *rho1 = s->resc_rho + dt * coef * S[0];
+    for (int c = 0; c < 3; ++c)
+        u1[c] = c < d ? (s->resc_rho * s->resc_u[c] + dt * coef * (S[1 + c] / sc + s->resc_u[c] * S[0])) / *rho1 : 0.0;
+    *e1 = (s->resc_rho * s->resc_e + dt * 0.5 * coef * S[1 + d] / (sc * sc)) / *rho1;
+    return BN_OK;
+}
+
+double resc_omega(int d, double eps0, double T, const double* u) {
+    double u2 = 0;
+    for (int c = 0; c < d; ++c) u2 += u[c] * u[c];
+    return eps0 != 0.0 ? std::sqrt(T) : std::sqrt(T + u2 / d);
+}
+
+// One forward Euler step of Sec. 3.3 (steps 2 to 5), in place on s->f and the macroscopic state;
+// a_used, b_used (d values) receive the dilation rate and drift of its divergence term.  On an error
+// the state is that of the start of the step.
+bn_status resc_euler_step(bn_solver* s, double dt, double eps0, double* a_used, double* b_used) {
+    const int d = s->g.d;
+    const double gamma = s->kernel == BN_HARD_SPHERE ? 1.0 : 0.0;
+    const double sc = M_PI * s->resc_w / s->resc_L;
+    double rho1 = 0, u1[3] = {0, 0, 0}, e1 = 0;
+    bn_status st = resc_eval_moments(s, dt, eps0, &rho1, u1, &e1);
+    if (st != BN_OK) return st;
+    // step 3(b), (c): temperature, fugacity, scale
+    double T1 = 0, z1 = 0;
+    std::string err;
+    st = bn::rescale_temperature(d, eps0, rho1, e1, &T1, &z1, &err);
+    if (st != BN_OK) return fail(st, err + " (state kept)");
+    const double w1 = resc_omega(d, eps0, T1, u1);
+    // steps 4, 5: the divergence term and G^{n+1}
+    const double a = (w1 - s->resc_w) / (dt * s->resc_w);
+    double b[3] = {0, 0, 0};
+    for (int c = 0; c < d; ++c) b[c] = sc * (u1[c] - s->resc_u[c]) / dt;
+    bn::launch_resc_advance(s, s->f, s->Qv, a, b, dt, std::pow(sc, -gamma), s->resc_H, s->resc_M, s->resc_acc,
+                            s->resc_div);
+    if (a_used) *a_used = a;
+    if (b_used)
+        for (int c = 0; c < d; ++c) b_used[c] = b[c];
+    s->resc_rho = rho1;
+    for (int c = 0; c < 3; ++c) s->resc_u[c] = u1[c];
+    s->resc_e = e1;
+    s->resc_T = T1;
+    s->resc_z = z1;
+    s->resc_w = w1;
+    return BN_OK;
+}
+
+bn_status resc_check(bn_solver* s, double dt, int nsteps) {
     if (!valid_solver(s)) return fail(BN_ERR_ARG, "null solver");
     if (!s->resc) return fail(BN_ERR_STATE, "velocity rescaling not set (bn_rescale_set)");
     if (!s->has_state) return fail(BN_ERR_STATE, "no state set");
     if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0) return fail(BN_ERR_ARG, "dt must be > 0 and nsteps >= 0");
-    const int d = s->g.d, N = s->g.N;
-    const double eps0 = s->eps, gamma = s->kernel == BN_HARD_SPHERE ? 1.0 : 0.0;
-    const double dxi = std::pow(2.0 * M_PI / N, d);
+    return BN_OK;
+}
+
+}  // namespace
+
+extern "C" bn_status bn_step_rescaled(bn_solver* s, double dt, int nsteps) {
+    bn_status st = resc_check(s, dt, nsteps);
+    if (st != BN_OK) return st;
+    const double eps0 = s->eps;
     cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
     for (int step = 0; step < nsteps; ++step) {
-        const double sc = M_PI * s->resc_w / s->resc_L;
-        // step 2: Q^n of G^n with the rescaled quantum parameter
-        s->eps = eps0 * std::pow(sc, d);
-        s->lo_refresh = true;
-        eval_device(s, s->f, s->Qv);
-        s->eps = eps0;
-        bn::launch_resc_moments(s, s->Qv, s->resc_mom);
-        cudaMemcpyAsync(s->resc_mom_host, s->resc_mom, (d + 2) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-        cudaMemcpyAsync(s->flags_host, s->flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        cudaError_t e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
-        if (s->flags_host[2]) {
-            cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
-            return fail(BN_ERR_TIMEOUT, "a bounded device wait gave up during the rescaled step");
+        st = resc_euler_step(s, dt, eps0, nullptr, nullptr);
+        if (st != BN_OK) return st;
+        s->t += dt;
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rescaled step");
+    return BN_OK;
+}
+
+extern "C" bn_status bn_step_rescaled_rk2(bn_solver* s, double dt, int nsteps) {
+    bn_status st = resc_check(s, dt, nsteps);
+    if (st != BN_OK) return st;
+    const int d = s->g.d;
+    const size_t n = s->g.nModes;
+    const double gamma = s->kernel == BN_HARD_SPHERE ? 1.0 : 0.0;
+    if (!s->resc_G0) {
+        cudaError_t e0 = cudaMalloc((void**)&s->resc_G0, n * sizeof(double));
+        if (e0 != cudaSuccess) return cuda_fail(e0, "rescaled RK2 buffer");
+    }
+    const double eps0 = s->eps;
+    cudaMemsetAsync(s->flags + 2, 0, sizeof(int), s->stream);
+    for (int step = 0; step < nsteps; ++step) {
+        // Y^n: G^n and the macroscopic state
+        cudaMemcpyAsync(s->resc_G0, s->f, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+        const double rho0 = s->resc_rho, e0 = s->resc_e, w0 = s->resc_w, T0 = s->resc_T, z0 = s->resc_z;
+        const double s0 = M_PI * w0 / s->resc_L;
+        double u0[3];
+        for (int c = 0; c < 3; ++c) u0[c] = s->resc_u[c];
+        auto restore = [&]() {
+            cudaMemcpyAsync(s->f, s->resc_G0, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+            s->resc_rho = rho0;
+            s->resc_e = e0;
+            s->resc_w = w0;
+            s->resc_T = T0;
+            s->resc_z = z0;
+            for (int c = 0; c < 3; ++c) s->resc_u[c] = u0[c];
+            cudaStreamSynchronize(s->stream);
+        };
+        // predictor: the forward Euler step (G^(1) in s->f; its rates a1, b1)
+        double a1 = 0, b1[3] = {0, 0, 0};
+        st = resc_euler_step(s, dt, eps0, &a1, b1);
+        if (st != BN_OK) {
+            restore();
+            return st;
         }
-        const double* S = s->resc_mom_host;   // [sum Q, sum xi_c Q (c < d), sum |xi|^2 Q]
-        bool fin = true;
-        for (int c = 0; c < d + 2; ++c) fin = fin && std::isfinite(S[c]);
-        if (!fin) return fail(BN_ERR_NONFINITE, "rescaled step: non-finite collision moments (state kept)");
-        // step 3(a): rho, u, e from the moments of Q^n
-        const double coef = dxi * std::pow(sc, -gamma);
-        const double rho1 = s->resc_rho + dt * coef * S[0];
-        double u1[3] = {0, 0, 0}, u2 = 0;
-        for (int c = 0; c < d; ++c) {
-            u1[c] = (s->resc_rho * s->resc_u[c] + dt * coef * (S[1 + c] / sc + s->resc_u[c] * S[0])) / rho1;
-            u2 += u1[c] * u1[c];
+        // second stage: Q1 = Q(G^(1)) at the scale of G^(1) and the Euler moment update Y^(2)
+        const double s1 = M_PI * s->resc_w / s->resc_L;
+        double rho2 = 0, u2[3] = {0, 0, 0}, e2 = 0;
+        st = resc_eval_moments(s, dt, eps0, &rho2, u2, &e2);
+        if (st != BN_OK) {
+            restore();
+            return st;
         }
-        const double e1 = (s->resc_rho * s->resc_e + dt * 0.5 * coef * S[1 + d] / (sc * sc)) / rho1;
-        // step 3(b), (c): temperature, fugacity, scale
-        double T1 = 0, z1 = 0;
+        // Y^{n+1} = (Y^n + Y^(2)) / 2 for rho, rho u, rho e; T, z, w from them
+        const double rhoN = 0.5 * (rho0 + rho2);
+        double uN[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) uN[c] = 0.5 * (rho0 * u0[c] + rho2 * u2[c]) / rhoN;
+        const double eN = 0.5 * (rho0 * e0 + rho2 * e2) / rhoN;
+        double TN = 0, zN = 0;
         std::string err;
-        const bn_status st = bn::rescale_temperature(d, eps0, rho1, e1, &T1, &z1, &err);
-        if (st != BN_OK) return fail(st, err + " (state kept)");
-        const double w1 = eps0 != 0.0 ? std::sqrt(T1) : std::sqrt(T1 + u2 / d);
-        // steps 4, 5: the divergence term and G^{n+1}
-        const double a = (w1 - s->resc_w) / (dt * s->resc_w);
-        double b[3] = {0, 0, 0};
-        for (int c = 0; c < d; ++c) b[c] = sc * (u1[c] - s->resc_u[c]) / dt;
-        bn::launch_resc_advance(s, s->f, s->Qv, a, b, dt, std::pow(sc, -gamma), s->resc_H, s->resc_M, s->resc_acc,
+        st = bn::rescale_temperature(d, eps0, rhoN, eN, &TN, &zN, &err);
+        if (st != BN_OK) {
+            restore();
+            return fail(st, err + " (state kept)");
+        }
+        const double wN = resc_omega(d, eps0, TN, uN);
+        // G^{n+1} = G0 + dt/2 [F(G0) + F(G1)] with the midpoint rates a = ln(wN / w0) / dt and
+        // u' = (uN - u0) / dt, each F at its stage's scale.  With the predictor G1 = G0 + dt F(G0; a1, b1):
+        // G^{n+1} = (Z + W) / 2, Z = G1 + dt F(G1; a, s1 u'), W = G0 + dt T(G0; a - a1, s0 u' - b1),
+        // T the divergence part of F alone
+        const double a = std::log(wN / w0) / dt;
+        double bZ[3] = {0, 0, 0}, bW[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) {
+            const double du = (uN[c] - u0[c]) / dt;
+            bZ[c] = s1 * du;
+            bW[c] = s0 * du - b1[c];
+        }
+        bn::launch_resc_advance(s, s->f, s->Qv, a, bZ, dt, std::pow(s1, -gamma), s->resc_H, s->resc_M, s->resc_acc,
                                 s->resc_div);
-        s->resc_rho = rho1;
-        for (int c = 0; c < 3; ++c) s->resc_u[c] = u1[c];
-        s->resc_e = e1;
-        s->resc_T = T1;
-        s->resc_z = z1;
-        s->resc_w = w1;
+        bn::launch_resc_advance(s, s->resc_G0, s->Qv, a - a1, bW, dt, 0.0, s->resc_H, s->resc_M, s->resc_acc,
+                                s->resc_div);
+        bn::launch_resc_average(s, s->f, s->resc_G0);
+        s->resc_rho = rhoN;
+        for (int c = 0; c < 3; ++c) s->resc_u[c] = uN[c];
+        s->resc_e = eN;
+        s->resc_T = TN;
+        s->resc_z = zN;
+        s->resc_w = wN;
         s->t += dt;
     }
     cudaError_t e = cudaStreamSynchronize(s->stream);

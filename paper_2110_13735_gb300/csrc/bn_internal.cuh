@@ -321,8 +321,9 @@ struct bn_solver {
     double2* resc_M = nullptr;
     double2* resc_acc = nullptr;
     double* resc_div = nullptr;
-    double* resc_mom = nullptr;       // device [4]
-    double* resc_mom_host = nullptr;  // pinned [4]
+    double* resc_mom = nullptr;       // device [5]
+    double* resc_mom_host = nullptr;  // pinned [5]
+    double* resc_G0 = nullptr;        // G at the start of an RK2 step (bn_step_rescaled_rk2)
     double* moments = nullptr;   // d+6
     int* flags = nullptr;        // [0] non-finite, [1] committed steps, [2] wait timeout, [4..5] max f (u64 bits)
     int* flags_host = nullptr;   // pinned copy of the 8 flag words
@@ -440,6 +441,8 @@ bn_status rescale_temperature(int d, double eps, double rho, double e, double* T
 void launch_resc_moments(bn_solver* s, const double* Q, double* out_dev);
 void launch_resc_advance(bn_solver* s, double* G, const double* Q, double a, const double* b, double dt, double qc,
                          double* H, double2* M, double2* acc, double* div);
+// G = (G0 + G) / 2 (the last stage of the RK2 rescaled step)
+void launch_resc_average(bn_solver* s, double* G, const double* G0);
 
 // batched launches (bn_fused2d.cu): variant 0 = mixed N <= 32, 1 = mixed N = 64,
 // 2 = FP64 N <= 32, 3 = FP64 N = 64

@@ -96,6 +96,11 @@ __global__ void k_resc_update(int n, double* __restrict__ G, const double* __res
         G[j] = fma(dt, fma(qc, Q[j], -div[j]), G[j]);
 }
 
+// G = (G0 + G) / 2
+__global__ void k_resc_average(int n, double* __restrict__ G, const double* __restrict__ G0) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) G[j] = 0.5 * (G0[j] + G[j]);
+}
+
 inline int blocks_for(int n) { return (n + kResThreads - 1) / kResThreads; }
 
 // ------------------------------------------------------------------ host: dilogarithm, K, Brent
@@ -337,6 +342,12 @@ void launch_resc_advance(bn_solver* s, double* G, const double* Q, double a, con
     }
     launch_dft_inverse_real(s, acc, div, 1.0);
     k_resc_update<<<blocks_for(n), kResThreads, 0, s->stream>>>(n, G, div, Q, dt, qc);
+    s->launches++;
+}
+
+void launch_resc_average(bn_solver* s, double* G, const double* G0) {
+    const int n = s->g.nModes;
+    k_resc_average<<<blocks_for(n), kResThreads, 0, s->stream>>>(n, G, G0);
     s->launches++;
 }
 

@@ -95,6 +95,62 @@ def test_rescaled_steps_match_the_oracle(B, N, L, kernel, eps, amp, precision, t
     assert w != run.w   # the scale moved: the divergence term was exercised
 
 
+@pytest.mark.parametrize("N,L,kernel,eps,amp,off", [(16, 4.0, 0, -9.0, 0.06, True), (16, 5.0, 0, 0.0, 0.3, False),
+                                                     (12, 4.0, 1, 9.0, 0.06, True)])
+def test_rk2_rescaled_steps_match_the_oracle(B, N, L, kernel, eps, amp, off):
+    """bn_step_rescaled_rk2 against the oracle's RK2 form (predictor, trapezoidal moments, midpoint
+    rates; two evaluations per step): FP64 within 1e-12, several steps, on and off the scale."""
+    dt, steps = 0.01, 3
+    G, rho, u, e, w = initial(N, L, eps, amp)
+    if off:
+        w, u = 1.25 * w, u + np.array([0.1, -0.05])
+    run = RS.RescaledRun(N, L, S_TRUNC, kernel, eps, G, rho, u, e, w)
+    for _ in range(steps):
+        run.step_rk2(dt)
+    with B.Solver(2, N, math.pi, S_TRUNC, kernel, eps, precision=B.FP64) as s:
+        s.set_state(G)
+        s.rescale_set(L, w, u, rho, e)
+        s.step_rescaled(dt, steps, rk2=True)
+        Gg = s.get_state().reshape(N, N)
+        st = s.rescale_state()
+    assert np.linalg.norm(Gg - run.G) <= 1e-12 * np.linalg.norm(run.G)
+    assert st["w"] == pytest.approx(run.w, rel=1e-12)
+    assert np.allclose(st["u"], run.u, rtol=1e-12, atol=1e-12 * (abs(run.u).max() + w))
+    assert st["rho"] == pytest.approx(run.rho, rel=1e-12) and st["e"] == pytest.approx(run.e, rel=1e-12)
+    assert st["t"] == pytest.approx(steps * dt)
+
+
+def test_rk2_rescaled_steps_3d(B):
+    """3-D Fermi-Dirac hard spheres, N = 8, RK2 form, against the oracle (FP64, 1e-12)."""
+    N, L, dt, steps, eps = 8, 4.0, 0.01, 2, -1.0
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, j, indexing="ij"), -1)
+
+    def g0(x):
+        return 0.3 * np.exp(-np.sum((x - [0.5, 0.2, -0.1]) ** 2, -1) / 0.9) + \
+            0.2 * np.exp(-np.sum((x + [0.4, 0.3, 0.0]) ** 2, -1) / 0.6)
+
+    dv = (2.0 * L / N) ** 3
+    f = g0(v)
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1, 2)) * dv / rho
+    e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
+    T, _ = RS.temperature(3, eps, rho, e)
+    w = 1.2 * RS.omega_of(3, eps, T, u)
+    s = math.pi * w / L
+    G = g0(u + RS.xi_grid(3, N) / s) / s ** 3
+    run = RS.RescaledRun(N, L, S_TRUNC, 1, eps, G, rho, u, e, w, d=3, M1=4, M2=4)
+    for _ in range(steps):
+        run.step_rk2(dt)
+    with B.Solver(3, N, math.pi, S_TRUNC, B.HARD_SPHERE, eps, precision=B.FP64, M1=4, M2=4) as sol:
+        sol.set_state(G)
+        sol.rescale_set(L, w, u, rho, e)
+        sol.step_rescaled(dt, steps, rk2=True)
+        Gg = sol.get_state().reshape((N,) * 3)
+        st = sol.rescale_state()
+    assert np.linalg.norm(Gg - run.G) <= 1e-12 * np.linalg.norm(run.G)
+    assert st["w"] == pytest.approx(run.w, rel=1e-12) and st["z"] == pytest.approx(run.z, rel=1e-10)
+
 @pytest.mark.parametrize("eps", [0.0, -1.0, 1.0])
 def test_rescaled_steps_3d(B, eps):
     """3-D hard spheres, N = 8, started 20 % off the scale: eps = 0 (the classical temperature

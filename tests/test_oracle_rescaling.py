@@ -197,3 +197,44 @@ def test_ieq_ends_3d():
         RS.temperature(3, -1.0, 1.0, 0.75 * (1.0 / (1.001 * xF)) ** (2.0 / 3.0) / math.pi)
     with pytest.raises(ValueError):                 # a condensate: x above the Bose-Einstein end
         RS.temperature(3, 1.0, 1.0, 0.75 * (1.0 / (1.001 * RS.IEQ_BE_3D)) ** (2.0 / 3.0) / math.pi)
+
+
+# ------------------------------------------------------------------ time order of the two schemes
+def test_euler_first_and_rk2_second_order():
+    """From a start on the scale (w0 = sqrt(T(rho0, e0)), 2-D Fermi-Dirac, N = 8) to t = 0.08 against
+    an RK2 run at dt = 0.00125: halving dt halves the forward Euler error (first order) and quarters
+    the RK2 error (second order) in w, e and every value of G.  A corrector that kept the predictor's
+    forward quotient (w1 - w0) / (dt w0) as the dilation rate would leave G first order."""
+    N, L, eps = 8, 4.0, -9.0
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, indexing="ij"), -1)
+
+    def f0(x):
+        return 0.06 * (np.exp(-np.sum((x - [0.8, 0.3]) ** 2, -1) / 0.8) +
+                       0.7 * np.exp(-np.sum((x + [0.6, 0.5]) ** 2, -1) / 0.5))
+
+    dv = (2.0 * L / N) ** 2
+    f = f0(v)
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1)) * dv / rho
+    e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
+    T, _ = RS.temperature(2, eps, rho, e)
+    w = RS.omega_of(2, eps, T, u)
+    s = math.pi * w / L
+    G = f0(u + RS.xi_grid(2, N) / s) / s ** 2
+
+    def run(dt, rk2):
+        r = RS.RescaledRun(N, L, S_TRUNC, 0, eps, G, rho, u, e, w)
+        for _ in range(int(round(0.08 / dt))):
+            (r.step_rk2 if rk2 else r.step)(dt)
+        return r
+
+    ref = run(0.00125, True)
+
+    def errs(r):
+        return abs(r.w - ref.w), abs(r.e - ref.e), np.abs(r.G - ref.G).max()
+
+    for rk2, lo, hi in ((False, 1.8, 2.2), (True, 3.6, 4.6)):
+        e1, e2 = errs(run(0.02, rk2)), errs(run(0.01, rk2))
+        for a, b in zip(e1, e2):
+            assert lo <= a / b <= hi
