@@ -324,6 +324,64 @@ def leg_rescale(bn, I, steps: int, peak_fp32: float):
             "after": {"w": st["w"], "T": st["T"], "z": st["z"], "t": st["t"]}}
 
 
+def leg_rescale3d(bn, steps: int):
+    """The velocity-rescaling method in 3-D at 32^3: hard spheres, Fermi-Dirac (eps = -1), mixed
+    precision, L = 6, R = S = 2 pi / (3 + sqrt 2) on the xi box, two Gaussian bumps (variance 0.8,
+    centres +-(1.5, 0, 0), 0.45 each) started on the scale (w = sqrt(T) of their discrete moments).
+    Times `steps` forward Euler steps and `steps` steps of the RK2 form (two evaluations each)
+    against plain evaluations of the same operator, by CUDA events on the solver's stream."""
+    import torch
+    N, L, eps = 32, 6.0, -1.0
+    S = 2.0 * math.pi / (3.0 + math.sqrt(2.0))
+    c = np.array([1.5, 0.0, 0.0])
+
+    def f0(x):
+        return 0.45 * (np.exp(-np.sum((x - c) ** 2, -1) / 1.6) + np.exp(-np.sum((x + c) ** 2, -1) / 1.6))
+
+    j = np.arange(-N // 2, N // 2) * (2.0 * L / N)
+    v = np.stack(np.meshgrid(j, j, j, indexing="ij"), -1)
+    dv = (2.0 * L / N) ** 3
+    f = f0(v)
+    rho = f.sum() * dv
+    u = (v * f[..., None]).sum((0, 1, 2)) * dv / rho
+    e = 0.5 * (np.sum((v - u) ** 2, -1) * f).sum() * dv / rho
+    T, z = bn.equilibrium_temperature(3, eps, rho, e)
+    w = math.sqrt(T)
+    sc = math.pi * w / L
+    xi1 = np.arange(-N // 2, N // 2) * (2.0 * math.pi / N)
+    xi = np.stack(np.meshgrid(xi1, xi1, xi1, indexing="ij"), -1)
+    stream = torch.cuda.Stream()
+    t_create = time.perf_counter()
+    with bn.Solver(3, N, math.pi, S, bn.HARD_SPHERE, eps, stream=stream, precision=bn.MIXED) as s:
+        t_create = time.perf_counter() - t_create
+        s.set_state(f0(u + xi / sc) / sc ** 3)
+        s.rescale_set(L, w, u, rho, e)
+        s.step_rescaled(0.01, 1)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_rescaled(0.01, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        euler_ms = e0.elapsed_time(e1) / steps
+        e0.record(stream)
+        s.step_rescaled(0.01, steps, rk2=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rk2_ms = e0.elapsed_time(e1) / steps
+        e0.record(stream)
+        for _ in range(steps):
+            s.eval_collision_modes()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eval_ms = e0.elapsed_time(e1) / steps
+        st = s.rescale_state()
+    return {"workload": "3-D hard spheres N=32, Fermi-Dirac eps=-1, velocity rescaling, L = 6, mixed precision",
+            "create_s": t_create, "steps": steps, "x": abs(eps) * rho * (3.0 / (4.0 * math.pi * e)) ** 1.5,
+            "ms_per_euler_step": euler_ms, "ms_per_rk2_step": rk2_ms, "ms_per_plain_evaluation": eval_ms,
+            "rescaling_overhead": euler_ms / eval_ms - 1.0,
+            "before": {"w": w, "T": T, "z": z}, "after": {"w": st["w"], "T": st["T"], "z": st["z"], "t": st["t"]}}
+
 def leg_2d64(bn, I, evals: int, peak_fp32: float):
     """The largest serving size alone: 2-D Maxwell molecules N=64, R=6, the Gaussian of mass 5 and
     temperature 0.5 with eps=+1, mixed precision; `evals` evaluations after two warm-up ones, timed
@@ -355,8 +413,9 @@ def leg_2d64(bn, I, evals: int, peak_fp32: float):
 
 
 def run_leg_only(args):
-    """One leg alone (`--only config2|config4|2d64`), printed as one JSON line: the profiling runs'
-    command, with the 3-D solver's slice budget and pair-weight mode set from the command line."""
+    """One leg alone (`--only config2|config4|2d64|rescale|rescale3d`), printed as one JSON line: the
+    profiling runs' command, with the 3-D solver's slice budget and pair-weight mode set from the
+    command line."""
     import torch
     torch.cuda.set_device(0)
     from paper_2110_13735_gb300 import build as BUILD
@@ -364,6 +423,9 @@ def run_leg_only(args):
     from paper_2110_13735_gb300 import bn
     from paper_2110_13735_gb300 import inputs as I
     bn.load()
+    if args.only == "rescale3d":
+        print(json.dumps({"leg": args.only, **leg_rescale3d(bn, max(1, args.leg3d_steps))}))
+        return
     if args.only in ("2d64", "rescale"):
         peak = bn.measure_fma_peak(1, None)[0]
         leg = leg_2d64(bn, I, max(3, args.steps), peak) if args.only == "2d64" else \
@@ -816,7 +878,7 @@ def main():
     ap.add_argument("--leg48", action="store_true", help="also time one evaluation of the 3-D N=48 configuration")
     ap.add_argument("--leg-rescale", type=int, default=20,
                     help="timed steps of the 2-D velocity-rescaling leg (0 = skip)")
-    ap.add_argument("--only", choices=["config2", "config4", "2d64", "rescale"],
+    ap.add_argument("--only", choices=["config2", "config4", "2d64", "rescale", "rescale3d"],
                     help="run one leg alone and print it (profiling runs): a 3-D configuration, or the 2-D "
                          "N=64 mixed operator (--steps evaluations)")
     ap.add_argument("--beta-budget-mb", type=int, default=0,
