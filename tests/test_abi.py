@@ -79,6 +79,11 @@ def test_null_handles(lib):
     assert lib.bn_eval_collision_noalloc(None, None, None, 0, None) == -1
     assert lib.bn_step_rk(None, 0.1, 1) == -1
     assert lib.bn_kernel_launches(None) == 0
+    # velocity rescaling: every entry point rejects a null solver before any device work
+    assert lib.bn_rescale_set(None, 4.0, 1.0, None, 2, 1.0, 1.0) == -1
+    assert lib.bn_step_rescaled(None, 0.1, 1) == -1
+    assert lib.bn_step_rescaled_rk2(None, 0.1, 1) == -1
+    assert lib.bn_rescale_get(None, None, 9) == -1
     lib.bn_destroy_solver(None)
 
 
