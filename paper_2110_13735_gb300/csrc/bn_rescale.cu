@@ -1,5 +1,6 @@
 // bn_rescale.cu -- the velocity-rescaling method (Mouton & Rey, Sec. 3), 2-D and 3-D: the kernels of one
-// forward Euler step of Sec. 3.3 around the operator evaluation, and the host-side temperature solve.
+// forward Euler step of Sec. 3.3 around the operator evaluation (and the stage average of the RK2 form
+// that bn_api.cu builds from them), and the host-side temperature solve.
 //
 // The state is G on the grid xi_j = 2 pi j / N of [-pi, pi]^d (the solver's box T = pi), with
 // f(v) = (pi w / L)^d G((pi w / L)(v - u)).  Per step (bn_step_rescaled in bn_api.cu):
