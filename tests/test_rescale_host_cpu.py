@@ -116,3 +116,21 @@ def test_temperature_3d_bosons_near_condensation(lib, eps, T, one_minus_z):
     To, zo = RS.temperature(3, eps, rho, e)
     assert Tl == pytest.approx(T, rel=1e-12) and To == pytest.approx(T, rel=1e-12)
     assert abs(zl - float(z)) <= 4e-16 and abs(zo - float(z)) <= 4e-16
+
+
+def test_printed_fugacities_through_both_temperature_solves(lib):
+    """The fugacities printed in the Sec. 4.1 captions (tests/golden/fugacities.txt; hbar = 3, T =
+    sigma, 2-D and 3-D, Fermi-Dirac and Bose-Einstein): with the paper's rho and the internal energy
+    e = (d/2) sigma K_{d/2+1}(z) / K_{d/2}(z) of the printed z (mom2_qmaxwell), the oracle's and the
+    library's solves give back T = sigma and the printed z to its printed digits."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "fugacities.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 10
+    for d, stat, rho, sig, z, *_ in rows:
+        d, rho, sig, z = int(d), float(rho), float(sig), float(z)
+        eps = -(3.0 ** d) if stat == "FD" else 3.0 ** d
+        K = EQ.fd_integral if stat == "FD" else EQ.be_integral
+        e = 0.5 * d * sig * K(0.5 * d + 1.0, z) / K(0.5 * d, z)
+        for T, zz in (RS.temperature(d, eps, rho, e), bn.equilibrium_temperature(d, eps, rho, e)):
+            assert T == pytest.approx(sig, rel=5e-4), (d, stat, rho, sig)
+            assert zz == pytest.approx(z, rel=5e-4), (d, stat, rho, sig)
