@@ -56,7 +56,8 @@ typedef enum {
     BN_ERR_CUDA = -4,        /* a CUDA runtime call failed */
     BN_ERR_NONFINITE = -5,   /* the state became NaN/Inf during step_rk (state rolled back) */
     BN_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
-    BN_ERR_STATE = -7,       /* call out of order (e.g. no state set) */
+    BN_ERR_STATE = -7,       /* call out of order (e.g. no state set), or moments that admit no
+                                equilibrium temperature (velocity rescaling: outside I_eq) */
     BN_ERR_UNSUPPORTED = -8  /* combination not implemented (e.g. 3-D Maxwell molecules) */
 } bn_status;
 
